@@ -1,0 +1,82 @@
+"""Seeded synthetic inputs for the SMMO applications.
+
+These generators produce the starting states that both the CUDA path and the
+oracle take as inputs. They hold none of the method's arithmetic: no
+allocation, no do-all and no application rule is computed here, only the
+initial grids, bodies, instance sizes and job streams, drawn from numpy's
+PCG64 generator (platform independent) with an explicit seed.
+
+Shapes and distributions follow the workloads the applications run on:
+  - game of life: W x H torus, each cell alive with probability 0.25;
+  - wa-tor: W x H torus, 30% of the cells hold a fish and 3% a shark, the rest
+    are empty;
+  - n-body: positions uniform in the unit cube, masses log-uniform in
+    [1e-3, 1], zero velocity, values rounded to float32 so that the FP32 GPU
+    state and the FP64 oracle start from the same numbers; a draw is rejected
+    (and the seed advanced) while some pair lies within `margin` of the merge
+    distance;
+  - batched wa-tor: side lengths log-uniform in [64, 1024];
+  - served jobs: Poisson arrivals, game-of-life or wa-tor with equal odds,
+    sides log-uniform in [128, 4096], step counts uniform in [50, 1000].
+"""
+import numpy as np
+
+EMPTY, FISH, SHARK = 0, 1, 2
+
+
+def gol_initial(W, H, seed, density=0.25):
+    """uint8[H, W]: 1 where the cell starts alive."""
+    rng = np.random.default_rng(seed)
+    return (rng.random((H, W)) < density).astype(np.uint8)
+
+
+def wator_initial(W, H, seed, fish=0.30, shark=0.03):
+    """uint8[H, W] of EMPTY / FISH / SHARK."""
+    rng = np.random.default_rng(seed)
+    u = rng.random((H, W))
+    k = np.zeros((H, W), dtype=np.uint8)
+    k[u < fish] = FISH
+    k[(u >= fish) & (u < fish + shark)] = SHARK
+    return k
+
+
+def nbody_initial(n, seed, r_merge=2e-3, margin=1e-5, max_tries=64):
+    """(float64[n, 7] rows (x, y, z, vx, vy, vz, m), seed actually used).
+
+    All values are exactly representable in float32.
+    """
+    from scipy.spatial import cKDTree
+
+    for k in range(max_tries):
+        rng = np.random.default_rng(seed + k)
+        pos = rng.random((n, 3)).astype(np.float32).astype(np.float64)
+        m = (10.0 ** rng.uniform(-3.0, 0.0, n)).astype(np.float32).astype(np.float64)
+        if margin > 0 and n > 1:
+            tree = cKDTree(pos)
+            pairs = tree.query_pairs(r_merge + margin, output_type="ndarray")
+            if len(pairs):
+                d = np.linalg.norm(pos[pairs[:, 0]] - pos[pairs[:, 1]], axis=1)
+                if np.any(np.abs(d - r_merge) < margin):
+                    continue
+        rows = np.zeros((n, 7), dtype=np.float64)
+        rows[:, 0:3] = pos
+        rows[:, 6] = m
+        return rows, seed + k
+    raise RuntimeError("no admissible n-body draw within max_tries seeds")
+
+
+def batched_sides(n, seed, lo=64, hi=1024):
+    """int64[n] side lengths, floor(exp(U[ln lo, ln hi]))."""
+    rng = np.random.default_rng(seed)
+    return np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi), n))).astype(np.int64)
+
+
+def served_jobs(n, seed, rate=200.0, lo=128, hi=4096, steps_lo=50, steps_hi=1000):
+    """Job stream as a dict of arrays: arrival (s), app (0 = life, 1 = wa-tor), side, steps, seed."""
+    rng = np.random.default_rng(seed)
+    arrival = np.cumsum(rng.exponential(1.0 / rate, n))
+    app = (rng.random(n) < 0.5).astype(np.int64)
+    side = np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi), n))).astype(np.int64)
+    steps = rng.integers(steps_lo, steps_hi + 1, n)
+    seeds = rng.integers(0, 2**31 - 1, n)
+    return {"arrival": arrival, "app": app, "side": side, "steps": steps, "seed": seeds}

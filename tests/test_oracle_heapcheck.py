@@ -1,0 +1,113 @@
+"""Oracle pins: the heap invariant checker accepts consistent heaps and flags each planted violation."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def _levels(M):
+    bits = [M]
+    while bits[-1] > 64:
+        bits.append(-(-bits[-1] // 64))
+    return bits, [-(-b // 64) for b in bits]
+
+
+def _bitmap(flags, M):
+    """Hierarchical bitmap words (levels concatenated) for per-position flags."""
+    bits, words = _levels(M)
+    out = []
+    cur = np.asarray(flags, dtype=bool)
+    for l, w in enumerate(words):
+        padded = np.zeros(w * 64, dtype=bool)
+        padded[:len(cur)] = cur
+        ws = np.packbits(padded.reshape(w, 64)[:, ::-1], axis=1).view(">u8").reshape(w).astype(np.uint64)
+        out.append(ws)
+        cur = padded.reshape(w, 64).any(axis=1)
+    return np.concatenate(out), np.array(words, dtype=np.uint64)
+
+
+def _heap(seed=0, M=300, caps=(64, 40)):
+    rng = np.random.default_rng(seed)
+    T = len(caps)
+    state = rng.integers(-1, T, M)  # -1 free
+    obj_free = np.zeros(M, dtype=np.uint64)
+    btype = np.full(M, 0xFF, dtype=np.uint8)
+    live = np.zeros(T, dtype=np.int64)
+    for b in range(M):
+        t = state[b]
+        if t < 0:
+            continue
+        c = caps[t]
+        occ = rng.random(c) < rng.choice([0.3, 1.0])
+        if not occ.any():
+            occ[rng.integers(0, c)] = True
+        live[t] += occ.sum()
+        fr = 0
+        for s in range(c):
+            if not occ[s]:
+                fr |= 1 << s
+        obj_free[b] = np.uint64(fr)
+        btype[b] = t
+    free_bm, wpl = _bitmap(state < 0, M)
+    alloc = np.stack([_bitmap(state == t, M)[0] for t in range(T)])
+    active = np.stack([_bitmap((state == t) & (obj_free != 0), M)[0] for t in range(T)])
+    return dict(M=M, capacity=np.array(caps), obj_free=obj_free, block_type=btype, free_bm=free_bm,
+                alloc_bm=alloc, active_bm=active, words_per_level=wpl), live
+
+
+@pytest.mark.parametrize("seed,M", [(0, 300), (1, 64), (2, 5000), (3, 64 * 64 + 7)])
+def test_consistent_heap_passes(seed, M):
+    h, live = _heap(seed, M)
+    bad, got = O.check_heap(**h)
+    assert bad == 0
+    assert np.array_equal(got, live)
+
+
+def test_flags_each_planted_violation():
+    h, _ = _heap(5, 300)
+    full_block = int(np.nonzero((h["block_type"] == 0) & (h["obj_free"] == 0))[0][0])
+    free_block = int(np.nonzero(h["block_type"] == 0xFF)[0][0])
+    typed_block = int(np.nonzero(h["block_type"] == 1)[0][0])
+
+    def plant(fn, bit):
+        g = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in h.items()}
+        fn(g)
+        bad, _ = O.check_heap(**g)
+        assert bad & bit, (bad, bit)
+
+    # I1: a nested bit out of step with its container
+    def nested(g):
+        n0 = int(g["words_per_level"][0])
+        g["free_bm"][n0] ^= np.uint64(1 << 3)
+    plant(nested, O.INV_CONTAINER)
+
+    # I5: a free block also allocated
+    def two_states(g):
+        g["free_bm"][free_block // 64] &= ~np.uint64(0)  # unchanged
+        g["alloc_bm"][0][free_block // 64] |= np.uint64(1 << (free_block % 64))
+    plant(two_states, O.INV_ONE_STATE)
+
+    # I3: allocated[1] bit on a block whose type byte says 0
+    def wrong_type(g):
+        g["block_type"][typed_block] = 0
+    plant(wrong_type, O.INV_ALLOCATED)
+
+    # I3: an allocated block with no object
+    def empty_alloc(g):
+        g["obj_free"][typed_block] = np.uint64((1 << 40) - 1)
+    plant(empty_alloc, O.INV_ALLOCATED)
+
+    # I4: a full block marked active
+    def full_active(g):
+        g["active_bm"][0][full_block // 64] |= np.uint64(1 << (full_block % 64))
+    plant(full_active, O.INV_ACTIVE)
+
+    # range: a free-slot bit beyond the type's capacity
+    def beyond_cap(g):
+        g["obj_free"][typed_block] |= np.uint64(1 << 50)
+    plant(beyond_cap, O.INV_RANGE)
+
+    # structure: wrong level sizes
+    def structure(g):
+        g["words_per_level"] = g["words_per_level"][:1]
+    plant(structure, O.INV_STRUCTURE)
