@@ -1,0 +1,95 @@
+/*
+ * dsr_apps.h -- C ABI of the SMMO applications that drive the heap.
+ *
+ * The paper evaluates its allocator with SMMO applications (Fig. 6): among
+ * them game-of-life (cellular automaton), wator (agent-based predator-prey)
+ * and nbody / collisions (particle systems). It names them without rules;
+ * the rules implemented here are stated at each entry point and are the same
+ * as the oracle's.
+ *
+ * Each application keeps its objects in a dsr_heap created with the type
+ * descriptors returned by its *_types call (type ids in that order), plus a
+ * caller-owned device workspace of *_workspace_bytes bytes (256-byte
+ * aligned). Steps are queued on `stream`; each step is a fixed sequence of
+ * parallel do-alls (dsr_parallel_do with the method ids below). Conventions
+ * for pointers, ownership and status codes are those of dsr.h.
+ */
+#ifndef DSR_APPS_H
+#define DSR_APPS_H
+
+#include "dsr.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- game of life --------------------------------------------------------
+ * Conway's B3/S23 on a W x H torus, Moore neighbourhood. Types: 0 Cell
+ * {alive, count, idx} with idx = y*W + x, 1 Alive {x, y}. One generation is
+ * three do-alls:
+ *   DSR_METHOD_GOL_COUNT (Cell):  count = alive neighbours
+ *   DSR_METHOD_GOL_DIE   (Alive): if its cell's count is not 2 or 3 the cell
+ *                                 dies and the Alive object deletes itself
+ *   DSR_METHOD_GOL_BIRTH (Cell):  a dead cell with count 3 becomes alive and
+ *                                 creates an Alive object.
+ * Workspace: uint64 Cell handle per cell. */
+enum { DSR_METHOD_GOL_COUNT = 100, DSR_METHOD_GOL_DIE = 101, DSR_METHOD_GOL_BIRTH = 102 };
+typedef struct dsr_gol dsr_gol;
+int dsr_gol_types(dsr_type_desc* out /* 2 entries */);
+int dsr_gol_workspace_bytes(int W, int H, size_t* out);
+/* alive0_dev: device uint8[W*H], 1 = alive. Allocates the Cells and the
+ * initial Alive objects inside the heap. */
+int dsr_gol_create(dsr_heap* heap, int W, int H, const void* alive0_dev, void* workspace_dev, void* stream,
+                   dsr_gol** out);
+int dsr_gol_step(dsr_gol* g, int n_gen, void* stream);
+int dsr_gol_destroy(dsr_gol* g);
+
+/* ---- wa-tor ----------------------------------------------------------------
+ * W x H torus, von Neumann neighbours in the order N (y-1), E (x+1), S (y+1),
+ * W (x-1); cell index c = y*W + x. Types: 0 Fish {x, y, timer}, 1 Shark
+ * {x, y, timer, energy}. Random choices: r = SplitMix64 counter draw keyed on
+ * (seed, stream 0 for fish / 1 for sharks, step, mover's cell); a mover picks
+ * candidate (r mod k) of its k candidates. One step is five do-alls:
+ *   F1 (Fish):  timer += 1; candidates = empty neighbours; claim the pick
+ *               (the lowest mover cell index wins a contested cell)
+ *   F2 (Fish):  winners move; timer >= fish_breed: leave a new Fish
+ *               (timer 0) behind and reset timer
+ *   S0 (Shark): energy -= 1; at 0 the shark is deleted
+ *   S1 (Shark): timer += 1; candidates = neighbouring fish, else empty
+ *               neighbours; claim as F1
+ *   S2 (Shark): winners move; a fish in the target is deleted and energy +=
+ *               shark_gain; timer >= shark_breed: leave a new Shark (timer 0,
+ *               energy shark_energy0) behind and reset timer.
+ * Workspace: uint64 grid (0 empty, else (handle << 2) | kind), uint64 claim
+ * and uint32 intent per cell, plus the step counter. */
+enum {
+    DSR_METHOD_WATOR_F1 = 200,
+    DSR_METHOD_WATOR_F2 = 201,
+    DSR_METHOD_WATOR_S0 = 202,
+    DSR_METHOD_WATOR_S1 = 203,
+    DSR_METHOD_WATOR_S2 = 204
+};
+typedef struct {
+    int32_t W, H;
+    uint64_t seed;
+    int32_t fish_breed;     /* 3 */
+    int32_t shark_breed;    /* 10 */
+    int32_t shark_energy0;  /* 5 */
+    int32_t shark_gain;     /* 3 */
+} dsr_wator_params;
+typedef struct dsr_wator dsr_wator;
+int dsr_wator_types(dsr_type_desc* out /* 2 entries */);
+int dsr_wator_workspace_bytes(int W, int H, size_t* out);
+/* kind0_dev: device uint8[W*H]: 0 empty, 1 fish, 2 shark. Initial fish have
+ * timer 0; sharks timer 0 and energy shark_energy0. */
+int dsr_wator_create(dsr_heap* heap, const dsr_wator_params* p, const void* kind0_dev, void* workspace_dev,
+                     void* stream, dsr_wator** out);
+int dsr_wator_step(dsr_wator* w, int n_steps, void* stream);
+/* Device uint8[W*H] occupancy snapshot (0/1/2) of the current state. */
+int dsr_wator_kinds(dsr_wator* w, void* kind_out_dev, void* stream);
+int dsr_wator_destroy(dsr_wator* w);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSR_APPS_H */

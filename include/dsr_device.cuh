@@ -1,0 +1,495 @@
+/*
+ * dsr_device.cuh -- device-side API of the GB300 SOA object heap.
+ *
+ * Include from CUDA code that allocates or deletes objects inside kernels, or
+ * that defines do-all methods. Everything here runs on the device; all
+ * operations are lock-free with bounded retries: a retry loop that reaches
+ * its limit sets a sticky error bit in the heap and gives up, it never spins
+ * forever (the paper's Alg. 1 loops forever when the heap is full; this one
+ * returns DSR_NULL and sets DSR_ERR_OOM).
+ *
+ * Data structures (Section 2 "Block States", Section 3):
+ *   obj[b]        64-bit object allocation bitmap of block b; bit s is SET
+ *                 when slot s is FREE, bits at or beyond the capacity are 0.
+ *                 It is the single source of truth (Section 2, linearization
+ *                 point): every slot is taken and returned by an atomic on it.
+ *   btype[b]      type of the objects in block b.
+ *   free_bm, alloc_bm[T], active_bm[T]
+ *                 hierarchical bitmaps over the M blocks (64-bit containers;
+ *                 a nested bit is set iff its container is non-zero). They are
+ *                 hints that are eventually consistent with obj[]: each
+ *                 zero/non-zero transition of an obj[b] word obliges the
+ *                 thread that caused it to set or clear the matching
+ *                 active_bm bit, and set/clear retry until this thread's own
+ *                 atomic changed the bit (Section 2.1), so that the bits end
+ *                 up consistent once all operations have finished (Section 3).
+ *
+ * Handles: dsr_ref = (block << 6) | slot; DSR_NULL = all ones.
+ */
+#ifndef DSR_DEVICE_CUH
+#define DSR_DEVICE_CUH
+
+#include <stdint.h>
+
+#include "dsr.h"
+
+typedef unsigned long long dsr_u64;
+typedef dsr_u64 dsr_ref;
+#define DSR_NULL (~0ull)
+#define DSR_SPIN_CAP (1u << 16)  /* set/clear retries before DSR_ERR_RETRY (about 70 ms with backoff) */
+#define DSR_FIND_CAP 4096u       /* find-and-clear attempts */
+#define DSR_ALLOC_CAP 4096u      /* allocation attempts before DSR_ERR_RETRY */
+#define DSR_CTR_SLOTS 256u       /* event-counter rows (indexed by SM id) */
+#define DSR_SLOW_WAITS 64u       /* rounds a leader may wait for another initialisation */
+
+/* One hierarchical bitmap: level l has nwords[l] 64-bit containers. */
+struct dsr_hbm {
+    dsr_u64* lvl[DSR_MAX_LEVELS];
+    uint32_t nwords[DSR_MAX_LEVELS];
+    int32_t n_levels;
+    uint32_t pad_;
+};
+
+/* Device view of a heap; passed by value to kernels. */
+struct dsr_dev_heap {
+    uint8_t* data;        /* M * block_bytes of SOA data */
+    dsr_u64* obj;         /* [M] free-slot bitmaps */
+    uint8_t* btype;       /* [M] */
+    uint32_t* err;        /* sticky DSR_ERR_* bits */
+    uint32_t* inject;     /* slow-path allocations left to fail (fault injection) */
+    uint32_t* R_bid;      /* do-all block list: block ids */
+    dsr_u64* R_mask;      /* do-all block list: occupied-slot snapshot */
+    uint32_t* R_count;    /* entries in R (zero between do-alls) */
+    uint32_t* R_done;     /* CTAs of the current method kernel that finished */
+    dsr_u64* ctr;         /* [DSR_CTR_SLOTS][4] event counters, one row per SM */
+    uint32_t* slow;       /* [DSR_MAX_TYPES] slow-path block initialisations in flight */
+    uint32_t slow_max;    /* at most this many in flight per type before leaders wait */
+    dsr_u64 M;
+    uint32_t block_bytes;
+    int32_t n_types;
+    dsr_hbm free_bm;
+    dsr_hbm alloc_bm[DSR_MAX_TYPES];
+    dsr_hbm active_bm[DSR_MAX_TYPES];
+    dsr_u64 valid[DSR_MAX_TYPES];                  /* mask of the slots a block of type T has */
+    uint32_t cap[DSR_MAX_TYPES];
+    uint32_t n_fields[DSR_MAX_TYPES];
+    uint32_t foff[DSR_MAX_TYPES][DSR_MAX_FIELDS];  /* byte offset of a field's SOA array */
+    uint8_t fsize[DSR_MAX_TYPES][DSR_MAX_FIELDS];
+};
+
+#ifdef __CUDACC__
+
+/* ------------------------------------------------------------------------ */
+/* small helpers                                                            */
+/* ------------------------------------------------------------------------ */
+__device__ __forceinline__ dsr_u64 dsr_ld_relaxed(const dsr_u64* p) {
+    dsr_u64 v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned dsr_lane() {
+    unsigned l;
+    asm("mov.u32 %0, %%laneid;" : "=r"(l));
+    return l;
+}
+
+/* Add n to event counter k (DSR_CTR_*) in the row of the calling SM, so that
+ * warps of different SMs never contend on one address. */
+__device__ __forceinline__ void dsr_count(dsr_u64* ctr, unsigned k, dsr_u64 n) {
+    unsigned smid;
+    asm("mov.u32 %0, %%smid;" : "=r"(smid));
+    atomicAdd(ctr + (smid % DSR_CTR_SLOTS) * 4 + k, n);
+}
+
+__device__ __forceinline__ void dsr_backoff(unsigned tries) {
+    if (tries > 8) __nanosleep(tries < 32 ? 32u * tries : 1024u);
+}
+
+/* Position of the n-th (0-based) set bit of m; requires n < popc(m). */
+__device__ __forceinline__ int dsr_nth_bit(dsr_u64 m, int n) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 32; w >= 1; w >>= 1) {
+        int c = __popcll(m & ((1ull << w) - 1));
+        if (n >= c) {
+            n -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+/* The lowest min(k, popc(m)) set bits of m. */
+__device__ __forceinline__ dsr_u64 dsr_lowest_bits(dsr_u64 m, int k) {
+    if (k >= __popcll(m)) return m;
+    return m & ((1ull << dsr_nth_bit(m, k)) - 1);
+}
+
+/* ------------------------------------------------------------------------ */
+/* hierarchical bitmap operations (Section 2.1, Alg. 2)                     */
+/* ------------------------------------------------------------------------ */
+
+/* Set bit pos of level l. With retry == false this is try_set: it fails if
+ * the bit is already set. With retry == true it is set(pos): it retries until
+ * its own atomicOr changed the bit. If the container was empty before, this
+ * thread owes the nested bit, which it sets with set() (never try_set). */
+__device__ __forceinline__ bool dsr_hb_set(const dsr_hbm& b, dsr_u64 pos, bool retry, uint32_t* err) {
+    for (int l = 0; l < b.n_levels; ++l) {
+        dsr_u64* w = b.lvl[l] + (pos >> 6);
+        const dsr_u64 m = 1ull << (pos & 63);
+        dsr_u64 prev;
+        for (unsigned tries = 0;; ++tries) {
+            prev = atomicOr(w, m);
+            if (!(prev & m)) break;
+            if (!retry) return false;
+            if (tries >= DSR_SPIN_CAP) {
+                atomicOr(err, DSR_ERR_RETRY);
+                return false;
+            }
+            dsr_backoff(tries);
+        }
+        retry = true;
+        if (prev != 0) break;  // container already non-empty: nothing owed above
+        pos >>= 6;
+    }
+    return true;
+}
+
+/* Clear bit pos of level l (Alg. 2). try_clear when retry == false, clear(pos)
+ * otherwise. If this call cleared the last set bit of its container
+ * (popc(prev) == 1) it clears the nested bit with clear(). */
+__device__ __forceinline__ bool dsr_hb_clear(const dsr_hbm& b, dsr_u64 pos, bool retry, uint32_t* err) {
+    for (int l = 0; l < b.n_levels; ++l) {
+        dsr_u64* w = b.lvl[l] + (pos >> 6);
+        const dsr_u64 m = 1ull << (pos & 63);
+        dsr_u64 prev;
+        for (unsigned tries = 0;; ++tries) {
+            prev = atomicAnd(w, ~m);
+            if (prev & m) break;
+            if (!retry) return false;
+            if (tries >= DSR_SPIN_CAP) {
+                atomicOr(err, DSR_ERR_RETRY);
+                return false;
+            }
+            dsr_backoff(tries);
+        }
+        retry = true;
+        if (prev != m) break;  // other bits remain in the container
+        pos >>= 6;
+    }
+    return true;
+}
+
+/* try_find_set (Section 2.1, Section 2.4): descend from the top level, one
+ * container read per level. At each level the search starts at a bit
+ * position derived from `hint` and wraps, so that concurrent searchers spread
+ * over the set bits. Returns -1 (FAIL) if a container on the way is empty,
+ * which can happen while the bitmap is temporarily inconsistent. */
+__device__ __forceinline__ long long dsr_hb_find(const dsr_hbm& b, unsigned hint) {
+    dsr_u64 pos = 0;
+    for (int l = b.n_levels - 1; l >= 0; --l) {
+        const dsr_u64 w = dsr_ld_relaxed(b.lvl[l] + pos);
+        if (w == 0) return -1;
+        const unsigned r = (hint >> (5 * (l & 3))) & 63;
+        const dsr_u64 rot = r ? ((w >> r) | (w << (64 - r))) : w;
+        const int k = (__ffsll((long long)rot) - 1 + (int)r) & 63;
+        pos = pos * 64 + (dsr_u64)k;
+    }
+    return (long long)pos;
+}
+
+/* clear() of Section 2.1: find a set bit and clear it. The printed loop is
+ * read as: repeat { i = try_find_set(); if FAIL give up; if try_clear(i)
+ * return i }, with a bounded number of rounds, and FAIL reported only after
+ * the top-level container reads empty or the rounds run out. */
+__device__ __forceinline__ long long dsr_hb_clear_any(const dsr_hbm& b, unsigned hint, uint32_t* err) {
+    for (unsigned a = 0; a < DSR_FIND_CAP; ++a) {
+        const long long i = dsr_hb_find(b, hint + a * 0x9E3779B9u);
+        if (i < 0) {
+            if (dsr_ld_relaxed(b.lvl[b.n_levels - 1]) == 0) return -1;
+            dsr_backoff(a);
+            continue;
+        }
+        if (dsr_hb_clear(b, (dsr_u64)i, false, err)) return i;
+    }
+    return -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* block-level allocation and release                                      */
+/* ------------------------------------------------------------------------ */
+struct dsr_grab {
+    dsr_u64 bid;
+    dsr_u64 bits;     /* slots taken (their free bits were cleared by this call) */
+    uint32_t status;  /* 0 or a DSR_ERR_* bit */
+};
+
+__device__ __forceinline__ int dsr_block_type(const dsr_dev_heap& H, dsr_u64 b) {
+    return *(volatile const uint8_t*)(H.btype + b);
+}
+
+/* Return the slots `bits` of block b (type T) to the heap. The atomicOr on
+ * obj[b] is the linearization point. A zero -> non-zero transition (the block
+ * was full) obliges active[T].set(b). A block that became empty is reclaimed
+ * by whoever wins the CAS valid -> 0 that locks it: that CAS takes every free
+ * slot, so it is a non-zero -> zero transition that obliges
+ * active[T].clear(b); then allocated[T].clear(b) and free.set(b). The type is
+ * re-read after the CAS: if the block was reclaimed and reused meanwhile, the
+ * CAS either fails or takes the free slots of the reused block, which are
+ * then returned through this same path. Deallocation is not spelled out in
+ * the paper's abstract; this protocol is this library's reading of the block
+ * states of Fig. 2 and the linearization rule of Section 2. */
+__device__ inline void dsr_release(const dsr_dev_heap& H, int T, dsr_u64 b, dsr_u64 bits) {
+    for (int round = 0; round < 4 && bits; ++round) {
+        const dsr_u64 prev = atomicOr(H.obj + b, bits);
+        if (prev & bits) {
+            atomicOr(H.err, DSR_ERR_DOUBLE_FREE);
+            bits &= ~prev;
+            if (!bits) return;
+        }
+        if (prev == 0) dsr_hb_set(H.active_bm[T], b, true, H.err);
+        const dsr_u64 v = H.valid[T];
+        if ((prev | bits) != v) return;
+        if (atomicCAS(H.obj + b, v, 0ull) != v) return;
+        __threadfence();
+        const int T2 = dsr_block_type(H, b);
+        dsr_hb_clear(H.active_bm[T2], b, true, H.err);
+        if (H.valid[T2] == v) {
+            dsr_hb_clear(H.alloc_bm[T2], b, true, H.err);
+            dsr_hb_set(H.free_bm, b, true, H.err);
+            return;
+        }
+        // The CAS took the free slots of a reused, non-empty block of another
+        // type: give them back.
+        T = T2;
+        bits = v;
+    }
+}
+
+/* Slow path of Alg. 1: take a block from the free bitmap (find and clear),
+ * initialise it for T with its first min(k, capacity) slots already taken,
+ * publish its object bitmap, then set allocated[T] and, if slots remain,
+ * active[T]. status DSR_ERR_OOM: fault injection; DSR_ERR_RETRY: no free
+ * block was found. */
+__device__ inline dsr_grab dsr_init_block(const dsr_dev_heap& H, int T, int k, unsigned hint) {
+    if (H.inject && *(volatile uint32_t*)H.inject != 0) {
+        const unsigned v = atomicSub(H.inject, 1u);
+        if (v != 0 && v < 0x80000000u) return {0, 0, DSR_ERR_OOM};
+        atomicAdd(H.inject, 1u);  // the count ran out under us: undo
+    }
+    const long long b = dsr_hb_clear_any(H.free_bm, hint, H.err);
+    if (b < 0) return {0, 0, DSR_ERR_RETRY};
+    const unsigned c = H.cap[T];
+    const unsigned take = (unsigned)k < c ? (unsigned)k : c;
+    const dsr_u64 want = take >= 64 ? ~0ull : ((1ull << take) - 1);
+    const dsr_u64 rest = H.valid[T] & ~want;
+    H.btype[b] = (uint8_t)T;
+    __threadfence();
+    atomicExch(H.obj + b, rest);
+    dsr_count(H.ctr, DSR_CTR_BLOCKS, 1);
+    dsr_hb_set(H.alloc_bm[T], (dsr_u64)b, true, H.err);
+    if (rest) dsr_hb_set(H.active_bm[T], (dsr_u64)b, true, H.err);
+    return {(dsr_u64)b, want, 0};
+}
+
+/* Alg. 1 for up to k objects of type T, run by one thread (the leader of a
+ * warp's requests for T, Section 2.4). Fast path: find a block in active[T],
+ * take the lowest free slots of a snapshot of its bitmap with one atomicAnd,
+ * keep those actually obtained; if that emptied the free bits, clear
+ * active[T] (the block is full). Slow path: take a block from free (find and
+ * clear), initialise it for T with the first slots already taken, publish
+ * its bitmap, then set allocated[T] and, if slots remain, active[T]. */
+__device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsigned hint) {
+    for (unsigned a = 0; a < DSR_ALLOC_CAP; ++a) {
+        long long b = dsr_hb_find(H.active_bm[T], hint + a * 0x61C88647u);
+        if (b < 0) {
+            // Many warps miss the fast path at the same moment (a kernel that
+            // starts by allocating). Rather than each opening its own block,
+            // which would leave thousands of blocks nearly empty, at most
+            // slow_max leaders per type initialise blocks at a time; the
+            // others wait briefly and retry the fast path on the blocks just
+            // published. After DSR_SLOW_WAITS rounds a leader goes ahead.
+            bool counted = false;
+            if (a < DSR_SLOW_WAITS) {
+                if (*(volatile uint32_t*)(H.slow + T) >= H.slow_max) {
+                    dsr_backoff(a + 12);
+                    continue;
+                }
+                if (atomicAdd(H.slow + T, 1u) >= H.slow_max) {
+                    atomicSub(H.slow + T, 1u);
+                    dsr_backoff(a + 12);
+                    continue;
+                }
+                counted = true;
+            }
+            const dsr_grab g = dsr_init_block(H, T, k, hint ^ (a * 0x9E3779B9u));
+            if (counted) atomicSub(H.slow + T, 1u);
+            if (g.status == 0) return g;
+            // No free block (or an injected failure). Active blocks may be in
+            // flight (a release between its slot return and its
+            // active[T].set): retry a few times before reporting
+            // out-of-memory.
+            if (g.status != DSR_ERR_RETRY || a >= 16) return {0, 0, DSR_ERR_OOM};
+            dsr_backoff(a + 9);
+            continue;
+        }
+        dsr_u64* w = H.obj + b;
+        const dsr_u64 snap = dsr_ld_relaxed(w);
+        if (snap == 0) {
+            dsr_backoff(a);
+            continue;
+        }
+        const dsr_u64 want = dsr_lowest_bits(snap, k);
+        const dsr_u64 prev = atomicAnd(w, ~want);
+        const dsr_u64 got = prev & want;
+        if (!got) continue;
+        __threadfence();
+        const int T2 = dsr_block_type(H, (dsr_u64)b);
+        if ((prev & ~want) == 0) dsr_hb_clear(H.active_bm[T2], (dsr_u64)b, true, H.err);
+        if (T2 != T) {
+            // Stale hint: the block was reclaimed and reused for another type.
+            dsr_release(H, T2, (dsr_u64)b, got);
+            continue;
+        }
+        return {(dsr_u64)b, got, 0};
+    }
+    return {0, 0, DSR_ERR_RETRY};
+}
+
+/* ------------------------------------------------------------------------ */
+/* public device API                                                         */
+/* ------------------------------------------------------------------------ */
+
+/* new T: callable by any subset of a warp's lanes, with any mix of types.
+ * Lanes asking for the same type are served by one leader (allocation
+ * request coalescing, Section 2.4): it reserves slots for all of them, in as
+ * few atomics as the free slots allow, and hands them out by shuffle.
+ * Returns DSR_NULL (and sets DSR_ERR_OOM or DSR_ERR_RETRY) on failure. The
+ * new object's fields are not initialised. */
+__device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, T);
+    const unsigned lane = dsr_lane();
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1));
+    const int need = __popc(peers);
+    const unsigned hint = (blockIdx.x * 0x9E3779B1u) ^ ((threadIdx.x >> 5) * 0x85EBCA77u) ^ (unsigned)T;
+    dsr_ref mine = DSR_NULL;
+    int served = 0;
+    while (served < need) {
+        dsr_u64 bid = 0, bits = 0;
+        uint32_t st = 0;
+        if ((int)lane == leader) {
+            const dsr_grab g = dsr_reserve(H, T, need - served, hint + (unsigned)served);
+            bid = g.bid;
+            bits = g.bits;
+            st = g.status;
+            if (st) atomicOr(H.err, st);
+            else dsr_count(H.ctr, DSR_CTR_ALLOCS, (dsr_u64)__popcll(bits));
+        }
+        bid = __shfl_sync(peers, bid, leader);
+        bits = __shfl_sync(peers, bits, leader);
+        st = __shfl_sync(peers, st, leader);
+        if (st) break;
+        const int n = __popcll(bits);
+        if (rank >= served && rank < served + n) mine = (bid << 6) | (dsr_u64)dsr_nth_bit(bits, rank - served);
+        served += n;
+    }
+    return mine;
+}
+
+/* delete: callable by any subset of a warp's lanes. Lanes deleting objects
+ * of the same block are combined into one atomicOr by a leader. DSR_NULL is
+ * ignored; a handle outside the heap sets DSR_ERR_BAD_HANDLE. */
+__device__ inline void dsr_delete(const dsr_dev_heap& H, dsr_ref r) {
+    if (r == DSR_NULL) return;
+    const unsigned act = __activemask();
+    const dsr_u64 bid = r >> 6;
+    const unsigned slot = (unsigned)(r & 63);
+    const unsigned peers = __match_any_sync(act, bid);
+    const unsigned lane = dsr_lane();
+    const unsigned lo = __reduce_or_sync(peers, slot < 32 ? (1u << slot) : 0u);
+    const unsigned hi = __reduce_or_sync(peers, slot >= 32 ? (1u << (slot - 32)) : 0u);
+    if ((int)lane != __ffs(peers) - 1) return;
+    if (bid >= H.M) {
+        atomicOr(H.err, DSR_ERR_BAD_HANDLE);
+        return;
+    }
+    const int T = dsr_block_type(H, bid);
+    if (T >= H.n_types) {
+        atomicOr(H.err, DSR_ERR_BAD_HANDLE);
+        return;
+    }
+    dsr_count(H.ctr, DSR_CTR_FREES, (dsr_u64)(__popc(lo) + __popc(hi)));
+    dsr_release(H, T, bid, ((dsr_u64)hi << 32) | lo);
+}
+
+/* Address of field f of the object r (type T): block base + the field's SOA
+ * array offset + slot * field size. Consecutive slots are adjacent. */
+template <class F>
+__device__ __forceinline__ F* dsr_field(const dsr_dev_heap& H, int T, dsr_ref r, int f) {
+    return reinterpret_cast<F*>(H.data + (r >> 6) * H.block_bytes + H.foff[T][f]) + (r & 63);
+}
+
+/* ------------------------------------------------------------------------ */
+/* parallel do-all (Section 2.3)                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Threads per listed block in the method kernel: 32 when the type's capacity
+ * fits one warp, else 64. Each warp then covers one block, reads its R entry
+ * once and touches one contiguous segment of every SOA array. */
+__device__ __forceinline__ unsigned dsr_span_shift(const dsr_dev_heap& H, int T) { return H.cap[T] <= 32 ? 5u : 6u; }
+
+/* End of every kernel that consumes R: the last CTA to finish resets the
+ * block-list counter for the next do-all. Returns true in thread 0 of that
+ * last CTA. */
+__device__ __forceinline__ bool dsr_doall_finish(const dsr_dev_heap& H) {
+    __syncthreads();
+    bool last = false;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(H.R_done, 1u);
+        if (t == gridDim.x - 1) {
+            *(volatile uint32_t*)H.R_count = 0;
+            *(volatile uint32_t*)H.R_done = 0;
+            __threadfence();
+            last = true;
+        }
+    }
+    return last;
+}
+
+/* Optional end-of-do-all hook: Method::finish(H, T, args) runs once, in the
+ * last CTA, after every object has been visited. */
+template <class M>
+__device__ __forceinline__ auto dsr_call_finish(const dsr_dev_heap& H, int T, const typename M::Args& a, int)
+    -> decltype(M::finish(H, T, a), void()) {
+    M::finish(H, T, a);
+}
+template <class M>
+__device__ __forceinline__ void dsr_call_finish(const dsr_dev_heap&, int, const typename M::Args&, long) {}
+
+/* Method kernel of a do-all over type T. Method is a type with
+ *   struct Args;  (trivially copyable)
+ *   static __device__ void run(const dsr_dev_heap&, int T, const Args&, dsr_ref self);
+ *   optionally static __device__ void finish(const dsr_dev_heap&, int T, const Args&);
+ * Persistent grid-stride loop over (listed block, slot); a slot runs the
+ * method iff it was occupied in the snapshot taken by the scan. */
+template <class Method>
+__global__ void dsr_doall_kernel(const __grid_constant__ dsr_dev_heap H, int T,
+                                 const __grid_constant__ typename Method::Args args) {
+    const unsigned sh = dsr_span_shift(H, T);
+    const dsr_u64 total = (dsr_u64)(*(volatile uint32_t*)H.R_count) << sh;
+    const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
+    for (dsr_u64 g = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        const dsr_u64 i = g >> sh;
+        const unsigned s = (unsigned)(g & ((1u << sh) - 1));
+        if ((H.R_mask[i] >> s) & 1ull) Method::run(H, T, args, ((dsr_u64)H.R_bid[i] << 6) | s);
+    }
+    if (dsr_doall_finish(H)) dsr_call_finish<Method>(H, T, args, 0);
+}
+
+#endif /* __CUDACC__ */
+#endif /* DSR_DEVICE_CUH */

@@ -1,0 +1,115 @@
+"""Python binding of the SMMO applications (include/dsr_apps.h): argument marshalling only."""
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from .heap import Heap, _stream_ptr, heap_bytes_for_blocks
+
+GOL_TYPES = [[4, 4, 4], [4, 4]]          # Cell {alive, count, idx}, Alive {x, y}
+WATOR_TYPES = [[4, 4, 4], [4, 4, 4, 4]]  # Fish {x, y, timer}, Shark {x, y, timer, energy}
+
+
+def _sorted_rows(a):
+    if len(a) == 0:
+        return a.reshape(0, a.shape[1] if a.ndim == 2 else 0)
+    idx = np.lexsort(a.T[::-1])
+    return a[idx]
+
+
+def _blocks_for(cells, caps, slack=2.0):
+    return int(slack * sum(math.ceil(cells / c) for c in caps)) + 256
+
+
+class Gol:
+    """Game of life (B3/S23) on a W x H torus, driven through libdsr."""
+
+    def __init__(self, W, H, alive0, heap_bytes=None, tuning=None, stream=None):
+        self.lib = L.load()
+        self.W, self.H = W, H
+        if heap_bytes is None:
+            heap_bytes = heap_bytes_for_blocks(GOL_TYPES, _blocks_for(W * H, [42, 64]), tuning)
+        self.heap = Heap(GOL_TYPES, heap_bytes, names=["Cell", "Alive"], tuning=tuning, stream=stream)
+        ws = C.c_size_t(0)
+        L.check(self.lib.dsr_gol_workspace_bytes(W, H, C.byref(ws)), "dsr_gol_workspace_bytes")
+        self.workspace = torch.empty(ws.value, dtype=torch.uint8, device="cuda")
+        a0 = torch.as_tensor(np.ascontiguousarray(alive0, dtype=np.uint8).reshape(-1)).cuda()
+        h = C.c_void_p()
+        L.check(self.lib.dsr_gol_create(self.heap.handle, W, H, C.c_void_p(a0.data_ptr()),
+                                        C.c_void_p(self.workspace.data_ptr()), _stream_ptr(stream), C.byref(h)),
+                "dsr_gol_create")
+        self.handle = h
+        self._a0 = a0
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.dsr_gol_destroy(self.handle)
+            self.handle = None
+
+    def step(self, n=1, stream=None):
+        L.check(self.lib.dsr_gol_step(self.handle, n, _stream_ptr(stream)), "dsr_gol_step")
+
+    def method_args(self):
+        return L.GolArgs(C.c_void_p(self.workspace.data_ptr()), self.W, self.H)
+
+    def dump(self):
+        """(cells int32[W*H, 3] in idx order, alive int32[k, 2] sorted)."""
+        cf, _ = self.heap.dump(0)
+        af, _ = self.heap.dump(1)
+        cells = cf.view(np.int32)
+        cells = cells[np.argsort(cells[:, 2], kind="stable")]
+        return cells, _sorted_rows(af.view(np.int32))
+
+    def hash(self):
+        return self.heap.hash(0), self.heap.hash(1)
+
+
+class Wator:
+    """Wa-Tor predator-prey on a W x H torus, driven through libdsr."""
+
+    def __init__(self, W, H, kind0, seed, fish_breed=3, shark_breed=10, shark_energy0=5, shark_gain=3,
+                 heap_bytes=None, tuning=None, stream=None):
+        self.lib = L.load()
+        self.W, self.H = W, H
+        if heap_bytes is None:
+            heap_bytes = heap_bytes_for_blocks(WATOR_TYPES, _blocks_for(W * H, [48]), tuning)
+        self.heap = Heap(WATOR_TYPES, heap_bytes, names=["Fish", "Shark"], tuning=tuning, stream=stream)
+        ws = C.c_size_t(0)
+        L.check(self.lib.dsr_wator_workspace_bytes(W, H, C.byref(ws)), "dsr_wator_workspace_bytes")
+        self.workspace = torch.empty(ws.value, dtype=torch.uint8, device="cuda")
+        k0 = torch.as_tensor(np.ascontiguousarray(kind0, dtype=np.uint8).reshape(-1)).cuda()
+        self.params = L.WatorParams(W, H, seed, fish_breed, shark_breed, shark_energy0, shark_gain)
+        h = C.c_void_p()
+        L.check(self.lib.dsr_wator_create(self.heap.handle, C.byref(self.params), C.c_void_p(k0.data_ptr()),
+                                          C.c_void_p(self.workspace.data_ptr()), _stream_ptr(stream),
+                                          C.byref(h)), "dsr_wator_create")
+        self.handle = h
+        self._k0 = k0
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.dsr_wator_destroy(self.handle)
+            self.handle = None
+
+    def step(self, n=1, stream=None):
+        L.check(self.lib.dsr_wator_step(self.handle, n, _stream_ptr(stream)), "dsr_wator_step")
+
+    def counts(self):
+        st = self.heap.stats()
+        return st["live_objects"][0], st["live_objects"][1]
+
+    def dump(self):
+        """(fish int32[n, 3] sorted, sharks int32[m, 4] sorted)."""
+        f, _ = self.heap.dump(0)
+        s, _ = self.heap.dump(1)
+        return _sorted_rows(f.view(np.int32)), _sorted_rows(s.view(np.int32))
+
+    def hash(self):
+        return self.heap.hash(0), self.heap.hash(1)
+
+    def grid(self):
+        out = torch.empty(self.W * self.H, dtype=torch.uint8, device="cuda")
+        L.check(self.lib.dsr_wator_kinds(self.handle, C.c_void_p(out.data_ptr()), _stream_ptr()), "dsr_wator_kinds")
+        return out.cpu().numpy().reshape(self.H, self.W)

@@ -1,0 +1,180 @@
+// Game of life as an SMMO program (Fig. 6c): three do-alls per generation
+// over Cell and Alive objects. Rules: B3/S23 on a torus, Moore neighbourhood.
+#include "dsr_apps.h"
+#include "dsr_internal.cuh"
+
+namespace {
+enum { CELL = 0, ALIVE = 1 };
+enum { C_ALIVE = 0, C_COUNT = 1, C_IDX = 2 };
+enum { A_X = 0, A_Y = 1 };
+
+struct GolArgs {
+    const dsr_ref* cell_ref;  // grid index -> Cell handle
+    int32_t W, H;
+};
+
+// (i) do-all Cell: number of alive cells among the 8 neighbours.
+struct MCount {
+    typedef GolArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref self) {
+        const int idx = *dsr_field<int32_t>(H, CELL, self, C_IDX);
+        const int x = idx % a.W, y = idx / a.W;
+        int n = 0;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int ny = y + dy < 0 ? y + dy + a.H : (y + dy >= a.H ? y + dy - a.H : y + dy);
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0) continue;
+                const int nx = x + dx < 0 ? x + dx + a.W : (x + dx >= a.W ? x + dx - a.W : x + dx);
+                const dsr_ref c = a.cell_ref[ny * a.W + nx];
+                if (c != DSR_NULL) n += *dsr_field<int32_t>(H, CELL, c, C_ALIVE);
+            }
+        }
+        *dsr_field<int32_t>(H, CELL, self, C_COUNT) = n;
+    }
+};
+
+// (ii) do-all Alive: death when the cell's count is not 2 or 3.
+struct MDie {
+    typedef GolArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref self) {
+        const int x = *dsr_field<int32_t>(H, ALIVE, self, A_X);
+        const int y = *dsr_field<int32_t>(H, ALIVE, self, A_Y);
+        const dsr_ref c = a.cell_ref[y * a.W + x];
+        if (c == DSR_NULL) return;
+        const int n = *dsr_field<int32_t>(H, CELL, c, C_COUNT);
+        if (n != 2 && n != 3) {
+            *dsr_field<int32_t>(H, CELL, c, C_ALIVE) = 0;
+            dsr_delete(H, self);
+        }
+    }
+};
+
+// (iii) do-all Cell: birth of a dead cell with exactly 3 alive neighbours.
+struct MBirth {
+    typedef GolArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref self) {
+        int32_t* alive = dsr_field<int32_t>(H, CELL, self, C_ALIVE);
+        if (*alive || *dsr_field<int32_t>(H, CELL, self, C_COUNT) != 3) return;
+        *alive = 1;
+        const int idx = *dsr_field<int32_t>(H, CELL, self, C_IDX);
+        const dsr_ref r = dsr_new(H, ALIVE);
+        if (r == DSR_NULL) return;
+        *dsr_field<int32_t>(H, ALIVE, r, A_X) = idx % a.W;
+        *dsr_field<int32_t>(H, ALIVE, r, A_Y) = idx / a.W;
+    }
+};
+
+// One thread per cell: create the Cell and, where alive, its Alive object.
+__global__ void k_gol_init(const __grid_constant__ dsr_dev_heap H, const uint8_t* alive0, dsr_ref* cell_ref,
+                           int W, int Hh) {
+    const int n = W * Hh;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int alive = alive0[i] ? 1 : 0;
+        const dsr_ref c = dsr_new(H, CELL);
+        cell_ref[i] = c;
+        if (c != DSR_NULL) {
+            *dsr_field<int32_t>(H, CELL, c, C_ALIVE) = alive;
+            *dsr_field<int32_t>(H, CELL, c, C_COUNT) = 0;
+            *dsr_field<int32_t>(H, CELL, c, C_IDX) = i;
+        }
+        if (alive) {
+            const dsr_ref r = dsr_new(H, ALIVE);
+            if (r != DSR_NULL) {
+                *dsr_field<int32_t>(H, ALIVE, r, A_X) = i % W;
+                *dsr_field<int32_t>(H, ALIVE, r, A_Y) = i / W;
+            }
+        }
+    }
+}
+
+const int kCellFields[3] = {4, 4, 4};
+const int kAliveFields[2] = {4, 4};
+
+bool heap_matches(const dsr_heap* h) {
+    const dsr_layout& L = h->layout;
+    if (L.n_types < 2 || L.n_fields[CELL] != 3 || L.n_fields[ALIVE] != 2) return false;
+    for (int f = 0; f < 3; ++f)
+        if (L.field_bytes[CELL][f] != 4) return false;
+    for (int f = 0; f < 2; ++f)
+        if (L.field_bytes[ALIVE][f] != 4) return false;
+    return true;
+}
+}  // namespace
+
+struct dsr_gol {
+    dsr_heap* heap;
+    GolArgs args;
+};
+
+extern "C" int dsr_gol_types(dsr_type_desc* out) {
+    if (!out) return DSR_E_INVALID;
+    out[0] = dsr_type_desc{"Cell", 3, kCellFields};
+    out[1] = dsr_type_desc{"Alive", 2, kAliveFields};
+    return DSR_OK;
+}
+
+extern "C" int dsr_gol_workspace_bytes(int W, int H, size_t* out) {
+    if (!out || W < 3 || H < 3 || (int64_t)W * H > (1ll << 31)) return DSR_E_INVALID;
+    *out = (size_t)W * H * sizeof(dsr_ref);
+    return DSR_OK;
+}
+
+extern "C" int dsr_gol_create(dsr_heap* heap, int W, int H, const void* alive0_dev, void* workspace_dev,
+                              void* stream, dsr_gol** out) {
+    size_t ws;
+    if (!heap || !alive0_dev || !workspace_dev || !out || dsr_gol_workspace_bytes(W, H, &ws)) return DSR_E_INVALID;
+    if (!heap_matches(heap)) return DSR_E_INVALID;
+    dsr_gol* g = new dsr_gol;
+    g->heap = heap;
+    g->args = GolArgs{static_cast<const dsr_ref*>(workspace_dev), W, H};
+    const int n = W * H;
+    int ctas = (n + 255) / 256;
+    if (ctas > heap->sm_count * 8) ctas = heap->sm_count * 8;
+    k_gol_init<<<ctas, 256, 0, dsr__stream(stream)>>>(heap->dev, static_cast<const uint8_t*>(alive0_dev),
+                                                       static_cast<dsr_ref*>(workspace_dev), W, H);
+    int rc = dsr__check_launch("k_gol_init");
+    if (rc) {
+        delete g;
+        return rc;
+    }
+    *out = g;
+    return DSR_OK;
+}
+
+extern "C" int dsr_gol_step(dsr_gol* g, int n_gen, void* stream) {
+    if (!g || n_gen < 0) return DSR_E_INVALID;
+    cudaStream_t s = dsr__stream(stream);
+    for (int i = 0; i < n_gen; ++i) {
+        int rc = dsr__doall<MCount>(g->heap, CELL, g->args, s);
+        if (!rc) rc = dsr__doall<MDie>(g->heap, ALIVE, g->args, s);
+        if (!rc) rc = dsr__doall<MBirth>(g->heap, CELL, g->args, s);
+        if (rc) return rc;
+    }
+    return DSR_OK;
+}
+
+extern "C" int dsr_gol_destroy(dsr_gol* g) {
+    delete g;
+    return DSR_OK;
+}
+
+// dsr_parallel_do entry for the game-of-life methods. Args: dsr_gol_method_args
+// = { const uint64_t* cell_ref_dev; int32_t W, H; }.
+int dsr__gol_method(dsr_heap* h, int type, int method, const void* args, size_t bytes, cudaStream_t s,
+                    bool with_scan) {
+    if (!heap_matches(h) || !args || bytes != sizeof(GolArgs)) return DSR_E_INVALID;
+    GolArgs a;
+    memcpy(&a, args, sizeof a);
+    switch (method) {
+        case DSR_METHOD_GOL_COUNT:
+            return type == CELL ? dsr__doall<MCount>(h, type, a, s, with_scan) : DSR_E_INVALID;
+        case DSR_METHOD_GOL_DIE:
+            return type == ALIVE ? dsr__doall<MDie>(h, type, a, s, with_scan) : DSR_E_INVALID;
+        case DSR_METHOD_GOL_BIRTH:
+            return type == CELL ? dsr__doall<MBirth>(h, type, a, s, with_scan) : DSR_E_INVALID;
+        default:
+            return DSR_E_INVALID;
+    }
+}

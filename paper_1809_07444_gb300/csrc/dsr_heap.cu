@@ -1,0 +1,711 @@
+// Heap creation, block geometry, the do-all scan, statistics, generic
+// methods and the C ABI of dsr.h.
+#include <algorithm>
+#include <cstdlib>
+#include <new>
+
+#include "dsr_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_cuda_err[256] = "";
+
+void dsr__set_cuda_error(cudaError_t e, const char* where) {
+    snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", where, cudaGetErrorString(e));
+}
+
+int dsr__check_launch(const char* where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        dsr__set_cuda_error(e, where);
+        return DSR_E_CUDA;
+    }
+    return DSR_OK;
+}
+
+extern "C" const char* dsr_last_cuda_error(void) { return g_cuda_err; }
+
+extern "C" const char* dsr_status_string(int s) {
+    switch (s) {
+        case DSR_OK: return "ok";
+        case DSR_E_INVALID: return "invalid argument";
+        case DSR_E_OOM: return "arena too small";
+        case DSR_E_CUDA: return "CUDA error";
+        case DSR_E_DEVICE: return "device-side error";
+        default: return "unknown status";
+    }
+}
+
+// ---------------------------------------------------------------------------
+// geometry (Section 2: equal-size blocks; the smallest type has cap_min
+// slots, which fixes the block size; larger types get fewer slots in
+// proportion to their size)
+// ---------------------------------------------------------------------------
+static inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+static uint64_t type_bytes(const dsr_layout& L, int t, uint32_t cap) {
+    uint64_t off = 0;
+    for (uint32_t f = 0; f < L.n_fields[t]; ++f) off += round_up((uint64_t)cap * L.field_bytes[t][f], 8);
+    return off;
+}
+
+static int geometry(const dsr_type_desc* types, int n_types, const dsr_tuning& tune, dsr_layout* L) {
+    if (!types || n_types < 1 || n_types > DSR_MAX_TYPES) return DSR_E_INVALID;
+    if (tune.cap_min != 32 && tune.cap_min != 64) return DSR_E_INVALID;
+    memset(L, 0, sizeof *L);
+    L->n_types = (uint32_t)n_types;
+    uint64_t smin = ~0ull;
+    int tmin = 0;
+    uint64_t size[DSR_MAX_TYPES];
+    for (int t = 0; t < n_types; ++t) {
+        const dsr_type_desc& d = types[t];
+        if (d.n_fields < 1 || d.n_fields > DSR_MAX_FIELDS || !d.field_bytes) return DSR_E_INVALID;
+        L->n_fields[t] = (uint32_t)d.n_fields;
+        size[t] = 0;
+        for (int f = 0; f < d.n_fields; ++f) {
+            if (d.field_bytes[f] != 4 && d.field_bytes[f] != 8) return DSR_E_INVALID;
+            L->field_bytes[t][f] = (uint32_t)d.field_bytes[f];
+            size[t] += (uint64_t)d.field_bytes[f];
+        }
+        if (size[t] < smin) {
+            smin = size[t];
+            tmin = t;
+        }
+    }
+    const uint64_t block_bytes = round_up(type_bytes(*L, tmin, (uint32_t)tune.cap_min), 128);
+    L->block_bytes = (uint32_t)block_bytes;
+    for (int t = 0; t < n_types; ++t) {
+        uint64_t c = (uint64_t)tune.cap_min * smin / size[t];
+        if (c > 64) c = 64;
+        if (c < 1) c = 1;
+        while (c > 1 && type_bytes(*L, t, (uint32_t)c) > block_bytes) --c;
+        L->capacity[t] = (uint32_t)c;
+        uint64_t off = 0;
+        for (uint32_t f = 0; f < L->n_fields[t]; ++f) {
+            L->field_offset[t][f] = (uint32_t)off;
+            off += round_up(c * L->field_bytes[t][f], 8);
+        }
+    }
+    return DSR_OK;
+}
+
+// Offsets of every metadata array for M blocks; returns the arena bytes used.
+static uint64_t place(dsr_layout* L, uint64_t M) {
+    L->n_blocks = M;
+    uint64_t n = M;
+    int lv = 0;
+    uint64_t words = 0;
+    for (;;) {
+        L->words_per_level[lv] = (n + 63) / 64;
+        words += L->words_per_level[lv];
+        ++lv;
+        if (n <= 64) break;
+        n = (n + 63) / 64;
+    }
+    L->n_levels = (uint32_t)lv;
+    L->bitmap_words = words;
+    const uint64_t T = L->n_types;
+    uint64_t off = DSR_HEADER_BYTES;
+    L->off_free_bm = off;
+    off += words * 8;
+    L->off_alloc_bm = off;
+    off += T * words * 8;
+    L->off_active_bm = off;
+    off += T * words * 8;
+    off = round_up(off, 256);
+    L->off_obj = off;
+    off += M * 8;
+    off = round_up(off, 256);
+    uint64_t off_rmask = off;
+    off += M * 8;
+    off = round_up(off, 256);
+    uint64_t off_rbid = off;
+    off += M * 4;
+    off = round_up(off, 256);
+    L->off_type = off;
+    off += M;
+    off = round_up(off, 1024);
+    L->off_data = off;
+    off += M * L->block_bytes;
+    L->arena_bytes_used = off;
+    (void)off_rmask;
+    (void)off_rbid;
+    return off;
+}
+
+static uint64_t off_rmask(const dsr_layout& L) { return round_up(L.off_obj + L.n_blocks * 8, 256); }
+static uint64_t off_rbid(const dsr_layout& L) { return round_up(off_rmask(L) + L.n_blocks * 8, 256); }
+
+static dsr_tuning resolve_tuning(const dsr_tuning* t) {
+    dsr_tuning r{64, 256, 0};
+    if (t) {
+        if (t->cap_min) r.cap_min = t->cap_min;
+        if (t->threads) r.threads = t->threads;
+        r.ctas_per_sm = t->ctas_per_sm;
+    }
+    return r;
+}
+
+extern "C" int dsr_heap_bytes_for_blocks(const dsr_type_desc* types, int n_types, uint64_t n_blocks,
+                                         const dsr_tuning* tune, size_t* out_bytes) {
+    if (!out_bytes || n_blocks == 0 || n_blocks > 0xFFFFFFFFull) return DSR_E_INVALID;
+    dsr_layout L;
+    int rc = geometry(types, n_types, resolve_tuning(tune), &L);
+    if (rc) return rc;
+    *out_bytes = (size_t)place(&L, n_blocks);
+    return DSR_OK;
+}
+
+extern "C" int dsr_heap_plan(const dsr_type_desc* types, int n_types, uint64_t n_blocks, const dsr_tuning* tune,
+                             dsr_layout* out) {
+    if (!out || n_blocks == 0 || n_blocks > 0xFFFFFFFFull) return DSR_E_INVALID;
+    dsr_layout L;
+    int rc = geometry(types, n_types, resolve_tuning(tune), &L);
+    if (rc) return rc;
+    place(&L, n_blocks);
+    *out = L;
+    return DSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernels: reset, scan, statistics
+// ---------------------------------------------------------------------------
+
+// Mark every block free: free bitmap bits [0, n_l) set on every level, the
+// other bitmaps and the object bitmaps zero (already cleared by memset).
+__global__ void k_heap_mark_free(const __grid_constant__ dsr_dev_heap H, dsr_u64 M) {
+    const dsr_u64 tid = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
+    dsr_u64 n = M;
+    for (int l = 0; l < H.free_bm.n_levels; ++l) {
+        const dsr_u64 nw = H.free_bm.nwords[l];
+        for (dsr_u64 i = tid; i < nw; i += stride) {
+            const dsr_u64 lo = i * 64;
+            const dsr_u64 k = n - lo >= 64 ? 64 : n - lo;
+            H.free_bm.lvl[l][i] = k >= 64 ? ~0ull : ((1ull << k) - 1);
+        }
+        n = (n + 63) / 64;
+    }
+    for (dsr_u64 b = tid; b < M; b += stride) H.btype[b] = 0xFF;
+}
+
+// Do-all steps 1 and 2 (Section 2.3, Fig. 4): list the set bits of
+// allocated[T] and compact them into R by a prefix sum. Each warp takes 32
+// level-0 words at a time (skipping words whose level-1 bit is clear), counts
+// their set bits, forms an exclusive prefix sum across the warp with
+// shuffles, reserves its run of R with one atomicAdd, and writes for every
+// listed block its id and the snapshot of its occupied slots.
+__global__ void k_scan(const __grid_constant__ dsr_dev_heap H, int T) {
+    const dsr_hbm& A = H.alloc_bm[T];
+    const uint32_t nw = A.nwords[0];
+    const dsr_u64 v = H.valid[T];
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = warp * 32; base < nw; base += nwarps * 32) {
+        const uint32_t idx = base + lane;
+        dsr_u64 w = 0;
+        if (idx < nw) {
+            bool maybe = true;
+            if (A.n_levels > 1) maybe = (A.lvl[1][idx >> 6] >> (idx & 63)) & 1ull;
+            if (maybe) w = A.lvl[0][idx];
+        }
+        const unsigned cnt = __popcll(w);
+        unsigned incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane >= (unsigned)d) incl += y;
+        }
+        const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (total == 0) continue;
+        unsigned start = 0;
+        if (lane == 31) start = atomicAdd(H.R_count, total);
+        start = __shfl_sync(0xFFFFFFFFu, start, 31) + incl - cnt;
+        unsigned objs = 0;
+        while (w) {
+            const int b = __ffsll((long long)w) - 1;
+            w &= w - 1;
+            const dsr_u64 bid = (dsr_u64)idx * 64 + b;
+            const dsr_u64 live = v & ~H.obj[bid];
+            H.R_bid[start] = (uint32_t)bid;
+            H.R_mask[start] = live;
+            objs += __popcll(live);
+            ++start;
+        }
+        objs = __reduce_add_sync(0xFFFFFFFFu, objs);
+        if (lane == 0 && objs) dsr_count(H.ctr, DSR_CTR_VISITS, objs);
+    }
+}
+
+// Statistics: out[0] free blocks; out[1 + 3T + {0,1,2}] allocated blocks,
+// active blocks, live objects of type T.
+__global__ void k_stats(const __grid_constant__ dsr_dev_heap H, dsr_u64* out) {
+    const dsr_u64 tid = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
+    const dsr_u64 nw = H.free_bm.nwords[0];
+    dsr_u64 nfree = 0;
+    for (dsr_u64 i = tid; i < nw; i += stride) nfree += __popcll(H.free_bm.lvl[0][i]);
+    if (nfree) atomicAdd(out, nfree);
+    for (int t = 0; t < H.n_types; ++t) {
+        dsr_u64 na = 0, nact = 0, live = 0;
+        const dsr_u64 v = H.valid[t];
+        for (dsr_u64 i = tid; i < nw; i += stride) {
+            dsr_u64 a = H.alloc_bm[t].lvl[0][i];
+            na += __popcll(a);
+            nact += __popcll(H.active_bm[t].lvl[0][i]);
+            while (a) {
+                const int b = __ffsll((long long)a) - 1;
+                a &= a - 1;
+                live += __popcll(v & ~H.obj[i * 64 + b]);
+            }
+        }
+        if (na) atomicAdd(out + 1 + 3 * t, na);
+        if (nact) atomicAdd(out + 2 + 3 * t, nact);
+        if (live) atomicAdd(out + 3 + 3 * t, live);
+    }
+}
+
+int dsr__scan_grid(const dsr_heap* h, int type) {
+    const uint64_t warps = (h->dev.alloc_bm[type].nwords[0] + 31) / 32;
+    uint64_t ctas = (warps + 7) / 8;
+    const uint64_t cap = (uint64_t)h->sm_count * 8;
+    if (ctas > cap) ctas = cap;
+    return ctas < 1 ? 1 : (int)ctas;
+}
+
+void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s) {
+    k_scan<<<dsr__scan_grid(h, type), 256, 0, s>>>(h->dev, type);
+}
+
+int dsr__persistent_grid(const dsr_heap* h, const void* kernel, int threads) {
+    int per_sm = h->tune.ctas_per_sm;
+    if (per_sm <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
+    return per_sm * h->sm_count;
+}
+
+// ---------------------------------------------------------------------------
+// create / destroy / reset / layout
+// ---------------------------------------------------------------------------
+static void build_dev_view(dsr_heap* h) {
+    const dsr_layout& L = h->layout;
+    dsr_dev_heap& D = h->dev;
+    memset(&D, 0, sizeof D);
+    uint8_t* a = h->arena;
+    D.data = a + L.off_data;
+    D.obj = reinterpret_cast<dsr_u64*>(a + L.off_obj);
+    D.btype = a + L.off_type;
+    D.err = reinterpret_cast<uint32_t*>(a + DSR_HDR_ERR);
+    D.inject = reinterpret_cast<uint32_t*>(a + DSR_HDR_INJECT);
+    D.R_count = reinterpret_cast<uint32_t*>(a + DSR_HDR_RCOUNT);
+    D.R_done = reinterpret_cast<uint32_t*>(a + DSR_HDR_RDONE);
+    D.ctr = reinterpret_cast<dsr_u64*>(a + DSR_HDR_CTR);
+    D.slow = reinterpret_cast<uint32_t*>(a + DSR_HDR_SLOW);
+    D.slow_max = (uint32_t)(h->sm_count > 0 ? h->sm_count : 1);
+    D.R_mask = reinterpret_cast<dsr_u64*>(a + off_rmask(L));
+    D.R_bid = reinterpret_cast<uint32_t*>(a + off_rbid(L));
+    D.M = L.n_blocks;
+    D.block_bytes = L.block_bytes;
+    D.n_types = (int32_t)L.n_types;
+    auto fill = [&](dsr_hbm& b, uint64_t off) {
+        b.n_levels = (int32_t)L.n_levels;
+        uint64_t o = off;
+        for (uint32_t l = 0; l < L.n_levels; ++l) {
+            b.lvl[l] = reinterpret_cast<dsr_u64*>(a + o);
+            b.nwords[l] = (uint32_t)L.words_per_level[l];
+            o += L.words_per_level[l] * 8;
+        }
+    };
+    fill(D.free_bm, L.off_free_bm);
+    for (uint32_t t = 0; t < L.n_types; ++t) {
+        fill(D.alloc_bm[t], L.off_alloc_bm + t * L.bitmap_words * 8);
+        fill(D.active_bm[t], L.off_active_bm + t * L.bitmap_words * 8);
+        D.cap[t] = L.capacity[t];
+        D.valid[t] = L.capacity[t] >= 64 ? ~0ull : ((1ull << L.capacity[t]) - 1);
+        D.n_fields[t] = L.n_fields[t];
+        for (uint32_t f = 0; f < L.n_fields[t]; ++f) {
+            D.foff[t][f] = L.field_offset[t][f];
+            D.fsize[t][f] = (uint8_t)L.field_bytes[t][f];
+        }
+    }
+    h->stats_dev = reinterpret_cast<dsr_u64*>(a + DSR_HDR_STATS);
+}
+
+static int reset_impl(dsr_heap* h, cudaStream_t s) {
+    const dsr_layout& L = h->layout;
+    cudaError_t e;
+    e = cudaMemsetAsync(h->arena, 0, DSR_HEADER_BYTES, s);
+    if (!e) e = cudaMemsetAsync(h->arena + L.off_free_bm, 0, (1 + 2 * L.n_types) * L.bitmap_words * 8, s);
+    if (!e) e = cudaMemsetAsync(h->arena + L.off_obj, 0, L.n_blocks * 8, s);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_heap_reset");
+        return DSR_E_CUDA;
+    }
+    uint64_t ctas = (L.n_blocks + 255) / 256;
+    if (ctas > (uint64_t)h->sm_count * 16) ctas = (uint64_t)h->sm_count * 16;
+    if (ctas < 1) ctas = 1;
+    k_heap_mark_free<<<(unsigned)ctas, 256, 0, s>>>(h->dev, L.n_blocks);
+    return dsr__check_launch("k_heap_mark_free");
+}
+
+extern "C" int dsr_heap_create(const dsr_type_desc* types, int n_types, void* arena_dev, size_t heap_bytes,
+                               const dsr_tuning* tune, void* stream, dsr_heap** out) {
+    if (!out || !arena_dev || (reinterpret_cast<uintptr_t>(arena_dev) & 255)) return DSR_E_INVALID;
+    *out = nullptr;
+    dsr_tuning tn = resolve_tuning(tune);
+    if (tn.threads < 64 || tn.threads > 1024 || tn.threads % 64) return DSR_E_INVALID;
+    dsr_layout L;
+    int rc = geometry(types, n_types, tn, &L);
+    if (rc) return rc;
+    // Largest M that fits: estimate, then step down.
+    const uint64_t per_block = L.block_bytes + 8 + 8 + 4 + 1 + (1 + 2 * (uint64_t)n_types) * 2;
+    if (heap_bytes < DSR_HEADER_BYTES + 4096 + per_block) return DSR_E_OOM;
+    uint64_t M = (heap_bytes - DSR_HEADER_BYTES - 4096) / per_block;
+    if (M > 0xFFFFFFFFull) M = 0xFFFFFFFFull;
+    while (M > 0 && place(&L, M) > heap_bytes) M -= 1 + M / 4096;
+    if (M == 0) return DSR_E_OOM;
+    while (place(&L, M + 1) <= heap_bytes && M < 0xFFFFFFFFull) ++M;
+    place(&L, M);
+
+    dsr_heap* h = new (std::nothrow) dsr_heap;
+    if (!h) return DSR_E_OOM;
+    h->layout = L;
+    h->arena = static_cast<uint8_t*>(arena_dev);
+    h->heap_bytes = heap_bytes;
+    h->tune = tn;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (!e) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_heap_create");
+        delete h;
+        return DSR_E_CUDA;
+    }
+    build_dev_view(h);
+    rc = reset_impl(h, dsr__stream(stream));
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return DSR_OK;
+}
+
+extern "C" int dsr_heap_destroy(dsr_heap* h) {
+    delete h;
+    return DSR_OK;
+}
+
+extern "C" int dsr_heap_reset(dsr_heap* h, void* stream) {
+    if (!h) return DSR_E_INVALID;
+    return reset_impl(h, dsr__stream(stream));
+}
+
+extern "C" int dsr_heap_layout(const dsr_heap* h, dsr_layout* out) {
+    if (!h || !out) return DSR_E_INVALID;
+    *out = h->layout;
+    return DSR_OK;
+}
+
+extern "C" size_t dsr_dev_heap_size(void) { return sizeof(dsr_dev_heap); }
+
+extern "C" int dsr_heap_device_view(const dsr_heap* h, void* out, size_t out_bytes) {
+    if (!h || !out || out_bytes < sizeof(dsr_dev_heap)) return DSR_E_INVALID;
+    memcpy(out, &h->dev, sizeof(dsr_dev_heap));
+    return DSR_OK;
+}
+
+extern "C" int dsr_heap_stats(dsr_heap* h, void* stream, dsr_stats* out) {
+    if (!h || !out) return DSR_E_INVALID;
+    cudaStream_t s = dsr__stream(stream);
+    const int n = 1 + 3 * DSR_MAX_TYPES;
+    cudaError_t e = cudaMemsetAsync(h->stats_dev, 0, n * sizeof(dsr_u64), s);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_heap_stats");
+        return DSR_E_CUDA;
+    }
+    uint64_t ctas = (h->layout.words_per_level[0] + 255) / 256;
+    if (ctas > (uint64_t)h->sm_count * 8) ctas = (uint64_t)h->sm_count * 8;
+    if (ctas < 1) ctas = 1;
+    k_stats<<<(unsigned)ctas, 256, 0, s>>>(h->dev, h->stats_dev);
+    int rc = dsr__check_launch("k_stats");
+    if (rc) return rc;
+    dsr_u64 buf[1 + 3 * DSR_MAX_TYPES];
+    uint32_t err = 0;
+    e = cudaMemcpyAsync(buf, h->stats_dev, sizeof buf, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(&err, h->dev.err, sizeof err, cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_heap_stats");
+        return DSR_E_CUDA;
+    }
+    memset(out, 0, sizeof *out);
+    out->n_blocks = h->layout.n_blocks;
+    out->free_blocks = buf[0];
+    out->n_types = h->layout.n_types;
+    out->error_flags = err;
+    for (uint32_t t = 0; t < h->layout.n_types; ++t) {
+        out->capacity[t] = h->layout.capacity[t];
+        out->allocated_blocks[t] = buf[1 + 3 * t];
+        out->active_blocks[t] = buf[2 + 3 * t];
+        out->live_objects[t] = buf[3 + 3 * t];
+    }
+    return DSR_OK;
+}
+
+extern "C" int dsr_heap_counters(dsr_heap* h, void* stream, uint64_t* out) {
+    if (!h || !out) return DSR_E_INVALID;
+    dsr_u64 rows[DSR_CTR_SLOTS][4];
+    cudaError_t e = cudaMemcpyAsync(rows, h->dev.ctr, sizeof rows, cudaMemcpyDeviceToHost, dsr__stream(stream));
+    if (!e) e = cudaStreamSynchronize(dsr__stream(stream));
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_heap_counters");
+        return DSR_E_CUDA;
+    }
+    for (int k = 0; k < 4; ++k) {
+        out[k] = 0;
+        for (unsigned r = 0; r < DSR_CTR_SLOTS; ++r) out[k] += rows[r][k];
+    }
+    return DSR_OK;
+}
+
+extern "C" int dsr_heap_inject_oom(dsr_heap* h, uint32_t n, void* stream) {
+    if (!h) return DSR_E_INVALID;
+    cudaError_t e = cudaMemcpyAsync(h->dev.inject, &n, sizeof n, cudaMemcpyHostToDevice, dsr__stream(stream));
+    if (!e) e = cudaStreamSynchronize(dsr__stream(stream));  // n lives on this stack frame
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_heap_inject_oom");
+        return DSR_E_CUDA;
+    }
+    return DSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// generic methods
+// ---------------------------------------------------------------------------
+struct MCount {
+    typedef dsr_count_args Args;
+    static __device__ void run(const dsr_dev_heap&, int, const Args& a, dsr_ref) {
+        // one atomic per warp
+        const unsigned act = __activemask();
+        if (dsr_lane() == (unsigned)(__ffs(act) - 1)) atomicAdd(a.counter_dev, (dsr_u64)__popc(act));
+    }
+};
+
+struct MStreamAdd {
+    struct Args { int dummy; };
+    static __device__ void run(const dsr_dev_heap& H, int T, const Args&, dsr_ref r) {
+        const int nf = (int)H.n_fields[T];
+        for (int f = 0; f + 1 < nf; ++f) {
+            int32_t* p = dsr_field<int32_t>(H, T, r, f);
+            *p += *dsr_field<int32_t>(H, T, r, f + 1);
+        }
+        *dsr_field<int32_t>(H, T, r, nf - 1) += 1;
+    }
+};
+
+struct MDeleteIf {
+    typedef dsr_delete_if_args Args;
+    static __device__ void run(const dsr_dev_heap& H, int T, const Args& a, dsr_ref r) {
+        const int32_t v = *dsr_field<int32_t>(H, T, r, 0);
+        int32_t m = v % a.modulus;
+        if (m < 0) m += a.modulus;
+        if (m == a.residue) dsr_delete(H, r);
+    }
+};
+
+struct MClone {
+    typedef dsr_clone_args Args;
+    static __device__ void run(const dsr_dev_heap& H, int T, const Args& a, dsr_ref r) {
+        const dsr_ref n = dsr_new(H, a.dst_type);
+        if (n == DSR_NULL) return;
+        const int nf = (int)(H.n_fields[T] < H.n_fields[a.dst_type] ? H.n_fields[T] : H.n_fields[a.dst_type]);
+        for (int f = 0; f < nf; ++f) *dsr_field<int32_t>(H, a.dst_type, n, f) = *dsr_field<int32_t>(H, T, r, f) + a.add;
+        for (int f = nf; f < (int)H.n_fields[a.dst_type]; ++f) *dsr_field<int32_t>(H, a.dst_type, n, f) = 0;
+    }
+};
+
+struct DumpArgs {
+    uint32_t* out;
+    dsr_u64* count;
+    dsr_u64 cap;
+    int row;
+};
+struct MDump {
+    typedef DumpArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int T, const Args& a, dsr_ref r) {
+        const dsr_u64 k = atomicAdd(a.count, 1ull);
+        if (k >= a.cap) {
+            atomicOr(H.err, DSR_ERR_CAPACITY);
+            return;
+        }
+        uint32_t* row = a.out + k * (dsr_u64)a.row;
+        int w = 0;
+        for (uint32_t f = 0; f < H.n_fields[T]; ++f) {
+            if (H.fsize[T][f] == 4) {
+                row[w++] = *dsr_field<uint32_t>(H, T, r, (int)f);
+            } else {
+                const dsr_u64 x = *dsr_field<dsr_u64>(H, T, r, (int)f);
+                row[w++] = (uint32_t)x;
+                row[w++] = (uint32_t)(x >> 32);
+            }
+        }
+        row[w++] = (uint32_t)r;
+        row[w++] = (uint32_t)(r >> 32);
+    }
+};
+
+struct HashArgs {
+    dsr_u64* out;
+};
+struct MHash {
+    typedef HashArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int T, const Args& a, dsr_ref r) {
+        dsr_u64 h = dsr_mix64((dsr_u64)T + DSR_GAMMA);
+        for (uint32_t f = 0; f < H.n_fields[T]; ++f) {
+            if (H.fsize[T][f] == 4) {
+                h = dsr_mix64((h ^ (dsr_u64)*dsr_field<uint32_t>(H, T, r, (int)f)) + DSR_GAMMA);
+            } else {
+                const dsr_u64 x = *dsr_field<dsr_u64>(H, T, r, (int)f);
+                h = dsr_mix64((h ^ (dsr_u64)(uint32_t)x) + DSR_GAMMA);
+                h = dsr_mix64((h ^ (x >> 32)) + DSR_GAMMA);
+            }
+        }
+        // Warp sum modulo 2^64 in three 22-bit chunks (each chunk sum of 32
+        // lanes fits 32 bits), one atomic per warp.
+        const unsigned act = __activemask();
+        const dsr_u64 s0 = __reduce_add_sync(act, (unsigned)(h & 0x3FFFFFu));
+        const dsr_u64 s1 = __reduce_add_sync(act, (unsigned)((h >> 22) & 0x3FFFFFu));
+        const dsr_u64 s2 = __reduce_add_sync(act, (unsigned)(h >> 44));
+        h = s0 + (s1 << 22) + (s2 << 44);
+        if (dsr_lane() == (unsigned)(__ffs(act) - 1)) atomicAdd(a.out, h);
+    }
+};
+
+extern "C" int dsr_row_words(const dsr_heap* h, int type) {
+    if (!h || type < 0 || type >= (int)h->layout.n_types) return -1;
+    int w = 2;
+    for (uint32_t f = 0; f < h->layout.n_fields[type]; ++f) w += (int)h->layout.field_bytes[type][f] / 4;
+    return w;
+}
+
+extern "C" int dsr_heap_dump(dsr_heap* h, int type, void* out_dev, uint64_t cap, void* count_dev, void* stream) {
+    if (!h || !out_dev || !count_dev || type < 0 || type >= (int)h->layout.n_types) return DSR_E_INVALID;
+    cudaStream_t s = dsr__stream(stream);
+    cudaError_t e = cudaMemsetAsync(count_dev, 0, sizeof(dsr_u64), s);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_heap_dump");
+        return DSR_E_CUDA;
+    }
+    DumpArgs a{static_cast<uint32_t*>(out_dev), static_cast<dsr_u64*>(count_dev), cap, dsr_row_words(h, type)};
+    return dsr__doall<MDump>(h, type, a, s);
+}
+
+extern "C" int dsr_heap_hash(dsr_heap* h, int type, void* hash_dev, void* stream) {
+    if (!h || !hash_dev || type < 0 || type >= (int)h->layout.n_types) return DSR_E_INVALID;
+    HashArgs a{static_cast<dsr_u64*>(hash_dev)};
+    return dsr__doall<MHash>(h, type, a, dsr__stream(stream));
+}
+
+template <class M>
+static int typed_args(const void* args, size_t bytes, typename M::Args* out) {
+    if (bytes != sizeof(typename M::Args) || !args) return DSR_E_INVALID;
+    memcpy(out, args, sizeof *out);
+    return DSR_OK;
+}
+
+static int dispatch(dsr_heap* h, int type, int method, const void* args, size_t args_bytes, cudaStream_t s,
+                    bool with_scan) {
+    if (!h || type < 0 || type >= (int)h->layout.n_types) return DSR_E_INVALID;
+    switch (method) {
+        case DSR_METHOD_COUNT: {
+            MCount::Args a;
+            if (typed_args<MCount>(args, args_bytes, &a) || !a.counter_dev) return DSR_E_INVALID;
+            return dsr__doall<MCount>(h, type, a, s, with_scan);
+        }
+        case DSR_METHOD_STREAM_ADD: {
+            for (uint32_t f = 0; f < h->layout.n_fields[type]; ++f)
+                if (h->layout.field_bytes[type][f] != 4) return DSR_E_INVALID;
+            return dsr__doall<MStreamAdd>(h, type, MStreamAdd::Args{0}, s, with_scan);
+        }
+        case DSR_METHOD_DELETE_IF: {
+            MDeleteIf::Args a;
+            if (typed_args<MDeleteIf>(args, args_bytes, &a) || a.modulus <= 0) return DSR_E_INVALID;
+            if (h->layout.field_bytes[type][0] != 4) return DSR_E_INVALID;
+            return dsr__doall<MDeleteIf>(h, type, a, s, with_scan);
+        }
+        case DSR_METHOD_CLONE: {
+            MClone::Args a;
+            if (typed_args<MClone>(args, args_bytes, &a)) return DSR_E_INVALID;
+            if (a.dst_type < 0 || a.dst_type >= (int)h->layout.n_types || a.dst_type == type) return DSR_E_INVALID;
+            for (uint32_t f = 0; f < h->layout.n_fields[type]; ++f)
+                if (h->layout.field_bytes[type][f] != 4) return DSR_E_INVALID;
+            for (uint32_t f = 0; f < h->layout.n_fields[a.dst_type]; ++f)
+                if (h->layout.field_bytes[a.dst_type][f] != 4) return DSR_E_INVALID;
+            return dsr__doall<MClone>(h, type, a, s, with_scan);
+        }
+        default:
+            break;
+    }
+    if (method >= 100 && method < 200) return dsr__gol_method(h, type, method, args, args_bytes, s, with_scan);
+    if (method >= 200 && method < 300) return dsr__wator_method(h, type, method, args, args_bytes, s, with_scan);
+    if (method >= 300 && method < 400) return dsr__nbody_method(h, type, method, args, args_bytes, s, with_scan);
+    return DSR_E_INVALID;
+}
+
+extern "C" int dsr_parallel_do(dsr_heap* h, int type, int method, const void* args, size_t args_bytes,
+                               void* stream) {
+    return dispatch(h, type, method, args, args_bytes, dsr__stream(stream), true);
+}
+
+extern "C" int dsr_doall_scan(dsr_heap* h, int type, void* stream) {
+    if (!h || type < 0 || type >= (int)h->layout.n_types) return DSR_E_INVALID;
+    dsr__launch_scan(h, type, dsr__stream(stream));
+    return dsr__check_launch("k_scan");
+}
+
+extern "C" int dsr_doall_run(dsr_heap* h, int type, int method, const void* args, size_t args_bytes, void* stream) {
+    return dispatch(h, type, method, args, args_bytes, dsr__stream(stream), false);
+}
+
+// ---------------------------------------------------------------------------
+// allocation microbenchmark kernels
+// ---------------------------------------------------------------------------
+__global__ void k_bench_alloc(const __grid_constant__ dsr_dev_heap H, dsr_u64 n, int n_types, dsr_u64 seed,
+                              dsr_ref* refs) {
+    const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
+    for (dsr_u64 i = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int T = (int)(dsr_mix64(seed ^ (i * DSR_GAMMA)) % (dsr_u64)n_types);
+        const dsr_ref r = dsr_new(H, T);
+        if (r != DSR_NULL) *dsr_field<int32_t>(H, T, r, 0) = (int32_t)i;
+        refs[i] = r;
+    }
+}
+
+__global__ void k_bench_free(const __grid_constant__ dsr_dev_heap H, dsr_u64 n, const dsr_ref* refs) {
+    const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
+    for (dsr_u64 i = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dsr_delete(H, refs[i]);
+}
+
+extern "C" int dsr_bench_alloc(dsr_heap* h, uint64_t n, int n_types_used, uint64_t seed, void* refs_dev,
+                               void* stream) {
+    if (!h || !refs_dev || n_types_used < 1 || n_types_used > (int)h->layout.n_types || n == 0) return DSR_E_INVALID;
+    for (int t = 0; t < n_types_used; ++t)
+        if (h->layout.field_bytes[t][0] != 4) return DSR_E_INVALID;
+    uint64_t ctas = (n + 255) / 256;
+    if (ctas > (uint64_t)h->sm_count * 8) ctas = (uint64_t)h->sm_count * 8;
+    k_bench_alloc<<<(unsigned)ctas, 256, 0, dsr__stream(stream)>>>(h->dev, n, n_types_used, seed,
+                                                                      static_cast<dsr_ref*>(refs_dev));
+    return dsr__check_launch("k_bench_alloc");
+}
+
+extern "C" int dsr_bench_free(dsr_heap* h, uint64_t n, const void* refs_dev, void* stream) {
+    if (!h || !refs_dev || n == 0) return DSR_E_INVALID;
+    uint64_t ctas = (n + 255) / 256;
+    if (ctas > (uint64_t)h->sm_count * 8) ctas = (uint64_t)h->sm_count * 8;
+    k_bench_free<<<(unsigned)ctas, 256, 0, dsr__stream(stream)>>>(h->dev, n, static_cast<const dsr_ref*>(refs_dev));
+    return dsr__check_launch("k_bench_free");
+}

@@ -1,0 +1,82 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "dsr.h"
+#include "dsr_device.cuh"
+
+struct dsr_heap {
+    dsr_dev_heap dev;    // device view, passed by value to every kernel
+    dsr_layout layout;
+    uint8_t* arena;
+    size_t heap_bytes;
+    dsr_tuning tune;
+    int device;
+    int sm_count;
+    dsr_u64* stats_dev;  // scratch in the arena header
+};
+
+// Arena header (first DSR_HEADER_BYTES bytes of the arena).
+#define DSR_HEADER_BYTES 16384u
+#define DSR_HDR_ERR 0u
+#define DSR_HDR_INJECT 4u
+#define DSR_HDR_RCOUNT 8u
+#define DSR_HDR_RDONE 12u
+#define DSR_HDR_STATS 256u  // dsr_u64[1 + 3 * DSR_MAX_TYPES]
+#define DSR_HDR_SLOW 192u   // uint32[DSR_MAX_TYPES] slow paths in flight
+#define DSR_HDR_CTR 4096u   // dsr_u64[DSR_CTR_SLOTS][4] event counters
+
+void dsr__set_cuda_error(cudaError_t e, const char* where);
+int dsr__check_launch(const char* where);
+
+inline cudaStream_t dsr__stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Persistent grid for a method kernel: CTAs that fit on the GPU at once,
+// capped by the most work a do-all over this heap can list.
+int dsr__persistent_grid(const dsr_heap* h, const void* kernel, int threads);
+int dsr__scan_grid(const dsr_heap* h, int type);
+void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s);
+
+// Run a do-all: scan + compaction of allocated[type] into R, then the method
+// kernel over the listed blocks.
+template <class M>
+int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t s, bool with_scan = true) {
+    if (type < 0 || type >= h->dev.n_types) return DSR_E_INVALID;
+    if (with_scan) dsr__launch_scan(h, type, s);
+    static int grid_cache[17] = {0};
+    const int threads = h->tune.threads;
+    int& grid = grid_cache[threads / 64];
+    if (grid == 0 || h->tune.ctas_per_sm > 0) grid = dsr__persistent_grid(h, (const void*)dsr_doall_kernel<M>, threads);
+    int g = grid;
+    const dsr_u64 cap_grid = (h->dev.M * 64 + threads - 1) / threads;
+    if ((dsr_u64)g > cap_grid) g = (int)cap_grid;
+    if (g < 1) g = 1;
+    dsr_doall_kernel<M><<<g, threads, 0, s>>>(h->dev, type, args);
+    return dsr__check_launch("dsr_doall_kernel");
+}
+
+// Application method dispatch (defined in the application files).
+int dsr__gol_method(dsr_heap* h, int type, int method, const void* args, size_t bytes, cudaStream_t s,
+                    bool with_scan);
+int dsr__wator_method(dsr_heap* h, int type, int method, const void* args, size_t bytes, cudaStream_t s,
+                      bool with_scan);
+int dsr__nbody_method(dsr_heap* h, int type, int method, const void* args, size_t bytes, cudaStream_t s,
+                      bool with_scan);
+
+// SplitMix64 finalizer and the object-state hash (same definition as the
+// dsr_heap_hash documentation).
+__device__ __forceinline__ dsr_u64 dsr_mix64(dsr_u64 z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+#define DSR_GAMMA 0x9E3779B97F4A7C15ull
+__device__ __forceinline__ dsr_u64 dsr_splitmix_at(dsr_u64 s, dsr_u64 n) { return dsr_mix64(s + (n + 1) * DSR_GAMMA); }
+// Counter-based draw keyed on (seed, stream, step, cell).
+__device__ __forceinline__ dsr_u64 dsr_rand(dsr_u64 seed, dsr_u64 stream, dsr_u64 step, dsr_u64 cell) {
+    return dsr_splitmix_at(dsr_splitmix_at(dsr_splitmix_at(seed, stream), step), cell);
+}

@@ -1,0 +1,109 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every declared entry point;
+host-only layout planning follows the block geometry of Section 2."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1809_07444_gb300 import build_ext, _lib
+
+    build_ext.build()
+    return _lib.load()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(dsr_[a-z0-9_]+)\s*\(", text, re.M):
+            if not m.group(0).lstrip().startswith(("typedef", "#")):
+                names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) > 20
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_declarations():
+    from paper_1809_07444_gb300 import _lib
+
+    assert set(_lib.SIGNATURES) <= _declared()
+
+
+def _plan(lib, types, n_blocks, cap_min=0):
+    from paper_1809_07444_gb300 import _lib as L
+    from paper_1809_07444_gb300.heap import _descs
+
+    descs, _keep = _descs(types)
+    lay = L.Layout()
+    tun = L.Tuning(cap_min, 0, 0)
+    rc = lib.dsr_heap_plan(descs, len(types), n_blocks, C.byref(tun), C.byref(lay))
+    return rc, lay
+
+
+def test_capacity_rule(lib):
+    # smallest type (8 B) gets 64 slots and fixes the block size; a 12 B
+    # type gets floor(64*8/12) = 42, a 32 B type 16, a 16 B type 32
+    rc, lay = _plan(lib, [[4, 4, 4], [4, 4], [4] * 8, [8, 8]], 1000)
+    assert rc == 0
+    assert [lay.capacity[t] for t in range(4)] == [42, 64, 16, 32]
+    assert lay.block_bytes == 512
+    # every SOA array starts 8-byte aligned and fits the block
+    for t in range(4):
+        offs = [lay.field_offset[t][f] for f in range(lay.n_fields[t])]
+        assert all(o % 8 == 0 for o in offs)
+        last = offs[-1] + lay.capacity[t] * lay.field_bytes[t][lay.n_fields[t] - 1]
+        assert last <= lay.block_bytes
+
+
+def test_cap_min_32_halves_blocks(lib):
+    rc, lay = _plan(lib, [[4, 4, 4], [4, 4, 4, 4]], 1000, cap_min=32)
+    assert rc == 0
+    assert [lay.capacity[0], lay.capacity[1]] == [32, 24]
+    assert lay.block_bytes == 384
+
+
+def test_levels_and_offsets(lib):
+    for M, levels in [(64, 1), (65, 2), (4096, 2), (4097, 3), (64 ** 3 + 1, 4)]:
+        rc, lay = _plan(lib, [[4, 4]], M)
+        assert rc == 0 and lay.n_levels == levels
+        n, words = M, []
+        while True:
+            words.append(-(-n // 64))
+            if n <= 64:
+                break
+            n = -(-n // 64)
+        assert [lay.words_per_level[l] for l in range(levels)] == words
+        assert lay.off_data % 1024 == 0 and lay.off_obj % 256 == 0
+        assert lay.arena_bytes_used >= lay.off_data + M * lay.block_bytes
+
+
+def test_invalid_descriptors_rejected(lib):
+    assert _plan(lib, [[4, 3]], 10)[0] == 1
+    assert _plan(lib, [[4] * 17], 10)[0] == 1
+    assert _plan(lib, [[4]] * 9, 10)[0] == 1
+    assert _plan(lib, [[4]], 0)[0] == 1
+    assert _plan(lib, [[4]], 10, cap_min=48)[0] == 1
+
+
+def test_product_path_fails_loudly_without_library(tmp_path):
+    from paper_1809_07444_gb300 import _lib
+
+    with pytest.raises(RuntimeError):
+        _lib._lib = None
+        try:
+            _lib.load(str(tmp_path / "missing.so"))
+        finally:
+            _lib._lib = None

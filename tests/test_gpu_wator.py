@@ -1,0 +1,61 @@
+"""GPU parity of wa-tor with the oracle (bit-exact Fish and Shark multisets, state hash every step)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1809_07444_gb300 import workloads as WL
+from paper_1809_07444_gb300.apps import Wator
+
+from helpers import check_invariants
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_pair(W, H, kind0, seed, steps, full_every=1, invariants_every=None):
+    gpu, ref = Wator(W, H, kind0, seed), O.Wator(W, H, kind0, seed)
+    assert gpu.hash() == ref.hash()
+    for t in range(1, steps + 1):
+        gpu.step(1)
+        ref.step(1)
+        hg, hr = gpu.hash(), ref.hash()
+        assert hg == hr, "step %d: hash %s vs oracle %s" % (t, hg, hr)
+        if t % full_every == 0 or t == steps:
+            fg, sg = gpu.dump()
+            fr, sr = ref.dump()
+            assert np.array_equal(fg, fr), "fish differ at step %d" % t
+            assert np.array_equal(sg, sr), "sharks differ at step %d" % t
+            assert np.array_equal(gpu.grid(), ref.grid())
+        if invariants_every and t % invariants_every == 0:
+            check_invariants(gpu.heap, list(ref.counts()))
+    st = gpu.heap.stats()
+    assert st["error_flags"] == 0, st
+    check_invariants(gpu.heap, list(ref.counts()))
+    return gpu, ref
+
+
+def test_wator_64x64_bit_exact():
+    _run_pair(64, 64, WL.wator_initial(64, 64, 1), 1, 150, full_every=10, invariants_every=25)
+
+
+@pytest.mark.parametrize("W,H,seed,steps", [(3, 3, 2, 30), (17, 9, 3, 80), (257, 129, 4, 60)])
+def test_wator_ragged_grids(W, H, seed, steps):
+    _run_pair(W, H, WL.wator_initial(W, H, seed), seed, steps, full_every=10)
+
+
+def test_wator_extinction_and_degenerate_starts():
+    # no agents; only sharks (they all starve); only fish (fill the grid)
+    _run_pair(32, 32, np.zeros((32, 32), np.uint8), 1, 5)
+    k = np.zeros((32, 32), np.uint8)
+    k[::3, ::2] = 2
+    gpu, ref = _run_pair(32, 32, k, 2, 8)
+    assert ref.counts() == (0, 0)
+    k = np.zeros((32, 32), np.uint8)
+    k[5, 5] = 1
+    _run_pair(32, 32, k, 3, 40, full_every=5)
+
+
+def test_wator_2048_full_size_hash_parity():
+    # the 2048 x 2048 workload (30% fish, 3% sharks): state hash every step
+    # for the first 40 steps, full multisets at the end
+    W = H = 2048
+    _run_pair(W, H, WL.wator_initial(W, H, 1), 1, 40, full_every=20)
