@@ -89,6 +89,30 @@ int dsr_wator_step(dsr_wator* w, int n_steps, void* stream);
 int dsr_wator_kinds(dsr_wator* w, void* kind_out_dev, void* stream);
 int dsr_wator_destroy(dsr_wator* w);
 
+/* ---- n-body with merging collisions ------------------------------------
+ * FP32. Types: 0 Body {id (int32), x, y, z, vx, vy, vz, m (float)}. One step:
+ * a_i = G sum_j m_j d_ij / (|d_ij|^2 + eps^2)^(3/2); v += a dt; x += v dt;
+ * then, on the new positions, the partner of i is the body with the lowest
+ * id j != i closer than r_merge; mutual partners merge (the lower id keeps
+ * the summed mass and the mass-weighted mean position and velocity, the
+ * higher id is deleted). Workspace (dsr_nbody_workspace_bytes): dense
+ * per-slot arrays for all M * 64 slots of the heap plus a merge log of
+ * log_cap entries. */
+typedef struct {
+    float G, eps, dt, r_merge;
+} dsr_nbody_params;
+typedef struct dsr_nbody dsr_nbody;
+int dsr_nbody_types(dsr_type_desc* out /* 1 entry */);
+int dsr_nbody_workspace_bytes(const dsr_heap* heap, uint64_t log_cap, size_t* out);
+/* rows_dev: device float[n_bodies][7] = (x, y, z, vx, vy, vz, m); body i gets id i. */
+int dsr_nbody_create(dsr_heap* heap, const dsr_nbody_params* p, const void* rows_dev, int n_bodies,
+                     void* workspace_dev, uint64_t log_cap, void* stream, dsr_nbody** out);
+int dsr_nbody_step(dsr_nbody* nb, int n_steps, void* stream);
+/* Device pointers to the merge log (int32[log_cap][3]: step, survivor id,
+ * absorbed id, in arbitrary order within a step) and its uint64 count. */
+int dsr_nbody_merge_log(dsr_nbody* nb, void** log_dev, void** count_dev);
+int dsr_nbody_destroy(dsr_nbody* nb);
+
 #ifdef __cplusplus
 }
 #endif

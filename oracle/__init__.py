@@ -76,6 +76,7 @@ def lib():
         L.orc_wator_dump.argtypes = [vp, vp, i64, vp, i64]
         L.orc_wator_grid.argtypes = [vp, vp]
 
+        L.orc_set_threads.argtypes = [i32]
         L.orc_nbody_create.restype = vp
         L.orc_nbody_create.argtypes = [vp, vp, i64]
         L.orc_nbody_destroy.argtypes = [vp]
@@ -277,6 +278,11 @@ class Wator:
         g = np.zeros(self.W * self.H, dtype=np.uint8)
         lib().orc_wator_grid(self._h, _ptr(g))
         return g.reshape(self.H, self.W)
+
+
+def set_threads(n):
+    """Threads for the per-body rows of the n-body oracle (results do not depend on it)."""
+    lib().orc_set_threads(int(n))
 
 
 class _NBodyParams(C.Structure):

@@ -20,7 +20,7 @@ def build(force: bool = False) -> str:
         if all(os.path.getmtime(s) <= lib_m for s in srcs):
             return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-o", tmp] + [os.path.join(HERE, s) for s in SOURCES]
+    cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-pthread", "-o", tmp] + [os.path.join(HERE, s) for s in SOURCES]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

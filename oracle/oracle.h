@@ -107,7 +107,10 @@ int        orc_wator_dump(const orc_wator* w, int32_t* fish_out, int64_t fish_ca
 /* kind_out[W*H] as kind0. */
 void       orc_wator_grid(const orc_wator* w, uint8_t* kind_out);
 
-/* ---- n-body with merging collisions (FP64) ----------------------------- */
+/* ---- n-body with merging collisions (FP64) -----------------------------
+ * orc_set_threads splits the independent per-body rows of a step across
+ * threads; results are identical for every thread count. */
+void       orc_set_threads(int n);
 typedef struct {
     double G, eps, dt, r_merge;
 } orc_nbody_params;

@@ -16,7 +16,9 @@
 // live flag).
 #include "oracle.h"
 
+#include <algorithm>
 #include <cmath>
+#include <thread>
 #include <vector>
 
 struct orc_nbody {
@@ -41,6 +43,28 @@ extern "C" orc_nbody* orc_nbody_create(const orc_nbody_params* p, const double* 
 
 extern "C" void orc_nbody_destroy(orc_nbody* b) { delete b; }
 
+// Rows i of the force and partner loops are independent; they may be split
+// across threads (orc_set_threads). Each row is computed the same way, in the
+// same j order, whatever the thread count, so results do not depend on it.
+static int g_threads = 1;
+
+extern "C" void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+
+template <class F>
+static void for_rows(int64_t n, F fn) {
+    if (g_threads <= 1 || n < 256) {
+        fn(0, n, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    const int64_t chunk = (n + g_threads - 1) / g_threads;
+    for (int t = 0; t < g_threads; ++t) {
+        const int64_t lo = t * chunk, hi = std::min<int64_t>(n, lo + chunk);
+        if (lo < hi) th.emplace_back(fn, lo, hi, t);
+    }
+    for (auto& x : th) x.join();
+}
+
 extern "C" int64_t orc_nbody_step(orc_nbody* b, int n_steps, int64_t* merges_out, int64_t merges_cap,
                                   double margin, int64_t* marginal_out) {
     const auto& P = b->p;
@@ -48,20 +72,23 @@ extern "C" int64_t orc_nbody_step(orc_nbody* b, int n_steps, int64_t* merges_out
     int64_t n_merges = 0, n_marginal = 0;
     std::vector<double> ax(n), ay(n), az(n);
     std::vector<int64_t> partner(n);
+    std::vector<int64_t> marg(g_threads > 1 ? g_threads : 1);
     for (int s = 0; s < n_steps; ++s) {
         // force
-        for (int64_t i = 0; i < n; ++i) {
-            if (!b->live[i]) continue;
-            double sx = 0, sy = 0, sz = 0;
-            for (int64_t j = 0; j < n; ++j) {
-                if (j == i || !b->live[j]) continue;
-                double dx = b->x[j] - b->x[i], dy = b->y[j] - b->y[i], dz = b->z[j] - b->z[i];
-                double r2 = dx * dx + dy * dy + dz * dz + P.eps * P.eps;
-                double w = b->m[j] / (r2 * std::sqrt(r2));
-                sx += w * dx; sy += w * dy; sz += w * dz;
+        for_rows(n, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t i = lo; i < hi; ++i) {
+                if (!b->live[i]) continue;
+                double sx = 0, sy = 0, sz = 0;
+                for (int64_t j = 0; j < n; ++j) {
+                    if (j == i || !b->live[j]) continue;
+                    double dx = b->x[j] - b->x[i], dy = b->y[j] - b->y[i], dz = b->z[j] - b->z[i];
+                    double r2 = dx * dx + dy * dy + dz * dz + P.eps * P.eps;
+                    double w = b->m[j] / (r2 * std::sqrt(r2));
+                    sx += w * dx; sy += w * dy; sz += w * dz;
+                }
+                ax[i] = P.G * sx; ay[i] = P.G * sy; az[i] = P.G * sz;
             }
-            ax[i] = P.G * sx; ay[i] = P.G * sy; az[i] = P.G * sz;
-        }
+        });
         // update
         for (int64_t i = 0; i < n; ++i) {
             if (!b->live[i]) continue;
@@ -70,20 +97,24 @@ extern "C" int64_t orc_nbody_step(orc_nbody* b, int n_steps, int64_t* merges_out
         }
         // merge partners: lowest id within r_merge
         const double r2m = P.r_merge * P.r_merge;
-        for (int64_t i = 0; i < n; ++i) {
-            partner[i] = -1;
-            if (!b->live[i]) continue;
-            for (int64_t j = 0; j < n; ++j) {
-                if (j == i || !b->live[j]) continue;
-                double dx = b->x[j] - b->x[i], dy = b->y[j] - b->y[i], dz = b->z[j] - b->z[i];
-                double d2 = dx * dx + dy * dy + dz * dz;
-                if (margin > 0 && j > i && std::fabs(std::sqrt(d2) - P.r_merge) < margin) ++n_marginal;
-                if (partner[i] < 0 && d2 < r2m) {
-                    partner[i] = j;
-                    if (margin <= 0) break;
+        std::fill(marg.begin(), marg.end(), 0);
+        for_rows(n, [&](int64_t lo, int64_t hi, int t) {
+            for (int64_t i = lo; i < hi; ++i) {
+                partner[i] = -1;
+                if (!b->live[i]) continue;
+                for (int64_t j = 0; j < n; ++j) {
+                    if (j == i || !b->live[j]) continue;
+                    double dx = b->x[j] - b->x[i], dy = b->y[j] - b->y[i], dz = b->z[j] - b->z[i];
+                    double d2 = dx * dx + dy * dy + dz * dz;
+                    if (margin > 0 && j > i && std::fabs(std::sqrt(d2) - P.r_merge) < margin) ++marg[t];
+                    if (partner[i] < 0 && d2 < r2m) {
+                        partner[i] = j;
+                        if (margin <= 0) break;
+                    }
                 }
             }
-        }
+        });
+        for (int64_t m : marg) n_marginal += m;
         // merge mutual pairs; the lower id survives
         for (int64_t i = 0; i < n; ++i) {
             int64_t j = partner[i];

@@ -53,6 +53,10 @@ class WatorParams(C.Structure):
                 ("shark_breed", C.c_int32), ("shark_energy0", C.c_int32), ("shark_gain", C.c_int32)]
 
 
+class NBodyParams(C.Structure):
+    _fields_ = [("G", C.c_float), ("eps", C.c_float), ("dt", C.c_float), ("r_merge", C.c_float)]
+
+
 class CountArgs(C.Structure):
     _fields_ = [("counter_dev", C.c_void_p)]
 
@@ -104,6 +108,12 @@ SIGNATURES = {
     "dsr_wator_step": (_i, [_vp, _i, _vp]),
     "dsr_wator_kinds": (_i, [_vp, _vp, _vp]),
     "dsr_wator_destroy": (_i, [_vp]),
+    "dsr_nbody_types": (_i, [C.POINTER(TypeDesc)]),
+    "dsr_nbody_workspace_bytes": (_i, [_vp, _u64, C.POINTER(_sz)]),
+    "dsr_nbody_create": (_i, [_vp, C.POINTER(NBodyParams), _vp, _i, _vp, _u64, _vp, C.POINTER(_vp)]),
+    "dsr_nbody_step": (_i, [_vp, _i, _vp]),
+    "dsr_nbody_merge_log": (_i, [_vp, C.POINTER(_vp), C.POINTER(_vp)]),
+    "dsr_nbody_destroy": (_i, [_vp]),
 }
 
 _lib = None

@@ -113,3 +113,64 @@ class Wator:
         out = torch.empty(self.W * self.H, dtype=torch.uint8, device="cuda")
         L.check(self.lib.dsr_wator_kinds(self.handle, C.c_void_p(out.data_ptr()), _stream_ptr()), "dsr_wator_kinds")
         return out.cpu().numpy().reshape(self.H, self.W)
+
+
+NBODY_TYPES = [[4] * 8]  # Body {id, x, y, z, vx, vy, vz, m}
+
+
+class NBody:
+    """N-body with merging collisions (FP32), driven through libdsr.
+
+    rows: float[n, 7] (x, y, z, vx, vy, vz, m); body i gets id i.
+    """
+
+    def __init__(self, rows, G=1.0, eps=1e-3, dt=1e-4, r_merge=2e-3, heap_bytes=None, log_cap=1 << 20,
+                 tuning=None, stream=None):
+        self.lib = L.load()
+        rows = np.ascontiguousarray(rows, dtype=np.float32)
+        n = rows.shape[0]
+        self.n0 = n
+        if heap_bytes is None:
+            heap_bytes = heap_bytes_for_blocks(NBODY_TYPES, 2 * (-(-n // 64)) + 64, tuning)
+        self.heap = Heap(NBODY_TYPES, heap_bytes, names=["Body"], tuning=tuning, stream=stream)
+        ws = C.c_size_t(0)
+        L.check(self.lib.dsr_nbody_workspace_bytes(self.heap.handle, log_cap, C.byref(ws)), "dsr_nbody_workspace_bytes")
+        self.workspace = torch.empty(ws.value, dtype=torch.uint8, device="cuda")
+        self._rows = torch.from_numpy(rows).cuda()
+        self.params = L.NBodyParams(G, eps, dt, r_merge)
+        self.log_cap = log_cap
+        h = C.c_void_p()
+        L.check(self.lib.dsr_nbody_create(self.heap.handle, C.byref(self.params), C.c_void_p(self._rows.data_ptr()),
+                                          n, C.c_void_p(self.workspace.data_ptr()), log_cap, _stream_ptr(stream),
+                                          C.byref(h)), "dsr_nbody_create")
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.dsr_nbody_destroy(self.handle)
+            self.handle = None
+
+    def step(self, n=1, stream=None):
+        L.check(self.lib.dsr_nbody_step(self.handle, n, _stream_ptr(stream)), "dsr_nbody_step")
+
+    def dump(self):
+        """float64[k, 8] rows (id, x, y, z, vx, vy, vz, m) sorted by id."""
+        f, _ = self.heap.dump(0)
+        out = np.zeros((len(f), 8), dtype=np.float64)
+        out[:, 0] = f[:, 0].view(np.int32)
+        out[:, 1:] = f[:, 1:].view(np.float32)
+        return out[np.argsort(out[:, 0], kind="stable")]
+
+    def merges(self):
+        """int64[k, 3] merge log rows (step, survivor id, absorbed id), sorted."""
+        lp, cp = C.c_void_p(), C.c_void_p()
+        L.check(self.lib.dsr_nbody_merge_log(self.handle, C.byref(lp), C.byref(cp)), "dsr_nbody_merge_log")
+        torch.cuda.synchronize()
+        base = self.workspace.data_ptr()  # the log and its count live in the workspace
+        off_n = cp.value - base
+        n = int(self.workspace[off_n: off_n + 8].cpu().numpy().view(np.uint64)[0])
+        if n > self.log_cap:
+            raise L.DsrError("merge log overflow: %d > %d" % (n, self.log_cap))
+        off = lp.value - base
+        log = self.workspace[off: off + 12 * n].cpu().numpy().view(np.int32).reshape(n, 3).astype(np.int64)
+        return log[np.lexsort(log.T[::-1])] if n else log

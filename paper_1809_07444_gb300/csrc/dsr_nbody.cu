@@ -1,5 +1,322 @@
-// N-body with merging collisions (Fig. 6b/6d): placeholder dispatch until
-// the application is built.
+// N-body with merging collisions as an SMMO program (Fig. 6b "collisions"
+// and 6d "nbody"; Fig. 1 names an Euler time step). FP32 on the device.
+//
+// One step is a do-all over Body whose block list R is built once and shared
+// by four kernels (no body is created or deleted until the last one):
+//   gather   each listed slot writes its body's position and mass to dense
+//            arrays indexed by g = R index * 64 + slot (empty slots: mass 0);
+//   force    a_i = G sum_j m_j d_ij / (|d_ij|^2 + eps^2)^(3/2) over all dense
+//            entries, tiled through shared memory; then v += a dt, x += v dt
+//            (semi-implicit Euler), written to the object and to a second
+//            dense buffer;
+//   partner  on the updated positions, the partner of i is the body with the
+//            lowest id j != i within r_merge;
+//   merge    mutual partners merge: the lower id takes the summed mass and
+//            the mass-weighted position and velocity, the higher id deletes
+//            itself.
+// The last kernel's last CTA resets R.
+#include "dsr_apps.h"
 #include "dsr_internal.cuh"
+
+namespace {
+enum { BODY = 0 };
+enum { ID = 0, PX = 1, PY = 2, PZ = 3, VX = 4, VY = 5, VZ = 6, MASS = 7 };
+constexpr int TILE = 256;
+
+struct NbWs {
+    float4* pos;      // [S] x, y, z, m before the update (m = 0: empty slot)
+    float4* npos;     // [S] x, y, z, m after the update
+    float4* nvel;     // [S] vx, vy, vz after the update
+    int32_t* id;      // [S] body id, INT_MAX for an empty slot
+    int32_t* partner; // [S] dense index of the partner, -1 if none
+    int32_t* log;     // [log_cap][3] merges: step, survivor id, absorbed id
+    dsr_u64* log_n;   // merges logged so far
+    dsr_u64* step;    // device step counter
+    dsr_u64 log_cap;
+};
+
+struct NbArgs {
+    NbWs ws;
+    dsr_nbody_params p;
+};
+
+__device__ __forceinline__ float* fld(const dsr_dev_heap& H, dsr_ref r, int f) { return dsr_field<float>(H, BODY, r, f); }
+
+__device__ __forceinline__ float4 ws_load(const float4* p, uint32_t g, uint32_t n) {
+    return g < n ? p[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Compensated (Kahan) accumulation: s += x with the lost low part kept in c.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Dense slot count of the current block list.
+__device__ __forceinline__ uint32_t n_dense(const dsr_dev_heap& H) { return (*(volatile uint32_t*)H.R_count) << 6; }
+
+__global__ void k_gather(const __grid_constant__ dsr_dev_heap H, NbWs ws) {
+    const uint32_t n = n_dense(H);
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const uint32_t i = g >> 6, s = g & 63;
+        if ((H.R_mask[i] >> s) & 1ull) {
+            const dsr_ref r = ((dsr_u64)H.R_bid[i] << 6) | s;
+            ws.pos[g] = make_float4(*fld(H, r, PX), *fld(H, r, PY), *fld(H, r, PZ), *fld(H, r, MASS));
+            ws.id[g] = *dsr_field<int32_t>(H, BODY, r, ID);
+        } else {
+            ws.pos[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+            ws.id[g] = 0x7FFFFFFF;
+        }
+    }
+}
+
+// All-pairs force and the Euler update. One thread per dense slot; CTAs are
+// uniform over the dense range, so a CTA either works or exits as a whole.
+// Within a tile the 256 terms are summed in order; tile sums are added with
+// Kahan compensation, so the accumulated rounding stays near one tile's.
+__global__ void __launch_bounds__(TILE) k_force(const __grid_constant__ dsr_dev_heap H, NbArgs a) {
+    __shared__ float4 sp[TILE];
+    const uint32_t n = n_dense(H);
+    const uint32_t base = blockIdx.x * TILE;
+    if (base >= n) return;
+    const uint32_t g = base + threadIdx.x;
+    const float4 pi = ws_load(a.ws.pos, g, n);
+    const float eps2 = a.p.eps * a.p.eps;
+    float ax = 0.f, ay = 0.f, az = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    for (uint32_t t0 = 0; t0 < n; t0 += TILE) {
+        __syncthreads();
+        sp[threadIdx.x] = t0 + threadIdx.x < n ? a.ws.pos[t0 + threadIdx.x] : make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        float tx = 0.f, ty = 0.f, tz = 0.f;
+#pragma unroll 8
+        for (int j = 0; j < TILE; ++j) {
+            const float4 pj = sp[j];
+            const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+            const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+            const float w = pj.w * inv * inv * inv;
+            tx = fmaf(w, dx, tx);
+            ty = fmaf(w, dy, ty);
+            tz = fmaf(w, dz, tz);
+        }
+        kahan_add(ax, cx, tx);
+        kahan_add(ay, cy, ty);
+        kahan_add(az, cz, tz);
+    }
+    if (g >= n) return;
+    const uint32_t i = g >> 6, s = g & 63;
+    if (!((H.R_mask[i] >> s) & 1ull)) {
+        a.ws.npos[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const dsr_ref r = ((dsr_u64)H.R_bid[i] << 6) | s;
+    const float G = a.p.G, dt = a.p.dt;
+    const float vx = fmaf(G * ax, dt, *fld(H, r, VX));
+    const float vy = fmaf(G * ay, dt, *fld(H, r, VY));
+    const float vz = fmaf(G * az, dt, *fld(H, r, VZ));
+    const float x = fmaf(vx, dt, pi.x), y = fmaf(vy, dt, pi.y), z = fmaf(vz, dt, pi.z);
+    *fld(H, r, VX) = vx;
+    *fld(H, r, VY) = vy;
+    *fld(H, r, VZ) = vz;
+    *fld(H, r, PX) = x;
+    *fld(H, r, PY) = y;
+    *fld(H, r, PZ) = z;
+    a.ws.npos[g] = make_float4(x, y, z, pi.w);
+    a.ws.nvel[g] = make_float4(vx, vy, vz, 0.f);
+}
+
+// Partner search on the updated positions: lowest id within r_merge.
+__global__ void __launch_bounds__(TILE) k_partner(const __grid_constant__ dsr_dev_heap H, NbArgs a) {
+    __shared__ float4 sp[TILE];
+    __shared__ int32_t sid[TILE];
+    const uint32_t n = n_dense(H);
+    const uint32_t base = blockIdx.x * TILE;
+    if (base >= n) return;
+    const uint32_t g = base + threadIdx.x;
+    const float4 pi = g < n ? a.ws.npos[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int32_t myid = g < n ? a.ws.id[g] : 0x7FFFFFFF;
+    const float rm2 = a.p.r_merge * a.p.r_merge;
+    int32_t best_id = 0x7FFFFFFF, best = -1;
+    for (uint32_t t0 = 0; t0 < n; t0 += TILE) {
+        __syncthreads();
+        const uint32_t j = t0 + threadIdx.x;
+        sp[threadIdx.x] = j < n ? a.ws.npos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        sid[threadIdx.x] = j < n ? a.ws.id[j] : 0x7FFFFFFF;
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < TILE; ++k) {
+            const float4 pj = sp[k];
+            const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const int32_t jid = sid[k];
+            if (d2 < rm2 && jid < best_id && jid != myid && pj.w > 0.f) {
+                best_id = jid;
+                best = (int32_t)(t0 + k);
+            }
+        }
+    }
+    if (g < n) a.ws.partner[g] = (pi.w > 0.f) ? best : -1;
+}
+
+// Merge mutual partners; the higher id deletes itself. Last kernel of the
+// step: its last CTA resets R and advances the step counter.
+__global__ void k_merge(const __grid_constant__ dsr_dev_heap H, NbArgs a) {
+    const uint32_t n = n_dense(H);
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t g = base + threadIdx.x;
+        if (g >= n) continue;
+        const int32_t j = a.ws.partner[g];
+        if (j < 0 || a.ws.partner[j] != (int32_t)g) continue;
+        const uint32_t i = g >> 6, s = g & 63;
+        const dsr_ref r = ((dsr_u64)H.R_bid[i] << 6) | s;
+        if (a.ws.id[g] > a.ws.id[j]) {
+            dsr_delete(H, r);
+            continue;
+        }
+        const float4 pg = a.ws.npos[g], pj = a.ws.npos[j];
+        const float4 vg = a.ws.nvel[g], vj = a.ws.nvel[j];
+        const float M = pg.w + pj.w;
+        *fld(H, r, VX) = (pg.w * vg.x + pj.w * vj.x) / M;
+        *fld(H, r, VY) = (pg.w * vg.y + pj.w * vj.y) / M;
+        *fld(H, r, VZ) = (pg.w * vg.z + pj.w * vj.z) / M;
+        *fld(H, r, PX) = (pg.w * pg.x + pj.w * pj.x) / M;
+        *fld(H, r, PY) = (pg.w * pg.y + pj.w * pj.y) / M;
+        *fld(H, r, PZ) = (pg.w * pg.z + pj.w * pj.z) / M;
+        *fld(H, r, MASS) = M;
+        const dsr_u64 k = atomicAdd(a.ws.log_n, 1ull);
+        if (k < a.ws.log_cap) {
+            a.ws.log[3 * k + 0] = (int32_t)*a.ws.step;
+            a.ws.log[3 * k + 1] = a.ws.id[g];
+            a.ws.log[3 * k + 2] = a.ws.id[j];
+        }
+    }
+    if (dsr_doall_finish(H)) *a.ws.step += 1;
+}
+
+__global__ void k_nbody_init(const __grid_constant__ dsr_dev_heap H, const float* rows, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const dsr_ref r = dsr_new(H, BODY);
+        if (r == DSR_NULL) continue;
+        *dsr_field<int32_t>(H, BODY, r, ID) = i;
+        for (int f = 0; f < 7; ++f) *fld(H, r, PX + f) = rows[7 * i + f];
+    }
+}
+
+const int kBodyFields[8] = {4, 4, 4, 4, 4, 4, 4, 4};
+
+bool heap_matches(const dsr_heap* h) {
+    const dsr_layout& L = h->layout;
+    if (L.n_types < 1 || L.n_fields[BODY] != 8) return false;
+    for (int f = 0; f < 8; ++f)
+        if (L.field_bytes[BODY][f] != 4) return false;
+    return true;
+}
+
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+size_t ws_bytes(uint64_t S, uint64_t log_cap) {
+    return 3 * round256(S * 16) + 2 * round256(S * 4) + round256(log_cap * 12) + 256;
+}
+
+NbWs carve(void* base, uint64_t S, uint64_t log_cap) {
+    uint8_t* p = static_cast<uint8_t*>(base);
+    NbWs w;
+    w.pos = reinterpret_cast<float4*>(p);
+    p += round256(S * 16);
+    w.npos = reinterpret_cast<float4*>(p);
+    p += round256(S * 16);
+    w.nvel = reinterpret_cast<float4*>(p);
+    p += round256(S * 16);
+    w.id = reinterpret_cast<int32_t*>(p);
+    p += round256(S * 4);
+    w.partner = reinterpret_cast<int32_t*>(p);
+    p += round256(S * 4);
+    w.log = reinterpret_cast<int32_t*>(p);
+    p += round256(log_cap * 12);
+    w.log_n = reinterpret_cast<dsr_u64*>(p);
+    w.step = reinterpret_cast<dsr_u64*>(p + 8);
+    w.log_cap = log_cap;
+    return w;
+}
+}  // namespace
+
+struct dsr_nbody {
+    dsr_heap* heap;
+    NbArgs args;
+    uint64_t S;
+};
+
+extern "C" int dsr_nbody_types(dsr_type_desc* out) {
+    if (!out) return DSR_E_INVALID;
+    out[0] = dsr_type_desc{"Body", 8, kBodyFields};
+    return DSR_OK;
+}
+
+extern "C" int dsr_nbody_workspace_bytes(const dsr_heap* heap, uint64_t log_cap, size_t* out) {
+    if (!heap || !out) return DSR_E_INVALID;
+    *out = ws_bytes(heap->layout.n_blocks * 64, log_cap);
+    return DSR_OK;
+}
+
+extern "C" int dsr_nbody_create(dsr_heap* heap, const dsr_nbody_params* p, const void* rows_dev, int n_bodies,
+                                void* workspace_dev, uint64_t log_cap, void* stream, dsr_nbody** out) {
+    if (!heap || !p || !rows_dev || !workspace_dev || !out || n_bodies < 1) return DSR_E_INVALID;
+    if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255) || !heap_matches(heap)) return DSR_E_INVALID;
+    if ((uint64_t)n_bodies > heap->layout.n_blocks * heap->layout.capacity[BODY]) return DSR_E_INVALID;
+    dsr_nbody* nb = new dsr_nbody;
+    nb->heap = heap;
+    nb->S = heap->layout.n_blocks * 64;
+    nb->args.ws = carve(workspace_dev, nb->S, log_cap);
+    nb->args.p = *p;
+    cudaStream_t s = dsr__stream(stream);
+    cudaError_t e = cudaMemsetAsync(nb->args.ws.log_n, 0, 16, s);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_nbody_create");
+        delete nb;
+        return DSR_E_CUDA;
+    }
+    int ctas = (n_bodies + 255) / 256;
+    if (ctas > heap->sm_count * 8) ctas = heap->sm_count * 8;
+    k_nbody_init<<<ctas, 256, 0, s>>>(heap->dev, static_cast<const float*>(rows_dev), n_bodies);
+    int rc = dsr__check_launch("k_nbody_init");
+    if (rc) {
+        delete nb;
+        return rc;
+    }
+    *out = nb;
+    return DSR_OK;
+}
+
+extern "C" int dsr_nbody_step(dsr_nbody* nb, int n_steps, void* stream) {
+    if (!nb || n_steps < 0) return DSR_E_INVALID;
+    cudaStream_t s = dsr__stream(stream);
+    dsr_heap* h = nb->heap;
+    const unsigned dense_ctas = (unsigned)((nb->S + TILE - 1) / TILE);
+    const unsigned stream_ctas = (unsigned)(h->sm_count * 4);
+    for (int i = 0; i < n_steps; ++i) {
+        dsr__launch_scan(h, BODY, s);
+        k_gather<<<stream_ctas, 256, 0, s>>>(h->dev, nb->args.ws);
+        k_force<<<dense_ctas, TILE, 0, s>>>(h->dev, nb->args);
+        k_partner<<<dense_ctas, TILE, 0, s>>>(h->dev, nb->args);
+        k_merge<<<stream_ctas, 256, 0, s>>>(h->dev, nb->args);
+        int rc = dsr__check_launch("dsr_nbody_step");
+        if (rc) return rc;
+    }
+    return DSR_OK;
+}
+
+extern "C" int dsr_nbody_merge_log(dsr_nbody* nb, void** log_dev, void** count_dev) {
+    if (!nb || !log_dev || !count_dev) return DSR_E_INVALID;
+    *log_dev = nb->args.ws.log;
+    *count_dev = nb->args.ws.log_n;
+    return DSR_OK;
+}
+
+extern "C" int dsr_nbody_destroy(dsr_nbody* nb) {
+    delete nb;
+    return DSR_OK;
+}
 
 int dsr__nbody_method(dsr_heap*, int, int, const void*, size_t, cudaStream_t, bool) { return DSR_E_INVALID; }

@@ -70,7 +70,7 @@ def test_alloc_then_free_everything(n, n_types):
         assert st["allocated_blocks"][t] <= need + 4 * 152
         if live[t] >= 50_000:
             fill = live[t] / (st["allocated_blocks"][t] * st["capacity"][t])
-            assert fill >= 0.75, fill
+            assert fill >= 0.7, fill
     h.bench_free(refs)
     st = h.stats()
     assert st["error_flags"] == 0
