@@ -46,7 +46,8 @@ enum {
     DSR_E_INVALID = 1,   /* bad argument: null pointer, bad type/method id, size out of range */
     DSR_E_OOM = 2,       /* arena too small for even one block per type */
     DSR_E_CUDA = 3,      /* a CUDA runtime call failed; see dsr_last_cuda_error */
-    DSR_E_DEVICE = 4     /* a device-side error bit is set (see dsr_stats.error_flags) */
+    DSR_E_DEVICE = 4,    /* a device-side error bit is set (see dsr_stats.error_flags) */
+    DSR_E_TOO_LARGE = 5  /* the problem exceeds a fixed maximum of the called entry point */
 };
 
 /* Event counters (dsr_heap_counters), cumulative since create or reset. */

@@ -113,6 +113,34 @@ int dsr_nbody_step(dsr_nbody* nb, int n_steps, void* stream);
 int dsr_nbody_merge_log(dsr_nbody* nb, void** log_dev, void** count_dev);
 int dsr_nbody_destroy(dsr_nbody* nb);
 
+/* Allocation-free n-body step (the paper has no counterpart). Same steps and
+ * results as dsr_nbody_step, for callers that cannot call cudaMalloc: code
+ * that runs where device allocation is not allowed or not available, such as
+ * a plugin handed device memory by a host program that owns it all, or work
+ * queued while a stream is being captured into a CUDA graph. Instead of a
+ * caller-allocated workspace, the per-slot scratch of a step (dense
+ * positions, velocities, ids, partners; 56 bytes per slot) and the step
+ * counter live in a static device array inside this library, sized for
+ * DSR_NOALLOC_MAX_SLOTS slots (about 0.9 MB), which every GPU that loads the
+ * library holds until the process exits. The call allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.
+ *   heap        a heap whose type 0 is Body (dsr_nbody_types) and whose block
+ *               count times 64 is at most DSR_NOALLOC_MAX_SLOTS; a larger
+ *               heap is rejected with DSR_E_TOO_LARGE.
+ *   step0       the step number recorded in the merge log for the first of
+ *               the n_steps steps.
+ *   log_dev     device int32[log_cap][3] merge log (may be NULL if log_cap
+ *               is 0); log_count_dev: device uint64 that receives, added to
+ *               its current value, the number of merges.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call shares the one array and it keeps
+ * the last call's contents: calls that overlap on the GPU (other streams, or
+ * other threads) race, so order them on one stream. */
+#define DSR_NOALLOC_MAX_SLOTS 16384
+int dsr_nbody_step_noalloc(dsr_heap* heap, const dsr_nbody_params* p, int n_steps, uint64_t step0, void* log_dev,
+                           uint64_t log_cap, void* log_count_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,7 +13,8 @@ MAX_TYPES = 8
 MAX_FIELDS = 16
 MAX_LEVELS = 6
 
-OK, E_INVALID, E_OOM, E_CUDA, E_DEVICE = 0, 1, 2, 3, 4
+OK, E_INVALID, E_OOM, E_CUDA, E_DEVICE, E_TOO_LARGE = 0, 1, 2, 3, 4, 5
+NOALLOC_MAX_SLOTS = 16384
 ERR_OOM, ERR_RETRY, ERR_DOUBLE_FREE, ERR_BAD_HANDLE, ERR_CAPACITY = 1, 2, 4, 8, 16
 
 METHOD_COUNT, METHOD_STREAM_ADD, METHOD_DELETE_IF, METHOD_CLONE = 1, 2, 3, 4
@@ -114,6 +115,7 @@ SIGNATURES = {
     "dsr_nbody_step": (_i, [_vp, _i, _vp]),
     "dsr_nbody_merge_log": (_i, [_vp, C.POINTER(_vp), C.POINTER(_vp)]),
     "dsr_nbody_destroy": (_i, [_vp]),
+    "dsr_nbody_step_noalloc": (_i, [_vp, C.POINTER(NBodyParams), _i, _u64, _vp, _u64, _vp, _vp]),
 }
 
 _lib = None

@@ -33,6 +33,7 @@ extern "C" const char* dsr_status_string(int s) {
         case DSR_E_OOM: return "arena too small";
         case DSR_E_CUDA: return "CUDA error";
         case DSR_E_DEVICE: return "device-side error";
+        case DSR_E_TOO_LARGE: return "size exceeds the entry point's fixed maximum";
         default: return "unknown status";
     }
 }

@@ -18,6 +18,8 @@
 #include "dsr_apps.h"
 #include "dsr_internal.cuh"
 
+#include <mutex>
+
 namespace {
 enum { BODY = 0 };
 enum { ID = 0, PX = 1, PY = 2, PZ = 3, VX = 4, VY = 5, VZ = 6, MASS = 7 };
@@ -320,3 +322,92 @@ extern "C" int dsr_nbody_destroy(dsr_nbody* nb) {
 }
 
 int dsr__nbody_method(dsr_heap*, int, int, const void*, size_t, cudaStream_t, bool) { return DSR_E_INVALID; }
+
+// ---------------------------------------------------------------------------
+// Allocation-free step. The per-slot scratch of a step (dense positions,
+// velocities, ids and partners) lives in this file-scope device array instead
+// of a caller-allocated workspace, for callers that cannot call cudaMalloc.
+// Every GPU that loads the library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+struct NoallocScratch {
+    float4 pos[DSR_NOALLOC_MAX_SLOTS];
+    float4 npos[DSR_NOALLOC_MAX_SLOTS];
+    float4 nvel[DSR_NOALLOC_MAX_SLOTS];
+    int32_t id[DSR_NOALLOC_MAX_SLOTS];
+    int32_t partner[DSR_NOALLOC_MAX_SLOTS];
+    dsr_u64 step;
+};
+
+__global__ void k_set_u64(dsr_u64* p, dsr_u64 v) { *p = v; }
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+NoallocScratch* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+// Device address of the scratch array on the current device. Host code may
+// not use g_noalloc_scratch itself (its host-side name is a stand-in, not a
+// device address); the address is looked up once per device, with that
+// device current, and cached.
+static int noalloc_scratch(int device, NoallocScratch** out) {
+    if (device < 0 || device >= kMaxDevices) return DSR_E_INVALID;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            dsr__set_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+            return DSR_E_CUDA;
+        }
+        g_noalloc_addr[device] = static_cast<NoallocScratch*>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return DSR_OK;
+}
+
+extern "C" int dsr_nbody_step_noalloc(dsr_heap* heap, const dsr_nbody_params* p, int n_steps, uint64_t step0,
+                                      void* log_dev, uint64_t log_cap, void* log_count_dev, void* stream) {
+    if (!heap || !p || n_steps < 0 || !log_count_dev || (log_cap && !log_dev) || !heap_matches(heap))
+        return DSR_E_INVALID;
+    const uint64_t S = heap->layout.n_blocks * 64;
+    if (S > DSR_NOALLOC_MAX_SLOTS) return DSR_E_TOO_LARGE;
+    int device = -1;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) {
+        dsr__set_cuda_error(e, "dsr_nbody_step_noalloc");
+        return DSR_E_CUDA;
+    }
+    if (device != heap->device) return DSR_E_INVALID;
+    NoallocScratch* sc = nullptr;
+    int rc = noalloc_scratch(device, &sc);
+    if (rc) return rc;
+    NbArgs a;
+    a.p = *p;
+    a.ws.pos = sc->pos;
+    a.ws.npos = sc->npos;
+    a.ws.nvel = sc->nvel;
+    a.ws.id = sc->id;
+    a.ws.partner = sc->partner;
+    a.ws.step = &sc->step;
+    a.ws.log = static_cast<int32_t*>(log_dev);
+    a.ws.log_n = static_cast<dsr_u64*>(log_count_dev);
+    a.ws.log_cap = log_cap;
+    cudaStream_t s = dsr__stream(stream);
+    // The array keeps the previous call's contents; the step counter is the
+    // only value a step reads before writing it.
+    k_set_u64<<<1, 1, 0, s>>>(&sc->step, step0);
+    dsr_heap* h = heap;
+    const unsigned dense_ctas = (unsigned)((S + TILE - 1) / TILE);
+    const unsigned stream_ctas = (unsigned)(h->sm_count * 4);
+    for (int i = 0; i < n_steps; ++i) {
+        dsr__launch_scan(h, BODY, s);
+        k_gather<<<stream_ctas, 256, 0, s>>>(h->dev, a.ws);
+        k_force<<<dense_ctas, TILE, 0, s>>>(h->dev, a);
+        k_partner<<<dense_ctas, TILE, 0, s>>>(h->dev, a);
+        k_merge<<<stream_ctas, 256, 0, s>>>(h->dev, a);
+    }
+    return dsr__check_launch("dsr_nbody_step_noalloc");
+}
