@@ -192,52 +192,48 @@ __global__ void k_heap_mark_free(const __grid_constant__ dsr_dev_heap H, dsr_u64
 }
 
 // Do-all steps 1 and 2 (Section 2.3, Fig. 4): list the set bits of
-// allocated[T] and compact them into R by a prefix sum. Each warp takes 32
-// level-0 words at a time (skipping words whose level-1 bit is clear), counts
-// their set bits, forms an exclusive prefix sum across the warp with
-// shuffles, reserves its run of R with one atomicAdd, and writes for every
-// listed block its id and the snapshot of its occupied slots.
-__global__ void k_scan(const __grid_constant__ dsr_dev_heap H, int T) {
-    const dsr_hbm& A = H.alloc_bm[T];
-    const uint32_t nw = A.nwords[0];
+// allocated[T] (step 1) and compact them into the block list R by a prefix
+// sum (step 2). One thread per block id: each CTA takes 256 consecutive
+// block ids per round; a warp ballots which of its 32 ids are allocated, the
+// CTA forms the exclusive prefix sum of its 8 warp counts in shared memory
+// and reserves its run of R with one atomicAdd; every listed block gets its
+// id and the snapshot of its occupied slots. Runs of R follow block order
+// within a round, so consecutive entries are usually neighbouring blocks.
+__global__ void __launch_bounds__(256) k_scan(const __grid_constant__ dsr_dev_heap H, int T) {
+    __shared__ unsigned warp_n[8];
+    __shared__ unsigned run_base;
+    const dsr_u64* leaf = H.alloc_bm[T].lvl[0];
     const dsr_u64 v = H.valid[T];
-    const unsigned lane = threadIdx.x & 31;
-    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t base = warp * 32; base < nw; base += nwarps * 32) {
-        const uint32_t idx = base + lane;
-        dsr_u64 w = 0;
-        if (idx < nw) {
-            bool maybe = true;
-            if (A.n_levels > 1) maybe = (A.lvl[1][idx >> 6] >> (idx & 63)) & 1ull;
-            if (maybe) w = A.lvl[0][idx];
+    const dsr_u64 M = H.M;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned objs = 0;
+    for (dsr_u64 base = (dsr_u64)blockIdx.x * 256; base < M; base += (dsr_u64)gridDim.x * 256) {
+        const dsr_u64 b = base + threadIdx.x;
+        const bool set = b < M && ((leaf[b >> 6] >> (b & 63)) & 1ull);
+        const unsigned ballot = __ballot_sync(0xFFFFFFFFu, set);
+        if (lane == 0) warp_n[warp] = __popc(ballot);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned total = 0;
+            for (int w = 0; w < 8; ++w) {
+                const unsigned n = warp_n[w];
+                warp_n[w] = total;
+                total += n;
+            }
+            run_base = total ? atomicAdd(H.R_count, total) : 0;
         }
-        const unsigned cnt = __popcll(w);
-        unsigned incl = cnt;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-            if (lane >= (unsigned)d) incl += y;
-        }
-        const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (total == 0) continue;
-        unsigned start = 0;
-        if (lane == 31) start = atomicAdd(H.R_count, total);
-        start = __shfl_sync(0xFFFFFFFFu, start, 31) + incl - cnt;
-        unsigned objs = 0;
-        while (w) {
-            const int b = __ffsll((long long)w) - 1;
-            w &= w - 1;
-            const dsr_u64 bid = (dsr_u64)idx * 64 + b;
-            const dsr_u64 live = v & ~H.obj[bid];
-            H.R_bid[start] = (uint32_t)bid;
-            H.R_mask[start] = live;
+        __syncthreads();
+        if (set) {
+            const dsr_u64 live = v & ~H.obj[b];
+            const unsigned k = run_base + warp_n[warp] + __popc(ballot & ((1u << lane) - 1));
+            H.R_bid[k] = (uint32_t)b;
+            H.R_mask[k] = live;
             objs += __popcll(live);
-            ++start;
         }
-        objs = __reduce_add_sync(0xFFFFFFFFu, objs);
-        if (lane == 0 && objs) dsr_count(H.ctr, DSR_CTR_VISITS, objs);
+        __syncthreads();
     }
+    objs = __reduce_add_sync(0xFFFFFFFFu, objs);
+    if (lane == 0 && objs) dsr_count(H.ctr, DSR_CTR_VISITS, objs);
 }
 
 // Statistics: out[0] free blocks; out[1 + 3T + {0,1,2}] allocated blocks,
@@ -269,8 +265,8 @@ __global__ void k_stats(const __grid_constant__ dsr_dev_heap H, dsr_u64* out) {
 }
 
 int dsr__scan_grid(const dsr_heap* h, int type) {
-    const uint64_t warps = (h->dev.alloc_bm[type].nwords[0] + 31) / 32;
-    uint64_t ctas = (warps + 7) / 8;
+    (void)type;
+    uint64_t ctas = (h->dev.M + 255) / 256;
     const uint64_t cap = (uint64_t)h->sm_count * 8;
     if (ctas > cap) ctas = cap;
     return ctas < 1 ? 1 : (int)ctas;
