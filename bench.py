@@ -53,6 +53,8 @@ def _args():
     p.add_argument("--impl", default="dsr", choices=["dsr", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-extra", action="store_true", help="headline only (no batched/served/microbenchmarks)")
+    p.add_argument("--served-seconds", type=float, default=20.0)
     return p.parse_args()
 
 
@@ -264,6 +266,160 @@ def run_gpu(args, rank, world):
     }
 
 
+# ---------------------------------------------------------------------------
+# secondary measurements (rank 0, after the headline)
+# ---------------------------------------------------------------------------
+def _ev():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def bench_alloc_free(n=1 << 24, n_types=2, reps=3):
+    """Allocation microbenchmark: n threads each create one object (types by a
+    hash of the thread index), then every object is deleted; fresh heap, L2
+    flushed before each timed kernel."""
+    import torch
+    from paper_1809_07444_gb300.heap import Heap, heap_bytes_for_blocks
+
+    types = [[4, 4], [4, 4, 4, 4]]
+    h = Heap(types, heap_bytes_for_blocks(types, int(n / 32 * 1.3) + 4096))
+    refs = torch.empty(n, dtype=torch.int64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ta, tf = [], []
+    for r in range(reps + 1):
+        h.reset()
+        flush.fill_(r)
+        a0, a1 = _ev()
+        a0.record()
+        h.bench_alloc(refs, n_types, 77 + r)
+        a1.record()
+        flush.fill_(r + 1)
+        f0, f1 = _ev()
+        f0.record()
+        h.bench_free(refs)
+        f1.record()
+        torch.cuda.synchronize()
+        if r:  # first round warms up
+            ta.append(a0.elapsed_time(a1) / 1e3)
+            tf.append(f0.elapsed_time(f1) / 1e3)
+    st = h.stats()
+    ok = st["error_flags"] == 0 and st["free_blocks"] == st["n_blocks"]
+    return {"objects": n, "types": n_types, "allocs_per_s": n / statistics.median(ta),
+            "frees_per_s": n / statistics.median(tf), "alloc_free_per_s": 2 * n / (statistics.median(ta) + statistics.median(tf)),
+            "heap_consistent_after": ok, "l2": "flushed before each kernel"}
+
+
+def bench_streaming_doall(n=1 << 28, fields=4, reps=5):
+    """Streaming do-all: one type with `fields` int32 fields, n objects (>> L2);
+    method field f += field f+1 (reads every field, writes every field)."""
+    import torch
+    from paper_1809_07444_gb300 import _lib as L
+    from paper_1809_07444_gb300.heap import Heap, heap_bytes_for_blocks, _stream_ptr
+
+    types = [[4] * fields]
+    blocks = n // 64
+    h = Heap(types, heap_bytes_for_blocks(types, blocks + 1024))
+    refs = torch.empty(n, dtype=torch.int64, device="cuda")
+    h.bench_alloc(refs, 1, 5)
+    del refs
+    torch.cuda.synchronize()
+    lib, sp = h.lib, _stream_ptr()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ms, ms_full = [], []
+    for r in range(reps + 1):
+        flush.fill_(r)
+        L.check(lib.dsr_doall_scan(h.handle, 0, sp), "dsr_doall_scan")
+        a0, a1 = _ev()
+        a0.record()
+        L.check(lib.dsr_doall_run(h.handle, 0, L.METHOD_STREAM_ADD, None, 0, sp), "dsr_doall_run")
+        a1.record()
+        flush.fill_(r + 1)
+        b0, b1 = _ev()
+        b0.record()
+        h.parallel_do(0, L.METHOD_STREAM_ADD, None)
+        b1.record()
+        torch.cuda.synchronize()
+        if r:
+            ms.append(a0.elapsed_time(a1))
+            ms_full.append(b0.elapsed_time(b1))
+    st = h.stats()
+    live = st["live_objects"][0]
+    alloc_blocks = st["allocated_blocks"][0]
+    # algorithmic bytes: every field read and written once, plus the R entry
+    # (12 B) of each listed block
+    bytes_method = live * fields * 4 * 2 + alloc_blocks * 12
+    t = statistics.median(ms) * 1e-3
+    peak, kind = _peaks()
+    return {"objects": live, "fields": fields, "method_ms": t * 1e3, "doall_ms": statistics.median(ms_full),
+            "object_updates_per_s": live / t, "achieved_gbs": bytes_method / t / 1e9, "peak_gbs": peak,
+            "frac": bytes_method / t / 1e9 / peak, "peak_source": kind,
+            "algorithmic_bytes": bytes_method, "fill": live / (alloc_blocks * 64)}
+
+
+def bench_batched(n_inst=256, steps=20, one_by_one_steps=3):
+    """The batched workload (256 wa-tor instances, sides log-uniform in
+    [64, 1024]) advanced by graph-captured group steps, against the same
+    instances stepped one by one in the plain form."""
+    import torch
+    from paper_1809_07444_gb300 import workloads as WL
+    from paper_1809_07444_gb300.apps import Wator, WatorBatch
+
+    sides = [int(s) for s in WL.batched_sides(n_inst, 1)]
+    need = sum(WatorBatch.blocks_for(s, s) * 1000 + s * s * 24 for s in sides)
+    b = WatorBatch(need + (256 << 20), max_instances=n_inst)
+    slots = [b.add(s, s, WL.wator_initial(s, s, 1000 + i), 1000 + i) for i, s in enumerate(sides)]
+    b.step(3)
+    torch.cuda.synchronize()
+    v0 = sum(b.heap(x).counters()["visits"] for x in slots)
+    e0, e1 = _ev()
+    e0.record()
+    b.step(steps)
+    e1.record()
+    e1.synchronize()
+    v1 = sum(b.heap(x).counters()["visits"] for x in slots)
+    t_b = e0.elapsed_time(e1) / 1e3
+    del b
+    torch.cuda.empty_cache()
+    plain = [Wator(s, s, WL.wator_initial(s, s, 1000 + i), 1000 + i) for i, s in enumerate(sides)]
+    for w in plain:
+        w.step(3)
+    torch.cuda.synchronize()
+    p0 = sum(w.heap.counters()["visits"] for w in plain)
+    e0, e1 = _ev()
+    e0.record()
+    for _ in range(one_by_one_steps):
+        for w in plain:
+            w.step(1)
+    e1.record()
+    e1.synchronize()
+    p1 = sum(w.heap.counters()["visits"] for w in plain)
+    t_p = e0.elapsed_time(e1) / 1e3
+    vb, vp = (v1 - v0) / t_b, (p1 - p0) / t_p
+    return {"workload": "wator-batched-%d (sides log-uniform [64, 1024], seeds 1000+i)" % n_inst,
+            "cells": int(sum(s * s for s in sides)), "steps": steps, "ms_per_step": t_b * 1e3 / steps,
+            "object_updates_per_s": vb, "one_by_one": {"object_updates_per_s": vp, "steps": one_by_one_steps,
+                                                       "ms_per_step": t_p * 1e3 / one_by_one_steps,
+                                                       "launches_per_step": 10 * n_inst},
+            "speedup_vs_one_by_one": vb / vp if vp else None, "launches_per_step": 10, "graph": True}
+
+
+def bench_served(seconds=20.0, n_jobs=10000, arena_gb=64):
+    """The served workload (Poisson 200 jobs/s, game-of-life and wa-tor, sides
+    log-uniform in [128, 4096], 50-1000 steps, 64 GB of arenas), in real time
+    for a bounded number of seconds."""
+    from paper_1809_07444_gb300 import workloads as WL
+    from paper_1809_07444_gb300.serve import Server, summarize
+
+    s = WL.served_jobs(n_jobs, 2024)
+    jobs = [{"id": i, "arrival": float(s["arrival"][i]), "app": int(s["app"][i]), "side": int(s["side"][i]),
+             "steps": int(s["steps"][i]), "seed": int(s["seed"][i])} for i in range(n_jobs)]
+    srv = Server(arena_bytes=arena_gb << 30, max_jobs=4096)
+    rep = srv.run(jobs, time_limit=seconds, realtime=True, keep_hashes=False)
+    out = summarize(rep)
+    out["sample"] = "first %.0f s of wall time of the 10,000-job stream (arrival seed 2024)" % seconds
+    return out
+
+
 def main():
     args = _args()
     rank = int(os.environ.get("RANK", 0))
@@ -324,6 +480,14 @@ def main():
         rate, n, el = oracle_wator_rate(args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "first %d steps of the same wa-tor 2048x2048 run (%.1f s)" % (n, el)}
+    if world == 1 and not args.no_extra:
+        # the other halves of the metric: batched vs plain, alloc+free/s, the
+        # streaming do-all against the HBM roofline, and the served form
+        line["batched"] = bench_batched()
+        line["alloc_free_microbench"] = bench_alloc_free()
+        line["streaming_doall"] = bench_streaming_doall()
+        if args.served_seconds > 0:
+            line["served"] = bench_served(args.served_seconds)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -215,6 +215,45 @@ int dsr_heap_counters(dsr_heap* heap, void* stream, uint64_t* out);
  * as if the heap were full. Queued on `stream`. */
 int dsr_heap_inject_oom(dsr_heap* heap, uint32_t n, void* stream);
 
+/* ---- heap groups -----------------------------------------------------------
+ * A group carves heaps with the same type descriptors and tuning out of one
+ * caller-owned arena and runs do-alls over all of its heaps in single kernel
+ * launches (no counterpart in the paper, which runs one heap; this is the
+ * batched form: many independent simulations, each with its own heap, so an
+ * instance that runs out of memory does not touch the others and a finished
+ * instance returns its bytes at once). A group do-all is one fused scan over
+ * every heap's allocated[T] bitmap (each listed block tagged with its heap
+ * index) and one method kernel over the combined list.
+ *   max_heaps   number of heap slots (indices 0 .. max_heaps-1).
+ * The arena holds the group's tables and lists first; heaps are placed in the
+ * rest, first fit by bytes. */
+typedef struct dsr_group dsr_group;
+int dsr_group_create(const dsr_type_desc* types, int n_types, void* arena_dev, size_t arena_bytes, int max_heaps,
+                     const dsr_tuning* tune, void* stream, dsr_group** out);
+int dsr_group_destroy(dsr_group* g);
+/* Carve a heap of at least n_blocks blocks plus extra_bytes of caller scratch
+ * (256-byte aligned, returned in *extra_dev) and queue its reset on `stream`.
+ * Returns DSR_E_OOM when no free range of the arena is large enough (the
+ * group is unchanged). The heap handle stays owned by the group. */
+int dsr_group_add_heap(dsr_group* g, uint64_t n_blocks, size_t extra_bytes, void* stream, int* index_out,
+                       dsr_heap** heap_out, void** extra_dev_out);
+/* Return a heap's bytes to the arena. Work queued on the heap must have
+ * finished, or be ordered before any later use of the bytes on one stream. */
+int dsr_group_remove_heap(dsr_group* g, int index);
+/* Bytes a heap of n_blocks blocks plus extra_bytes takes in a group arena. */
+int dsr_group_heap_bytes(const dsr_group* g, uint64_t n_blocks, size_t extra_bytes, size_t* out);
+/* Free bytes of the arena, and the largest free range. */
+int dsr_group_free_bytes(const dsr_group* g, size_t* total_free, size_t* largest_free);
+int dsr_group_heap_count(const dsr_group* g);
+/* Builds compiled with -DDSR_DEVICE_CHECKS check indices and handles on the
+ * device; a failed check sets DSR_ERR_CHECK (32) and records the first
+ * failure as (code << 48 | value). These calls read the group's and a heap's
+ * record (both are 0 in ordinary builds). Synchronous. */
+int dsr_group_check_record(dsr_group* g, uint32_t* err_out, uint64_t* record_out);
+int dsr_heap_check_record(dsr_heap* heap, uint32_t* err_out, uint64_t* record_out);
+/* Group do-all with a built-in method (DSR_METHOD_COUNT). */
+int dsr_group_parallel_do(dsr_group* g, int type, int method, const void* args, size_t args_bytes, void* stream);
+
 /* Text for a status code; the CUDA error of the last DSR_E_CUDA. */
 const char* dsr_status_string(int status);
 const char* dsr_last_cuda_error(void);

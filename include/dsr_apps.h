@@ -44,6 +44,21 @@ int dsr_gol_create(dsr_heap* heap, int W, int H, const void* alive0_dev, void* w
 int dsr_gol_step(dsr_gol* g, int n_gen, void* stream);
 int dsr_gol_destroy(dsr_gol* g);
 
+/* Batched game of life: many instances, each with its own heap in one heap
+ * group, advanced together by three group do-alls per generation captured
+ * into a CUDA graph (same conventions as the batched wa-tor below). */
+typedef struct dsr_gol_batch dsr_gol_batch;
+int dsr_gol_batch_create(void* arena_dev, size_t arena_bytes, int max_instances, const dsr_tuning* tune, void* stream,
+                         dsr_gol_batch** out);
+int dsr_gol_batch_instance_bytes(const dsr_gol_batch* b, int W, int H, uint64_t n_blocks, size_t* out);
+int dsr_gol_batch_add(dsr_gol_batch* b, int W, int H, uint64_t n_blocks, const void* alive0_dev, void* stream,
+                      int* inst_out);
+int dsr_gol_batch_remove(dsr_gol_batch* b, int inst);
+int dsr_gol_batch_step(dsr_gol_batch* b, int n_gen, void* stream);
+int dsr_gol_batch_heap(dsr_gol_batch* b, int inst, dsr_heap** out);
+int dsr_gol_batch_group(dsr_gol_batch* b, dsr_group** out);
+int dsr_gol_batch_destroy(dsr_gol_batch* b);
+
 /* ---- wa-tor ----------------------------------------------------------------
  * W x H torus, von Neumann neighbours in the order N (y-1), E (x+1), S (y+1),
  * W (x-1); cell index c = y*W + x. Types: 0 Fish {x, y, timer}, 1 Shark
@@ -88,6 +103,36 @@ int dsr_wator_step(dsr_wator* w, int n_steps, void* stream);
 /* Device uint8[W*H] occupancy snapshot (0/1/2) of the current state. */
 int dsr_wator_kinds(dsr_wator* w, void* kind_out_dev, void* stream);
 int dsr_wator_destroy(dsr_wator* w);
+
+/* ---- batched wa-tor ----------------------------------------------------------
+ * Many independent wa-tor instances (each with its own sizes, parameters and
+ * seed) advance together: every instance has its own heap in a heap group
+ * (dsr_group_* in dsr.h) carved from one caller-owned arena, and one batched
+ * step is five group do-alls (one fused scan and one method kernel each) over
+ * all instances, captured once into a CUDA graph and replayed until an
+ * instance is added or removed. Each instance follows exactly the rules and
+ * results of the plain form. The arena must be 256-byte aligned; its first
+ * bytes hold the instance table. */
+typedef struct dsr_wator_batch dsr_wator_batch;
+int dsr_wator_batch_create(void* arena_dev, size_t arena_bytes, int max_instances, const dsr_tuning* tune,
+                           void* stream, dsr_wator_batch** out);
+/* Arena bytes an instance of W x H with a heap of n_blocks blocks takes. */
+int dsr_wator_batch_instance_bytes(const dsr_wator_batch* b, int W, int H, uint64_t n_blocks, size_t* out);
+/* Add an instance (kind0_dev as for dsr_wator_create) whose heap has at least
+ * n_blocks blocks; *inst_out receives its slot. DSR_E_OOM when the arena has
+ * no free range large enough or all slots are taken. Synchronises `stream`. */
+int dsr_wator_batch_add(dsr_wator_batch* b, const dsr_wator_params* p, uint64_t n_blocks, const void* kind0_dev,
+                        void* stream, int* inst_out);
+/* Remove an instance and return its bytes. The caller must have finished all
+ * work on it (synchronise the stream first). */
+int dsr_wator_batch_remove(dsr_wator_batch* b, int inst);
+/* n_steps batched steps of every instance, queued on `stream`. */
+int dsr_wator_batch_step(dsr_wator_batch* b, int n_steps, void* stream);
+/* The heap of an instance (for dsr_heap_hash, dsr_heap_dump, dsr_heap_stats). */
+int dsr_wator_batch_heap(dsr_wator_batch* b, int inst, dsr_heap** out);
+int dsr_wator_batch_kinds(dsr_wator_batch* b, int inst, void* kind_out_dev, void* stream);
+int dsr_wator_batch_group(dsr_wator_batch* b, dsr_group** out);
+int dsr_wator_batch_destroy(dsr_wator_batch* b);
 
 /* ---- n-body with merging collisions ------------------------------------
  * FP32. Types: 0 Body {id (int32), x, y, z, vx, vy, vz, m (float)}. One step:

@@ -36,9 +36,15 @@
 typedef unsigned long long dsr_u64;
 typedef dsr_u64 dsr_ref;
 #define DSR_NULL (~0ull)
+#ifndef DSR_SPIN_CAP
 #define DSR_SPIN_CAP (1u << 16)  /* set/clear retries before DSR_ERR_RETRY (about 70 ms with backoff) */
+#endif
+#ifndef DSR_FIND_CAP
 #define DSR_FIND_CAP 4096u       /* find-and-clear attempts */
+#endif
+#ifndef DSR_ALLOC_CAP
 #define DSR_ALLOC_CAP 4096u      /* allocation attempts before DSR_ERR_RETRY */
+#endif
 #define DSR_CTR_SLOTS 256u       /* event-counter rows (indexed by SM id) */
 #define DSR_SLOW_WAITS 64u       /* rounds a leader may wait for another initialisation */
 
@@ -63,6 +69,7 @@ struct dsr_dev_heap {
     uint32_t* R_done;     /* CTAs of the current method kernel that finished */
     dsr_u64* ctr;         /* [DSR_CTR_SLOTS][4] event counters, one row per SM */
     uint32_t* slow;       /* [DSR_MAX_TYPES] slow-path block initialisations in flight */
+    dsr_u64* dbg;         /* first failed device check (code << 48 | value), checked builds only */
     uint32_t slow_max;    /* at most this many in flight per type before leaders wait */
     dsr_u64 M;
     uint32_t block_bytes;
@@ -86,6 +93,47 @@ __device__ __forceinline__ dsr_u64 dsr_ld_relaxed(const dsr_u64* p) {
     dsr_u64 v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+/* 64-bit atomics with acquire/release ordering (PTX memory model), used where
+ * a block's object bitmap publishes or guards its type byte. */
+__device__ __forceinline__ dsr_u64 dsr_atom_and_acq_rel(dsr_u64* p, dsr_u64 v) {
+    dsr_u64 old;
+    asm volatile("atom.acq_rel.gpu.global.and.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ dsr_u64 dsr_atom_cas_acq_rel(dsr_u64* p, dsr_u64 cmp, dsr_u64 v) {
+    dsr_u64 old;
+    asm volatile("atom.acq_rel.gpu.global.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "l"(p), "l"(cmp), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void dsr_atom_exch_release(dsr_u64* p, dsr_u64 v) {
+    dsr_u64 old;
+    asm volatile("atom.release.gpu.global.exch.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    (void)old;
+}
+
+/* Device self-checks, compiled in with -DDSR_DEVICE_CHECKS: a failed check
+ * sets DSR_ERR_CHECK, records the first failure (code << 48 | value) and
+ * returns false so that the caller skips the access. Without the macro every
+ * check is true and costs nothing. */
+#define DSR_ERR_CHECK 32u
+__device__ __forceinline__ bool dsr_check(bool ok, uint32_t* err, dsr_u64* dbg, unsigned code, dsr_u64 value) {
+#ifdef DSR_DEVICE_CHECKS
+    if (!ok) {
+        atomicOr(err, DSR_ERR_CHECK);
+        atomicCAS(dbg, 0ull, ((dsr_u64)code << 48) | (value & 0xFFFFFFFFFFFFull));
+        return false;
+    }
+    return true;
+#else
+    (void)ok;
+    (void)err;
+    (void)dbg;
+    (void)code;
+    (void)value;
+    return true;
+#endif
 }
 
 __device__ __forceinline__ unsigned dsr_lane() {
@@ -252,9 +300,8 @@ __device__ inline void dsr_release(const dsr_dev_heap& H, int T, dsr_u64 b, dsr_
         if (prev == 0) dsr_hb_set(H.active_bm[T], b, true, H.err);
         const dsr_u64 v = H.valid[T];
         if ((prev | bits) != v) return;
-        if (atomicCAS(H.obj + b, v, 0ull) != v) return;
-        __threadfence();
-        const int T2 = dsr_block_type(H, b);
+        if (dsr_atom_cas_acq_rel(H.obj + b, v, 0ull) != v) return;
+        const int T2 = dsr_block_type(H, b);  // ordered after the acquiring CAS
         dsr_hb_clear(H.active_bm[T2], b, true, H.err);
         if (H.valid[T2] == v) {
             dsr_hb_clear(H.alloc_bm[T2], b, true, H.err);
@@ -286,8 +333,7 @@ __device__ inline dsr_grab dsr_init_block(const dsr_dev_heap& H, int T, int k, u
     const dsr_u64 want = take >= 64 ? ~0ull : ((1ull << take) - 1);
     const dsr_u64 rest = H.valid[T] & ~want;
     H.btype[b] = (uint8_t)T;
-    __threadfence();
-    atomicExch(H.obj + b, rest);
+    dsr_atom_exch_release(H.obj + b, rest);  // publishes the type with the bitmap
     dsr_count(H.ctr, DSR_CTR_BLOCKS, 1);
     dsr_hb_set(H.alloc_bm[T], (dsr_u64)b, true, H.err);
     if (rest) dsr_hb_set(H.active_bm[T], (dsr_u64)b, true, H.err);
@@ -335,19 +381,30 @@ __device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsi
             dsr_backoff(a + 9);
             continue;
         }
+        // Take the lowest free slots of a snapshot; while the block still has
+        // free slots (as the atomic's return value shows) and more are
+        // wanted, take those too, without searching again.
         dsr_u64* w = H.obj + b;
-        const dsr_u64 snap = dsr_ld_relaxed(w);
+        dsr_u64 snap = dsr_ld_relaxed(w);
         if (snap == 0) {
             dsr_backoff(a);
             continue;
         }
-        const dsr_u64 want = dsr_lowest_bits(snap, k);
-        const dsr_u64 prev = atomicAnd(w, ~want);
-        const dsr_u64 got = prev & want;
+        dsr_u64 got = 0;
+        bool emptied = false;
+        for (int r = 0; r < 64 && snap; ++r) {
+            const dsr_u64 want = dsr_lowest_bits(snap, k - __popcll(got));
+            const dsr_u64 prev = dsr_atom_and_acq_rel(w, ~want);
+            got |= prev & want;
+            snap = prev & ~want;
+            emptied = prev != 0 && snap == 0;  // this atomic left no free slot
+            if (__popcll(got) >= k) break;
+        }
         if (!got) continue;
-        __threadfence();
+        // The acquire above orders this read after the atomic: while this
+        // call holds slots of the block, its type cannot change.
         const int T2 = dsr_block_type(H, (dsr_u64)b);
-        if ((prev & ~want) == 0) dsr_hb_clear(H.active_bm[T2], (dsr_u64)b, true, H.err);
+        if (emptied) dsr_hb_clear(H.active_bm[T2], (dsr_u64)b, true, H.err);
         if (T2 != T) {
             // Stale hint: the block was reclaimed and reused for another type.
             dsr_release(H, T2, (dsr_u64)b, got);
@@ -362,15 +419,25 @@ __device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsi
 /* public device API                                                         */
 /* ------------------------------------------------------------------------ */
 
-/* new T: callable by any subset of a warp's lanes, with any mix of types.
- * Lanes asking for the same type are served by one leader (allocation
- * request coalescing, Section 2.4): it reserves slots for all of them, in as
- * few atomics as the free slots allow, and hands them out by shuffle.
- * Returns DSR_NULL (and sets DSR_ERR_OOM or DSR_ERR_RETRY) on failure. The
- * new object's fields are not initialised. */
+/* Key that identifies a heap among the lanes of a warp: the address of its
+ * object bitmaps (256-byte aligned, so the low bits are free for a type id).
+ * Lanes that meet at one call site may come from different iterations of a
+ * kernel's loop (independent thread scheduling lets them drift apart and
+ * converge again) and so may work on different heaps; aggregation must only
+ * combine lanes of the same heap. */
+__device__ __forceinline__ dsr_u64 dsr_heap_key(const dsr_dev_heap& H) {
+    return (dsr_u64)reinterpret_cast<uintptr_t>(H.obj);
+}
+
+/* new T: callable by any subset of a warp's lanes, with any mix of heaps and
+ * types. Lanes asking for the same type of the same heap are served by one
+ * leader (allocation request coalescing, Section 2.4): it reserves slots for
+ * all of them, in as few atomics as the free slots allow, and hands them out
+ * by shuffle. Returns DSR_NULL (and sets DSR_ERR_OOM or DSR_ERR_RETRY) on
+ * failure. The new object's fields are not initialised. */
 __device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
     const unsigned act = __activemask();
-    const unsigned peers = __match_any_sync(act, T);
+    const unsigned peers = __match_any_sync(act, dsr_heap_key(H) | (dsr_u64)T);
     const unsigned lane = dsr_lane();
     const int leader = __ffs(peers) - 1;
     const int rank = __popc(peers & ((1u << lane) - 1));
@@ -378,6 +445,8 @@ __device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
     const unsigned hint = (blockIdx.x * 0x9E3779B1u) ^ ((threadIdx.x >> 5) * 0x85EBCA77u) ^ (unsigned)T;
     dsr_ref mine = DSR_NULL;
     int served = 0;
+    // Each round the leader takes as many slots as the block it finds (or a
+    // new block) offers, until the group is served.
     while (served < need) {
         dsr_u64 bid = 0, bits = 0;
         uint32_t st = 0;
@@ -400,15 +469,16 @@ __device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
     return mine;
 }
 
-/* delete: callable by any subset of a warp's lanes. Lanes deleting objects
- * of the same block are combined into one atomicOr by a leader. DSR_NULL is
- * ignored; a handle outside the heap sets DSR_ERR_BAD_HANDLE. */
+/* delete: callable by any subset of a warp's lanes, with any mix of heaps.
+ * Lanes deleting objects of the same block of the same heap are combined
+ * into one atomicOr by a leader. DSR_NULL is ignored; a handle outside the
+ * heap sets DSR_ERR_BAD_HANDLE. */
 __device__ inline void dsr_delete(const dsr_dev_heap& H, dsr_ref r) {
     if (r == DSR_NULL) return;
     const unsigned act = __activemask();
     const dsr_u64 bid = r >> 6;
     const unsigned slot = (unsigned)(r & 63);
-    const unsigned peers = __match_any_sync(act, bid);
+    const unsigned peers = __match_any_sync(act, bid) & __match_any_sync(act, dsr_heap_key(H));
     const unsigned lane = dsr_lane();
     const unsigned lo = __reduce_or_sync(peers, slot < 32 ? (1u << slot) : 0u);
     const unsigned hi = __reduce_or_sync(peers, slot >= 32 ? (1u << (slot - 32)) : 0u);
@@ -430,6 +500,11 @@ __device__ inline void dsr_delete(const dsr_dev_heap& H, dsr_ref r) {
  * array offset + slot * field size. Consecutive slots are adjacent. */
 template <class F>
 __device__ __forceinline__ F* dsr_field(const dsr_dev_heap& H, int T, dsr_ref r, int f) {
+#ifdef DSR_DEVICE_CHECKS
+    // a bad handle is redirected to scratch words next to the check record
+    if (!dsr_check((r >> 6) < H.M && (r & 63) < H.cap[T], H.err, H.dbg, 11, r))
+        return reinterpret_cast<F*>(H.dbg + 1);
+#endif
     return reinterpret_cast<F*>(H.data + (r >> 6) * H.block_bytes + H.foff[T][f]) + (r & 63);
 }
 
@@ -486,9 +561,80 @@ __global__ void dsr_doall_kernel(const __grid_constant__ dsr_dev_heap H, int T,
     for (dsr_u64 g = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
         const dsr_u64 i = g >> sh;
         const unsigned s = (unsigned)(g & ((1u << sh) - 1));
-        if ((H.R_mask[i] >> s) & 1ull) Method::run(H, T, args, ((dsr_u64)H.R_bid[i] << 6) | s);
+        if (((H.R_mask[i] >> s) & 1ull) && dsr_check(H.R_bid[i] < H.M, H.err, H.dbg, 10, i))
+            Method::run(H, T, args, ((dsr_u64)H.R_bid[i] << 6) | s);
     }
     if (dsr_doall_finish(H)) dsr_call_finish<Method>(H, T, args, 0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* heap groups: one do-all over many heaps                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Device view of a heap group (dsr_group_* in dsr.h): the device views of its
+ * heaps, the chunk table that maps each run of 256 block ids to its heap,
+ * and the group's block list R (heap index, block id, occupied-slot
+ * snapshot). */
+struct dsr_group_dev {
+    const dsr_dev_heap* heaps;  /* [max_heaps] */
+    const uint32_t* chunk_heap; /* [n_chunks] heap of each chunk */
+    const uint32_t* chunk_base; /* [n_chunks] first block id of each chunk */
+    uint32_t n_chunks;
+    uint32_t n_slots;           /* heap indices in use are below this */
+    uint32_t* R_heap;
+    uint32_t* R_bid;
+    dsr_u64* R_mask;
+    uint32_t* R_count;
+    uint32_t* R_done;
+    dsr_u64 R_cap;              /* entries R can hold */
+    uint32_t* err;              /* group-level check failures (checked builds) */
+    dsr_u64* dbg;
+};
+
+/* Method kernel of a group do-all over type T (all heaps of a group share
+ * their type descriptors and tuning, so the span is the same for all). A
+ * group method is a type with
+ *   struct Args;
+ *   static __device__ void run(const dsr_dev_heap&, int T, const Args&, dsr_ref self, uint32_t heap);
+ *   optionally static __device__ void finish_group(const dsr_group_dev&, int T, const Args&);
+ * finish_group runs in every thread of the last CTA to finish, after every
+ * object has been visited. */
+template <class M>
+__device__ __forceinline__ auto dsr_call_finish_group(const dsr_group_dev& G, int T, const typename M::Args& a, int)
+    -> decltype(M::finish_group(G, T, a), void()) {
+    M::finish_group(G, T, a);
+}
+template <class M>
+__device__ __forceinline__ void dsr_call_finish_group(const dsr_group_dev&, int, const typename M::Args&, long) {}
+
+template <class Method>
+__global__ void dsr_group_doall_kernel(const __grid_constant__ dsr_group_dev G, int T, unsigned sh,
+                                       const __grid_constant__ typename Method::Args args) {
+    __shared__ bool last;
+    const dsr_u64 total = (dsr_u64)(*(volatile uint32_t*)G.R_count) << sh;
+    const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
+    for (dsr_u64 g = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        const dsr_u64 i = g >> sh;
+        const unsigned s = (unsigned)(g & ((1u << sh) - 1));
+        if ((G.R_mask[i] >> s) & 1ull) {
+            const uint32_t h = G.R_heap[i];
+            if (dsr_check(h < G.n_slots, G.err, G.dbg, 3, i) &&
+                dsr_check(G.R_bid[i] < G.heaps[h].M, G.err, G.dbg, 4, i))
+                Method::run(G.heaps[h], T, args, ((dsr_u64)G.R_bid[i] << 6) | s, h);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(G.R_done, 1u) == gridDim.x - 1;
+        if (last) {
+            *(volatile uint32_t*)G.R_count = 0;
+            *(volatile uint32_t*)G.R_done = 0;
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    if (last) dsr_call_finish_group<Method>(G, T, args, 0);
 }
 
 #endif /* __CUDACC__ */

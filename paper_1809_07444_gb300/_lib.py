@@ -7,7 +7,8 @@ import ctypes as C
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libdsr.so")
+# DSR_LIBRARY=check selects the build with device self-checks (libdsr_check.so)
+LIB_PATH = os.path.join(_PKG, "libdsr_check.so" if os.environ.get("DSR_LIBRARY") == "check" else "libdsr.so")
 
 MAX_TYPES = 8
 MAX_FIELDS = 16
@@ -116,6 +117,33 @@ SIGNATURES = {
     "dsr_nbody_merge_log": (_i, [_vp, C.POINTER(_vp), C.POINTER(_vp)]),
     "dsr_nbody_destroy": (_i, [_vp]),
     "dsr_nbody_step_noalloc": (_i, [_vp, C.POINTER(NBodyParams), _i, _u64, _vp, _u64, _vp, _vp]),
+    "dsr_group_create": (_i, [C.POINTER(TypeDesc), _i, _vp, _sz, _i, C.POINTER(Tuning), _vp, C.POINTER(_vp)]),
+    "dsr_group_destroy": (_i, [_vp]),
+    "dsr_group_add_heap": (_i, [_vp, _u64, _sz, _vp, C.POINTER(_i), C.POINTER(_vp), C.POINTER(_vp)]),
+    "dsr_group_remove_heap": (_i, [_vp, _i]),
+    "dsr_group_heap_bytes": (_i, [_vp, _u64, _sz, C.POINTER(_sz)]),
+    "dsr_group_free_bytes": (_i, [_vp, C.POINTER(_sz), C.POINTER(_sz)]),
+    "dsr_group_heap_count": (_i, [_vp]),
+    "dsr_group_parallel_do": (_i, [_vp, _i, _i, _vp, _sz, _vp]),
+    "dsr_group_check_record": (_i, [_vp, C.POINTER(_u32), C.POINTER(_u64)]),
+    "dsr_heap_check_record": (_i, [_vp, C.POINTER(_u32), C.POINTER(_u64)]),
+    "dsr_wator_batch_create": (_i, [_vp, _sz, _i, C.POINTER(Tuning), _vp, C.POINTER(_vp)]),
+    "dsr_wator_batch_instance_bytes": (_i, [_vp, _i, _i, _u64, C.POINTER(_sz)]),
+    "dsr_wator_batch_add": (_i, [_vp, C.POINTER(WatorParams), _u64, _vp, _vp, C.POINTER(_i)]),
+    "dsr_wator_batch_remove": (_i, [_vp, _i]),
+    "dsr_wator_batch_step": (_i, [_vp, _i, _vp]),
+    "dsr_wator_batch_heap": (_i, [_vp, _i, C.POINTER(_vp)]),
+    "dsr_wator_batch_kinds": (_i, [_vp, _i, _vp, _vp]),
+    "dsr_wator_batch_group": (_i, [_vp, C.POINTER(_vp)]),
+    "dsr_wator_batch_destroy": (_i, [_vp]),
+    "dsr_gol_batch_create": (_i, [_vp, _sz, _i, C.POINTER(Tuning), _vp, C.POINTER(_vp)]),
+    "dsr_gol_batch_instance_bytes": (_i, [_vp, _i, _i, _u64, C.POINTER(_sz)]),
+    "dsr_gol_batch_add": (_i, [_vp, _i, _i, _u64, _vp, _vp, C.POINTER(_i)]),
+    "dsr_gol_batch_remove": (_i, [_vp, _i]),
+    "dsr_gol_batch_step": (_i, [_vp, _i, _vp]),
+    "dsr_gol_batch_heap": (_i, [_vp, _i, C.POINTER(_vp)]),
+    "dsr_gol_batch_group": (_i, [_vp, C.POINTER(_vp)]),
+    "dsr_gol_batch_destroy": (_i, [_vp]),
 }
 
 _lib = None

@@ -115,6 +115,173 @@ class Wator:
         return out.cpu().numpy().reshape(self.H, self.W)
 
 
+def _heap_base(lib, handle):
+    """Device address of a heap's arena (its device view starts with the data pointer)."""
+    n = lib.dsr_dev_heap_size()
+    buf = (C.c_uint8 * n)()
+    L.check(lib.dsr_heap_device_view(handle, buf, n), "dsr_heap_device_view")
+    data = C.c_uint64.from_buffer(buf, 0).value
+    lay = L.Layout()
+    L.check(lib.dsr_heap_layout(handle, C.byref(lay)), "dsr_heap_layout")
+    return data - lay.off_data
+
+
+class WatorBatch:
+    """Many wa-tor instances in one arena, stepped together by graph-captured group do-alls."""
+
+    def __init__(self, arena_bytes, max_instances=256, tuning=None, stream=None):
+        from .heap import _tuning
+        self.lib = L.load()
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+        tun = _tuning(tuning)
+        h = C.c_void_p()
+        L.check(self.lib.dsr_wator_batch_create(C.c_void_p(self.arena.data_ptr()), int(arena_bytes), max_instances,
+                                                C.byref(tun) if tun else None, _stream_ptr(stream), C.byref(h)),
+                "dsr_wator_batch_create")
+        self.handle = h
+        self.inst = {}  # slot -> (W, H, params)
+        self._kinds = {}
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.dsr_wator_batch_destroy(self.handle)
+            self.handle = None
+
+    @staticmethod
+    def blocks_for(W, H):
+        return _blocks_for(W * H, [48])
+
+    def instance_bytes(self, W, H, n_blocks=None):
+        out = C.c_size_t(0)
+        L.check(self.lib.dsr_wator_batch_instance_bytes(self.handle, W, H, n_blocks or self.blocks_for(W, H),
+                                                        C.byref(out)), "dsr_wator_batch_instance_bytes")
+        return int(out.value)
+
+    def add(self, W, H, kind0, seed, fish_breed=3, shark_breed=10, shark_energy0=5, shark_gain=3, n_blocks=None,
+            stream=None):
+        """Add an instance; returns its slot, or None when the arena has no room."""
+        k0 = torch.as_tensor(np.ascontiguousarray(kind0, dtype=np.uint8).reshape(-1)).cuda()
+        p = L.WatorParams(W, H, seed, fish_breed, shark_breed, shark_energy0, shark_gain)
+        slot = C.c_int(-1)
+        rc = self.lib.dsr_wator_batch_add(self.handle, C.byref(p), n_blocks or self.blocks_for(W, H),
+                                          C.c_void_p(k0.data_ptr()), _stream_ptr(stream), C.byref(slot))
+        if rc == L.E_OOM:
+            return None
+        L.check(rc, "dsr_wator_batch_add")
+        self.inst[slot.value] = (W, H, p)
+        return slot.value
+
+    def remove(self, slot):
+        torch.cuda.synchronize()
+        L.check(self.lib.dsr_wator_batch_remove(self.handle, slot), "dsr_wator_batch_remove")
+        del self.inst[slot]
+
+    def step(self, n=1, stream=None):
+        L.check(self.lib.dsr_wator_batch_step(self.handle, n, _stream_ptr(stream)), "dsr_wator_batch_step")
+
+    def heap(self, slot):
+        h = C.c_void_p()
+        L.check(self.lib.dsr_wator_batch_heap(self.handle, slot, C.byref(h)), "dsr_wator_batch_heap")
+        off = _heap_base(self.lib, h) - self.arena.data_ptr()
+        return Heap.view(h, WATOR_TYPES, self.arena[off:], names=["Fish", "Shark"])
+
+    def hash(self, slot):
+        hp = self.heap(slot)
+        return hp.hash(0), hp.hash(1)
+
+    def dump(self, slot):
+        hp = self.heap(slot)
+        f, _ = hp.dump(0)
+        s, _ = hp.dump(1)
+        return _sorted_rows(f.view(np.int32)), _sorted_rows(s.view(np.int32))
+
+    def counts(self, slot):
+        st = self.heap(slot).stats()
+        return st["live_objects"][0], st["live_objects"][1]
+
+    def grid(self, slot):
+        W, H, _ = self.inst[slot]
+        out = torch.empty(W * H, dtype=torch.uint8, device="cuda")
+        L.check(self.lib.dsr_wator_batch_kinds(self.handle, slot, C.c_void_p(out.data_ptr()), _stream_ptr()),
+                "dsr_wator_batch_kinds")
+        return out.cpu().numpy().reshape(H, W)
+
+    def free_bytes(self):
+        g = C.c_void_p()
+        L.check(self.lib.dsr_wator_batch_group(self.handle, C.byref(g)), "dsr_wator_batch_group")
+        t, l = C.c_size_t(0), C.c_size_t(0)
+        L.check(self.lib.dsr_group_free_bytes(g, C.byref(t), C.byref(l)), "dsr_group_free_bytes")
+        return int(t.value), int(l.value)
+
+
+class GolBatch:
+    """Many game-of-life instances in one arena, stepped together by graph-captured group do-alls."""
+
+    def __init__(self, arena_bytes, max_instances=256, tuning=None, stream=None):
+        from .heap import _tuning
+        self.lib = L.load()
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+        tun = _tuning(tuning)
+        h = C.c_void_p()
+        L.check(self.lib.dsr_gol_batch_create(C.c_void_p(self.arena.data_ptr()), int(arena_bytes), max_instances,
+                                              C.byref(tun) if tun else None, _stream_ptr(stream), C.byref(h)),
+                "dsr_gol_batch_create")
+        self.handle = h
+        self.inst = {}
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.dsr_gol_batch_destroy(self.handle)
+            self.handle = None
+
+    @staticmethod
+    def blocks_for(W, H):
+        return _blocks_for(W * H, [42, 64])
+
+    def instance_bytes(self, W, H, n_blocks=None):
+        out = C.c_size_t(0)
+        L.check(self.lib.dsr_gol_batch_instance_bytes(self.handle, W, H, n_blocks or self.blocks_for(W, H),
+                                                      C.byref(out)), "dsr_gol_batch_instance_bytes")
+        return int(out.value)
+
+    def add(self, W, H, alive0, n_blocks=None, stream=None):
+        """Add an instance; returns its slot, or None when the arena has no room."""
+        a0 = torch.as_tensor(np.ascontiguousarray(alive0, dtype=np.uint8).reshape(-1)).cuda()
+        slot = C.c_int(-1)
+        rc = self.lib.dsr_gol_batch_add(self.handle, W, H, n_blocks or self.blocks_for(W, H),
+                                        C.c_void_p(a0.data_ptr()), _stream_ptr(stream), C.byref(slot))
+        if rc == L.E_OOM:
+            return None
+        L.check(rc, "dsr_gol_batch_add")
+        self.inst[slot.value] = (W, H)
+        return slot.value
+
+    def remove(self, slot):
+        torch.cuda.synchronize()
+        L.check(self.lib.dsr_gol_batch_remove(self.handle, slot), "dsr_gol_batch_remove")
+        del self.inst[slot]
+
+    def step(self, n=1, stream=None):
+        L.check(self.lib.dsr_gol_batch_step(self.handle, n, _stream_ptr(stream)), "dsr_gol_batch_step")
+
+    def heap(self, slot):
+        h = C.c_void_p()
+        L.check(self.lib.dsr_gol_batch_heap(self.handle, slot, C.byref(h)), "dsr_gol_batch_heap")
+        off = _heap_base(self.lib, h) - self.arena.data_ptr()
+        return Heap.view(h, GOL_TYPES, self.arena[off:], names=["Cell", "Alive"])
+
+    def hash(self, slot):
+        hp = self.heap(slot)
+        return hp.hash(0), hp.hash(1)
+
+    def free_bytes(self):
+        g = C.c_void_p()
+        L.check(self.lib.dsr_gol_batch_group(self.handle, C.byref(g)), "dsr_gol_batch_group")
+        t, l = C.c_size_t(0), C.c_size_t(0)
+        L.check(self.lib.dsr_group_free_bytes(g, C.byref(t), C.byref(l)), "dsr_group_free_bytes")
+        return int(t.value), int(l.value)
+
+
 NBODY_TYPES = [[4] * 8]  # Body {id, x, y, z, vx, vy, vz, m}
 
 

@@ -178,3 +178,178 @@ int dsr__gol_method(dsr_heap* h, int type, int method, const void* args, size_t 
             return DSR_E_INVALID;
     }
 }
+
+// ===========================================================================
+// batched form: many game-of-life instances in one heap group
+// ===========================================================================
+#include "dsr_group.cuh"
+
+namespace {
+struct GolBatchArgs {
+    const GolArgs* table;  // slot -> instance view (cell_ref == nullptr: unused slot)
+};
+struct GCount {
+    typedef GolBatchArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int T, const Args& a, dsr_ref s, uint32_t h) {
+        MCount::run(H, T, a.table[h], s);
+    }
+};
+struct GDie {
+    typedef GolBatchArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int T, const Args& a, dsr_ref s, uint32_t h) {
+        MDie::run(H, T, a.table[h], s);
+    }
+};
+struct GBirth {
+    typedef GolBatchArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int T, const Args& a, dsr_ref s, uint32_t h) {
+        MBirth::run(H, T, a.table[h], s);
+    }
+};
+size_t gol_table_bytes(int n) { return ((size_t)n * sizeof(GolArgs) + 1023) / 1024 * 1024; }
+}  // namespace
+
+struct dsr_gol_batch {
+    dsr_group* group;
+    GolArgs* table_d;
+    std::vector<GolArgs> table_h;
+    cudaStream_t capture;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t exec_epoch = ~0ull;
+};
+
+extern "C" int dsr_gol_batch_create(void* arena_dev, size_t arena_bytes, int max_instances, const dsr_tuning* tune,
+                                    void* stream, dsr_gol_batch** out) {
+    if (!arena_dev || !out || max_instances < 1 || (reinterpret_cast<uintptr_t>(arena_dev) & 255)) return DSR_E_INVALID;
+    const size_t tb = gol_table_bytes(max_instances);
+    if (arena_bytes <= tb) return DSR_E_OOM;
+    dsr_type_desc types[2];
+    dsr_gol_types(types);
+    dsr_gol_batch* b = new dsr_gol_batch;
+    int rc = dsr_group_create(types, 2, static_cast<uint8_t*>(arena_dev) + tb, arena_bytes - tb, max_instances, tune,
+                              stream, &b->group);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    b->table_d = static_cast<GolArgs*>(arena_dev);
+    b->table_h.assign(max_instances, GolArgs{nullptr, 0, 0});
+    cudaError_t e = cudaMemsetAsync(b->table_d, 0, tb, dsr__stream(stream));
+    if (!e) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_gol_batch_create");
+        dsr_group_destroy(b->group);
+        delete b;
+        return DSR_E_CUDA;
+    }
+    *out = b;
+    return DSR_OK;
+}
+
+extern "C" int dsr_gol_batch_instance_bytes(const dsr_gol_batch* b, int W, int H, uint64_t n_blocks, size_t* out) {
+    size_t ws;
+    if (!b || !out || dsr_gol_workspace_bytes(W, H, &ws)) return DSR_E_INVALID;
+    return dsr_group_heap_bytes(b->group, n_blocks, ws, out);
+}
+
+extern "C" int dsr_gol_batch_add(dsr_gol_batch* b, int W, int H, uint64_t n_blocks, const void* alive0_dev,
+                                 void* stream, int* inst_out) {
+    size_t ws;
+    if (!b || !alive0_dev || !inst_out || n_blocks == 0 || dsr_gol_workspace_bytes(W, H, &ws)) return DSR_E_INVALID;
+    int slot = -1;
+    dsr_heap* heap = nullptr;
+    void* extra = nullptr;
+    int rc = dsr_group_add_heap(b->group, n_blocks, ws, stream, &slot, &heap, &extra);
+    if (rc) return rc;
+    cudaStream_t s = dsr__stream(stream);
+    const int n = W * H;
+    int ctas = (n + 255) / 256;
+    if (ctas > heap->sm_count * 8) ctas = heap->sm_count * 8;
+    k_gol_init<<<ctas, 256, 0, s>>>(heap->dev, static_cast<const uint8_t*>(alive0_dev), static_cast<dsr_ref*>(extra),
+                                    W, H);
+    rc = dsr__check_launch("k_gol_init");
+    if (rc) return rc;
+    b->table_h[slot] = GolArgs{static_cast<const dsr_ref*>(extra), W, H};
+    cudaError_t e = cudaMemcpyAsync(b->table_d + slot, &b->table_h[slot], sizeof(GolArgs), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_gol_batch_add");
+        return DSR_E_CUDA;
+    }
+    *inst_out = slot;
+    return DSR_OK;
+}
+
+extern "C" int dsr_gol_batch_remove(dsr_gol_batch* b, int inst) {
+    if (!b || inst < 0 || inst >= (int)b->table_h.size() || !b->table_h[inst].cell_ref) return DSR_E_INVALID;
+    b->table_h[inst] = GolArgs{nullptr, 0, 0};
+    cudaError_t e = cudaMemcpy(b->table_d + inst, &b->table_h[inst], sizeof(GolArgs), cudaMemcpyHostToDevice);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_gol_batch_remove");
+        return DSR_E_CUDA;
+    }
+    return dsr_group_remove_heap(b->group, inst);
+}
+
+// One batched generation: three group do-alls (6 launches), captured into a
+// CUDA graph once per set of instances.
+extern "C" int dsr_gol_batch_step(dsr_gol_batch* b, int n_gen, void* stream) {
+    if (!b || n_gen < 0) return DSR_E_INVALID;
+    if (b->exec_epoch != b->group->epoch) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+        if (e) {
+            dsr__set_cuda_error(e, "dsr_gol_batch_step capture");
+            return DSR_E_CUDA;
+        }
+        GolBatchArgs a{b->table_d};
+        int rc = dsr__group_doall<GCount>(b->group, CELL, a, b->capture);
+        if (!rc) rc = dsr__group_doall<GDie>(b->group, ALIVE, a, b->capture);
+        if (!rc) rc = dsr__group_doall<GBirth>(b->group, CELL, a, b->capture);
+        e = cudaStreamEndCapture(b->capture, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (!e) e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e) {
+            dsr__set_cuda_error(e, "dsr_gol_batch_step instantiate");
+            b->exec = nullptr;
+            return DSR_E_CUDA;
+        }
+        b->exec_epoch = b->group->epoch;
+    }
+    cudaStream_t s = dsr__stream(stream);
+    for (int i = 0; i < n_gen; ++i) {
+        cudaError_t e = cudaGraphLaunch(b->exec, s);
+        if (e) {
+            dsr__set_cuda_error(e, "dsr_gol_batch_step launch");
+            return DSR_E_CUDA;
+        }
+    }
+    return DSR_OK;
+}
+
+extern "C" int dsr_gol_batch_heap(dsr_gol_batch* b, int inst, dsr_heap** out) {
+    if (!b || !out || inst < 0 || inst >= (int)b->table_h.size() || !b->table_h[inst].cell_ref) return DSR_E_INVALID;
+    *out = b->group->heaps[inst];
+    return DSR_OK;
+}
+
+extern "C" int dsr_gol_batch_group(dsr_gol_batch* b, dsr_group** out) {
+    if (!b || !out) return DSR_E_INVALID;
+    *out = b->group;
+    return DSR_OK;
+}
+
+extern "C" int dsr_gol_batch_destroy(dsr_gol_batch* b) {
+    if (!b) return DSR_E_INVALID;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    cudaStreamDestroy(b->capture);
+    dsr_group_destroy(b->group);
+    delete b;
+    return DSR_OK;
+}

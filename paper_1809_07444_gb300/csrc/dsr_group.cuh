@@ -1,0 +1,54 @@
+// Host-side internals of heap groups, shared by the group and the batched
+// applications.
+#pragma once
+
+#include <map>
+#include <vector>
+
+#include "dsr_internal.cuh"
+
+struct dsr_group {
+    uint8_t* arena;
+    size_t arena_bytes;
+    int max_heaps;
+    uint64_t max_chunks;
+    int n_types;
+    std::vector<dsr_type_desc> types;
+    std::vector<std::vector<int>> fields;
+    dsr_tuning tune;
+    int device;
+    int sm_count;
+    std::vector<dsr_heap*> heaps;          // slot -> heap (nullptr = free slot)
+    std::vector<size_t> offsets, sizes;    // slot -> range in the arena
+    std::vector<dsr_dev_heap> views;       // host copies of the device views
+    std::map<size_t, size_t> free_ranges;  // offset -> bytes
+    std::vector<uint32_t> chunk_heap_h, chunk_base_h;
+    uint32_t n_chunks = 0;
+    uint64_t epoch = 0;                    // bumped whenever the set of heaps changes
+    dsr_dev_heap* heaps_d;
+    uint32_t* chunk_heap_d;
+    uint32_t* chunk_base_d;
+    dsr_group_dev dev;
+};
+
+void dsr__group_launch_scan(const dsr_group* g, int type, cudaStream_t s);
+int dsr__group_grid(const dsr_group* g, const void* kernel, int threads);
+
+// Slots of a block of type T covered per listed block (log2): 5 for
+// capacities up to 32, else 6; the same for every heap of a group.
+inline unsigned dsr__group_span(const dsr_group* g, int type) {
+    dsr_layout L;
+    dsr_heap_plan(g->types.data(), g->n_types, 1, &g->tune, &L);
+    return L.capacity[type] <= 32 ? 5u : 6u;
+}
+
+// A group do-all: fused scan over every heap, then the method kernel.
+template <class M>
+int dsr__group_doall(dsr_group* g, int type, const typename M::Args& args, cudaStream_t s) {
+    if (type < 0 || type >= g->n_types) return DSR_E_INVALID;
+    dsr__group_launch_scan(g, type, s);
+    const int threads = g->tune.threads > 0 ? g->tune.threads : 256;
+    const int grid = dsr__group_grid(g, (const void*)dsr_group_doall_kernel<M>, threads);
+    dsr_group_doall_kernel<M><<<grid, threads, 0, s>>>(g->dev, type, dsr__group_span(g, type), args);
+    return dsr__check_launch("dsr_group_doall_kernel");
+}

@@ -302,7 +302,12 @@ static void build_dev_view(dsr_heap* h) {
     D.R_done = reinterpret_cast<uint32_t*>(a + DSR_HDR_RDONE);
     D.ctr = reinterpret_cast<dsr_u64*>(a + DSR_HDR_CTR);
     D.slow = reinterpret_cast<uint32_t*>(a + DSR_HDR_SLOW);
-    D.slow_max = (uint32_t)(h->sm_count > 0 ? h->sm_count : 1);
+    // At most one block initialisation in flight per SM per type, and no more
+    // than one per 64 blocks of the heap, so that a small heap is not carved
+    // into nearly empty blocks by a burst of concurrent leaders.
+    uint64_t sm = (uint64_t)(h->sm_count > 0 ? h->sm_count : 1), by_size = L.n_blocks / 64;
+    D.slow_max = (uint32_t)(by_size < 1 ? 1 : (by_size < sm ? by_size : sm));
+    D.dbg = reinterpret_cast<dsr_u64*>(a + DSR_HDR_DBG);
     D.R_mask = reinterpret_cast<dsr_u64*>(a + off_rmask(L));
     D.R_bid = reinterpret_cast<uint32_t*>(a + off_rbid(L));
     D.M = L.n_blocks;
@@ -466,6 +471,21 @@ extern "C" int dsr_heap_counters(dsr_heap* h, void* stream, uint64_t* out) {
         out[k] = 0;
         for (unsigned r = 0; r < DSR_CTR_SLOTS; ++r) out[k] += rows[r][k];
     }
+    return DSR_OK;
+}
+
+extern "C" int dsr_heap_check_record(dsr_heap* h, uint32_t* err_out, uint64_t* record_out) {
+    if (!h) return DSR_E_INVALID;
+    uint32_t e32 = 0;
+    dsr_u64 rec = 0;
+    cudaError_t e = cudaMemcpy(&e32, h->dev.err, 4, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(&rec, h->dev.dbg, 8, cudaMemcpyDeviceToHost);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_heap_check_record");
+        return DSR_E_CUDA;
+    }
+    if (err_out) *err_out = e32;
+    if (record_out) *record_out = rec;
     return DSR_OK;
 }
 

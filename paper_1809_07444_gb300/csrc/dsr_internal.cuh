@@ -28,6 +28,7 @@ struct dsr_heap {
 #define DSR_HDR_RDONE 12u
 #define DSR_HDR_STATS 256u  // dsr_u64[1 + 3 * DSR_MAX_TYPES]
 #define DSR_HDR_SLOW 192u   // uint32[DSR_MAX_TYPES] slow paths in flight
+#define DSR_HDR_DBG 224u    // dsr_u64 first failed device check + 24 scratch bytes
 #define DSR_HDR_CTR 4096u   // dsr_u64[DSR_CTR_SLOTS][4] event counters
 
 void dsr__set_cuda_error(cudaError_t e, const char* where);
@@ -51,8 +52,15 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
     const int threads = h->tune.threads;
     int& grid = grid_cache[threads / 64];
     if (grid == 0 || h->tune.ctas_per_sm > 0) grid = dsr__persistent_grid(h, (const void*)dsr_doall_kernel<M>, threads);
-    int g = grid;
+    // Without an explicit CTAs-per-SM setting the grid is 16 times what fits
+    // on the GPU at once (capped by the work a do-all over this heap can
+    // list): CTAs whose slots hold slow objects (allocation, long chains of
+    // dependent loads) then do not hold up the rest, which finish and make
+    // room for further CTAs.
+    dsr_u64 g64 = (dsr_u64)grid * (h->tune.ctas_per_sm > 0 ? 1 : 16);
     const dsr_u64 cap_grid = (h->dev.M * 64 + threads - 1) / threads;
+    if (g64 > cap_grid) g64 = cap_grid;
+    int g = (int)g64;
     if ((dsr_u64)g > cap_grid) g = (int)cap_grid;
     if (g < 1) g = 1;
     dsr_doall_kernel<M><<<g, threads, 0, s>>>(h->dev, type, args);

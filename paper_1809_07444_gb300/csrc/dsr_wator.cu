@@ -1,8 +1,10 @@
 // Wa-Tor predator-prey as an SMMO program (Fig. 6h): five do-alls per step
 // over Fish and Shark objects; births and deaths are device new/delete.
-// Rules are stated in dsr_apps.h.
+// Rules are stated in dsr_apps.h. The rules are written once, over a device
+// view of one instance; the plain form runs them as do-alls over one heap,
+// the batched form as group do-alls over the heaps of many instances.
 #include "dsr_apps.h"
-#include "dsr_internal.cuh"
+#include "dsr_group.cuh"
 
 namespace {
 enum { FISH = 0, SHARK = 1 };
@@ -10,17 +12,12 @@ enum { X = 0, Y = 1, TIMER = 2, ENERGY = 3 };
 enum : dsr_u64 { K_EMPTY = 0, K_FISH = 1, K_SHARK = 2 };
 constexpr uint32_t NO_MOVE = 0xFFFFFFFFu;
 
-// Workspace layout (byte offsets); grid and claim are uint64 per cell,
-// intent uint32 per cell, then the step counter.
-struct WatorWs {
-    dsr_u64* grid;    // 0 = empty, else (handle << 2) | kind
-    dsr_u64* claim;   // lowest claim key of the current phase
-    uint32_t* intent; // target chosen by the agent in this cell, or NO_MOVE
-    dsr_u64* step;    // device step counter
-};
-
-struct WatorArgs {
-    WatorWs ws;
+// Device view of one instance: its workspace and its parameters.
+struct WatorInst {
+    dsr_u64* grid;     // 0 = empty, else (handle << 2) | kind
+    dsr_u64* claim;    // lowest claim key of the current phase
+    uint32_t* intent;  // target chosen by the agent in this cell, or NO_MOVE
+    dsr_u64* step;     // device step counter (nullptr: unused batch slot)
     dsr_wator_params p;
 };
 
@@ -39,163 +36,231 @@ __device__ __forceinline__ void neighbours(uint32_t c, int W, int H, uint32_t nb
     nb[3] = (uint32_t)(y * W + (x == 0 ? W - 1 : x - 1));  // W
 }
 
-// F1: age, pick an empty neighbour, claim it.
-struct MFishChoose {
-    typedef WatorArgs Args;
-    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref self) {
-        const dsr_u64 t = *(volatile dsr_u64*)a.ws.step;
-        const int x = *dsr_field<int32_t>(H, FISH, self, X), y = *dsr_field<int32_t>(H, FISH, self, Y);
-        *dsr_field<int32_t>(H, FISH, self, TIMER) += 1;
-        const uint32_t c = (uint32_t)(y * a.p.W + x);
-        uint32_t nb[4], cand[4];
-        neighbours(c, a.p.W, a.p.H, nb);
-        int k = 0;
-#pragma unroll
-        for (int d = 0; d < 4; ++d)
-            if (a.ws.grid[nb[d]] == K_EMPTY) cand[k++] = nb[d];
-        uint32_t tgt = NO_MOVE;
-        if (k) {
-            tgt = cand[dsr_rand(a.p.seed, 0, t, c) % (dsr_u64)k];
-            atomicMin(a.ws.claim + tgt, claim_key(t, 0, c));
+// Checked builds only: the instance exists and c is one of its cells.
+__device__ __forceinline__ bool cell_ok(const dsr_dev_heap& H, const WatorInst& I, uint32_t c, unsigned code) {
+    return dsr_check(I.grid != nullptr && c < (uint32_t)I.p.W * (uint32_t)I.p.H, H.err, H.dbg, code, c);
+}
+
+// The k-th (0-based) set position among the low 4 bits of m, as a neighbour index.
+__device__ __forceinline__ int pick(unsigned m, unsigned k) {
+    for (int d = 0; d < 4; ++d)
+        if ((m >> d) & 1u) {
+            if (k == 0) return d;
+            --k;
         }
-        a.ws.intent[c] = tgt;
+    return 0;
+}
+
+// F1: age, pick an empty neighbour, claim it.
+__device__ __forceinline__ void fish_choose(const dsr_dev_heap& H, const WatorInst& I, dsr_ref self) {
+    const dsr_u64 t = *(volatile dsr_u64*)I.step;
+    const int x = *dsr_field<int32_t>(H, FISH, self, X), y = *dsr_field<int32_t>(H, FISH, self, Y);
+    *dsr_field<int32_t>(H, FISH, self, TIMER) += 1;
+    const uint32_t c = (uint32_t)(y * I.p.W + x);
+    if (!cell_ok(H, I, c, 6)) return;
+    uint32_t nb[4];
+    neighbours(c, I.p.W, I.p.H, nb);
+    unsigned m = 0;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) m |= (I.grid[nb[d]] == K_EMPTY ? 1u : 0u) << d;
+    uint32_t tgt = NO_MOVE;
+    if (m) {
+        tgt = nb[pick(m, (unsigned)(dsr_rand(I.p.seed, 0, t, c) % (dsr_u64)__popc(m)))];
+        atomicMin(I.claim + tgt, claim_key(t, 0, c));
     }
-};
+    I.intent[c] = tgt;
+}
 
 // F2: winners move and breed.
-struct MFishMove {
-    typedef WatorArgs Args;
-    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref self) {
-        const dsr_u64 t = *(volatile dsr_u64*)a.ws.step;
-        int32_t* px = dsr_field<int32_t>(H, FISH, self, X);
-        int32_t* py = dsr_field<int32_t>(H, FISH, self, Y);
-        const uint32_t c = (uint32_t)(*py * a.p.W + *px);
-        const uint32_t tgt = a.ws.intent[c];
-        if (tgt == NO_MOVE || a.ws.claim[tgt] != claim_key(t, 0, c)) return;
-        a.ws.grid[tgt] = (self << 2) | K_FISH;
-        *px = (int32_t)(tgt % (uint32_t)a.p.W);
-        *py = (int32_t)(tgt / (uint32_t)a.p.W);
-        int32_t* timer = dsr_field<int32_t>(H, FISH, self, TIMER);
-        dsr_u64 left = K_EMPTY;
-        if (*timer >= a.p.fish_breed) {
-            *timer = 0;
-            const dsr_ref n = dsr_new(H, FISH);
-            if (n != DSR_NULL) {
-                *dsr_field<int32_t>(H, FISH, n, X) = (int32_t)(c % (uint32_t)a.p.W);
-                *dsr_field<int32_t>(H, FISH, n, Y) = (int32_t)(c / (uint32_t)a.p.W);
-                *dsr_field<int32_t>(H, FISH, n, TIMER) = 0;
-                left = (n << 2) | K_FISH;
-            }
+__device__ __forceinline__ void fish_move(const dsr_dev_heap& H, const WatorInst& I, dsr_ref self) {
+    const dsr_u64 t = *(volatile dsr_u64*)I.step;
+    int32_t* px = dsr_field<int32_t>(H, FISH, self, X);
+    int32_t* py = dsr_field<int32_t>(H, FISH, self, Y);
+    const uint32_t c = (uint32_t)(*py * I.p.W + *px);
+    if (!cell_ok(H, I, c, 6)) return;
+    const uint32_t tgt = I.intent[c];
+    if (tgt != NO_MOVE && !cell_ok(H, I, tgt, 7)) return;
+    if (tgt == NO_MOVE || I.claim[tgt] != claim_key(t, 0, c)) return;
+    I.grid[tgt] = (self << 2) | K_FISH;
+    *px = (int32_t)(tgt % (uint32_t)I.p.W);
+    *py = (int32_t)(tgt / (uint32_t)I.p.W);
+    int32_t* timer = dsr_field<int32_t>(H, FISH, self, TIMER);
+    dsr_u64 left = K_EMPTY;
+    if (*timer >= I.p.fish_breed) {
+        *timer = 0;
+        const dsr_ref n = dsr_new(H, FISH);
+        if (n != DSR_NULL) {
+            *dsr_field<int32_t>(H, FISH, n, X) = (int32_t)(c % (uint32_t)I.p.W);
+            *dsr_field<int32_t>(H, FISH, n, Y) = (int32_t)(c / (uint32_t)I.p.W);
+            *dsr_field<int32_t>(H, FISH, n, TIMER) = 0;
+            left = (n << 2) | K_FISH;
         }
-        a.ws.grid[c] = left;
     }
-};
+    I.grid[c] = left;
+}
 
 // S0: starvation.
-struct MSharkStarve {
-    typedef WatorArgs Args;
-    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref self) {
-        int32_t* e = dsr_field<int32_t>(H, SHARK, self, ENERGY);
-        if (--*e > 0) return;
-        const int x = *dsr_field<int32_t>(H, SHARK, self, X), y = *dsr_field<int32_t>(H, SHARK, self, Y);
-        a.ws.grid[y * a.p.W + x] = K_EMPTY;
-        dsr_delete(H, self);
-    }
-};
+__device__ __forceinline__ void shark_starve(const dsr_dev_heap& H, const WatorInst& I, dsr_ref self) {
+    int32_t* e = dsr_field<int32_t>(H, SHARK, self, ENERGY);
+    if (--*e > 0) return;
+    const int x = *dsr_field<int32_t>(H, SHARK, self, X), y = *dsr_field<int32_t>(H, SHARK, self, Y);
+    if (cell_ok(H, I, (uint32_t)(y * I.p.W + x), 6)) I.grid[y * I.p.W + x] = K_EMPTY;
+    dsr_delete(H, self);
+}
 
 // S1: age, prefer a neighbouring fish, else an empty cell; claim it.
-struct MSharkChoose {
-    typedef WatorArgs Args;
-    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref self) {
-        const dsr_u64 t = *(volatile dsr_u64*)a.ws.step;
-        const int x = *dsr_field<int32_t>(H, SHARK, self, X), y = *dsr_field<int32_t>(H, SHARK, self, Y);
-        *dsr_field<int32_t>(H, SHARK, self, TIMER) += 1;
-        const uint32_t c = (uint32_t)(y * a.p.W + x);
-        uint32_t nb[4], fish[4], empty[4];
-        neighbours(c, a.p.W, a.p.H, nb);
-        int kf = 0, ke = 0;
+__device__ __forceinline__ void shark_choose(const dsr_dev_heap& H, const WatorInst& I, dsr_ref self) {
+    const dsr_u64 t = *(volatile dsr_u64*)I.step;
+    const int x = *dsr_field<int32_t>(H, SHARK, self, X), y = *dsr_field<int32_t>(H, SHARK, self, Y);
+    *dsr_field<int32_t>(H, SHARK, self, TIMER) += 1;
+    const uint32_t c = (uint32_t)(y * I.p.W + x);
+    if (!cell_ok(H, I, c, 6)) return;
+    uint32_t nb[4];
+    neighbours(c, I.p.W, I.p.H, nb);
+    unsigned mf = 0, me = 0;
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            const dsr_u64 g = a.ws.grid[nb[d]];
-            if ((g & 3) == K_FISH) fish[kf++] = nb[d];
-            else if (g == K_EMPTY) empty[ke++] = nb[d];
-        }
-        uint32_t tgt = NO_MOVE;
-        if (kf || ke) {
-            const dsr_u64 r = dsr_rand(a.p.seed, 1, t, c);
-            tgt = kf ? fish[r % (dsr_u64)kf] : empty[r % (dsr_u64)ke];
-            atomicMin(a.ws.claim + tgt, claim_key(t, 1, c));
-        }
-        a.ws.intent[c] = tgt;
+    for (int d = 0; d < 4; ++d) {
+        const dsr_u64 g = I.grid[nb[d]];
+        mf |= ((g & 3) == K_FISH ? 1u : 0u) << d;
+        me |= (g == K_EMPTY ? 1u : 0u) << d;
     }
+    const unsigned m = mf ? mf : me;
+    uint32_t tgt = NO_MOVE;
+    if (m) {
+        tgt = nb[pick(m, (unsigned)(dsr_rand(I.p.seed, 1, t, c) % (dsr_u64)__popc(m)))];
+        atomicMin(I.claim + tgt, claim_key(t, 1, c));
+    }
+    I.intent[c] = tgt;
+}
+
+// S2: winners move, eat and breed.
+__device__ __forceinline__ void shark_move(const dsr_dev_heap& H, const WatorInst& I, dsr_ref self) {
+    const dsr_u64 t = *(volatile dsr_u64*)I.step;
+    int32_t* px = dsr_field<int32_t>(H, SHARK, self, X);
+    int32_t* py = dsr_field<int32_t>(H, SHARK, self, Y);
+    const uint32_t c = (uint32_t)(*py * I.p.W + *px);
+    if (!cell_ok(H, I, c, 6)) return;
+    const uint32_t tgt = I.intent[c];
+    if (tgt != NO_MOVE && !cell_ok(H, I, tgt, 7)) return;
+    if (tgt == NO_MOVE || I.claim[tgt] != claim_key(t, 1, c)) return;
+    const dsr_u64 g = I.grid[tgt];
+    int32_t* energy = dsr_field<int32_t>(H, SHARK, self, ENERGY);
+    if ((g & 3) == K_FISH) {
+        dsr_delete(H, g >> 2);
+        *energy += I.p.shark_gain;
+    }
+    I.grid[tgt] = (self << 2) | K_SHARK;
+    *px = (int32_t)(tgt % (uint32_t)I.p.W);
+    *py = (int32_t)(tgt / (uint32_t)I.p.W);
+    int32_t* timer = dsr_field<int32_t>(H, SHARK, self, TIMER);
+    dsr_u64 left = K_EMPTY;
+    if (*timer >= I.p.shark_breed) {
+        *timer = 0;
+        const dsr_ref n = dsr_new(H, SHARK);
+        if (n != DSR_NULL) {
+            *dsr_field<int32_t>(H, SHARK, n, X) = (int32_t)(c % (uint32_t)I.p.W);
+            *dsr_field<int32_t>(H, SHARK, n, Y) = (int32_t)(c / (uint32_t)I.p.W);
+            *dsr_field<int32_t>(H, SHARK, n, TIMER) = 0;
+            *dsr_field<int32_t>(H, SHARK, n, ENERGY) = I.p.shark_energy0;
+            left = (n << 2) | K_SHARK;
+        }
+    }
+    I.grid[c] = left;
+}
+
+// ---- plain form: do-all methods over one heap ------------------------------
+struct MFishChoose {
+    typedef WatorInst Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s) { fish_choose(H, a, s); }
+};
+struct MFishMove {
+    typedef WatorInst Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s) { fish_move(H, a, s); }
+};
+struct MSharkStarve {
+    typedef WatorInst Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s) { shark_starve(H, a, s); }
+};
+struct MSharkChoose {
+    typedef WatorInst Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s) { shark_choose(H, a, s); }
+};
+// The last CTA of the last phase advances the step counter.
+struct MSharkMove {
+    typedef WatorInst Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s) { shark_move(H, a, s); }
+    static __device__ void finish(const dsr_dev_heap&, int, const Args& a) { *a.step += 1; }
 };
 
-// S2: winners move, eat and breed. The last CTA advances the step counter.
-struct MSharkMove {
-    typedef WatorArgs Args;
-    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref self) {
-        const dsr_u64 t = *(volatile dsr_u64*)a.ws.step;
-        int32_t* px = dsr_field<int32_t>(H, SHARK, self, X);
-        int32_t* py = dsr_field<int32_t>(H, SHARK, self, Y);
-        const uint32_t c = (uint32_t)(*py * a.p.W + *px);
-        const uint32_t tgt = a.ws.intent[c];
-        if (tgt == NO_MOVE || a.ws.claim[tgt] != claim_key(t, 1, c)) return;
-        const dsr_u64 g = a.ws.grid[tgt];
-        int32_t* energy = dsr_field<int32_t>(H, SHARK, self, ENERGY);
-        if ((g & 3) == K_FISH) {
-            dsr_delete(H, g >> 2);
-            *energy += a.p.shark_gain;
-        }
-        a.ws.grid[tgt] = (self << 2) | K_SHARK;
-        *px = (int32_t)(tgt % (uint32_t)a.p.W);
-        *py = (int32_t)(tgt / (uint32_t)a.p.W);
-        int32_t* timer = dsr_field<int32_t>(H, SHARK, self, TIMER);
-        dsr_u64 left = K_EMPTY;
-        if (*timer >= a.p.shark_breed) {
-            *timer = 0;
-            const dsr_ref n = dsr_new(H, SHARK);
-            if (n != DSR_NULL) {
-                *dsr_field<int32_t>(H, SHARK, n, X) = (int32_t)(c % (uint32_t)a.p.W);
-                *dsr_field<int32_t>(H, SHARK, n, Y) = (int32_t)(c / (uint32_t)a.p.W);
-                *dsr_field<int32_t>(H, SHARK, n, TIMER) = 0;
-                *dsr_field<int32_t>(H, SHARK, n, ENERGY) = a.p.shark_energy0;
-                left = (n << 2) | K_SHARK;
-            }
-        }
-        a.ws.grid[c] = left;
+// ---- batched form: group do-all methods over the heaps of many instances ----
+// Heap index h of a group is the instance slot; table[h] is its view.
+struct BatchArgs {
+    const WatorInst* table;
+};
+struct GFishChoose {
+    typedef BatchArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s, uint32_t h) {
+        fish_choose(H, a.table[h], s);
     }
-    static __device__ void finish(const dsr_dev_heap&, int, const Args& a) { *a.ws.step += 1; }
+};
+struct GFishMove {
+    typedef BatchArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s, uint32_t h) {
+        fish_move(H, a.table[h], s);
+    }
+};
+struct GSharkStarve {
+    typedef BatchArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s, uint32_t h) {
+        shark_starve(H, a.table[h], s);
+    }
+};
+struct GSharkChoose {
+    typedef BatchArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s, uint32_t h) {
+        shark_choose(H, a.table[h], s);
+    }
+};
+struct GSharkMove {
+    typedef BatchArgs Args;
+    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s, uint32_t h) {
+        shark_move(H, a.table[h], s);
+    }
+    // every instance in the batch advances one step
+    static __device__ void finish_group(const dsr_group_dev& G, int, const Args& a) {
+        for (uint32_t i = threadIdx.x; i < G.n_slots; i += blockDim.x)
+            if (a.table[i].step) *a.table[i].step += 1;
+    }
 };
 
 // One thread per cell: create the initial agents and clear the claim state.
-__global__ void k_wator_init(const __grid_constant__ dsr_dev_heap H, const uint8_t* kind0, WatorWs ws,
-                             dsr_wator_params p) {
-    const uint32_t n = (uint32_t)p.W * (uint32_t)p.H;
+__global__ void k_wator_init(const __grid_constant__ dsr_dev_heap H, const uint8_t* kind0, WatorInst I) {
+    const uint32_t n = (uint32_t)I.p.W * (uint32_t)I.p.H;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const uint8_t k = kind0[c];
         dsr_u64 g = K_EMPTY;
         if (k == 1) {
             const dsr_ref r = dsr_new(H, FISH);
             if (r != DSR_NULL) {
-                *dsr_field<int32_t>(H, FISH, r, X) = (int32_t)(c % (uint32_t)p.W);
-                *dsr_field<int32_t>(H, FISH, r, Y) = (int32_t)(c / (uint32_t)p.W);
+                *dsr_field<int32_t>(H, FISH, r, X) = (int32_t)(c % (uint32_t)I.p.W);
+                *dsr_field<int32_t>(H, FISH, r, Y) = (int32_t)(c / (uint32_t)I.p.W);
                 *dsr_field<int32_t>(H, FISH, r, TIMER) = 0;
                 g = (r << 2) | K_FISH;
             }
         } else if (k == 2) {
             const dsr_ref r = dsr_new(H, SHARK);
             if (r != DSR_NULL) {
-                *dsr_field<int32_t>(H, SHARK, r, X) = (int32_t)(c % (uint32_t)p.W);
-                *dsr_field<int32_t>(H, SHARK, r, Y) = (int32_t)(c / (uint32_t)p.W);
+                *dsr_field<int32_t>(H, SHARK, r, X) = (int32_t)(c % (uint32_t)I.p.W);
+                *dsr_field<int32_t>(H, SHARK, r, Y) = (int32_t)(c / (uint32_t)I.p.W);
                 *dsr_field<int32_t>(H, SHARK, r, TIMER) = 0;
-                *dsr_field<int32_t>(H, SHARK, r, ENERGY) = p.shark_energy0;
+                *dsr_field<int32_t>(H, SHARK, r, ENERGY) = I.p.shark_energy0;
                 g = (r << 2) | K_SHARK;
             }
         }
-        ws.grid[c] = g;
-        ws.claim[c] = ~0ull;
-        ws.intent[c] = NO_MOVE;
-        if (c == 0) *ws.step = 0;
+        I.grid[c] = g;
+        I.claim[c] = ~0ull;
+        I.intent[c] = NO_MOVE;
+        if (c == 0) *I.step = 0;
     }
 }
 
@@ -217,27 +282,52 @@ bool heap_matches(const dsr_heap* h) {
     return true;
 }
 
+bool params_ok(const dsr_wator_params* p) {
+    return p && p->W >= 3 && p->H >= 3 && (int64_t)p->W * p->H < (1ll << 31) && p->fish_breed >= 1 &&
+           p->shark_breed >= 1 && p->shark_energy0 >= 1 && p->shark_gain >= 0;
+}
+
 size_t ws_bytes(int W, int H) {
     const size_t n = (size_t)W * H;
     return ((n * 8 + 255) / 256 * 256) * 2 + (n * 4 + 255) / 256 * 256 + 256;
 }
 
-WatorWs carve(void* base, int W, int H) {
-    const size_t n = (size_t)W * H;
-    uint8_t* p = static_cast<uint8_t*>(base);
+WatorInst carve(void* base, const dsr_wator_params& p) {
+    const size_t n = (size_t)p.W * p.H;
+    uint8_t* b = static_cast<uint8_t*>(base);
     const size_t g = (n * 8 + 255) / 256 * 256, in = (n * 4 + 255) / 256 * 256;
-    WatorWs w;
-    w.grid = reinterpret_cast<dsr_u64*>(p);
-    w.claim = reinterpret_cast<dsr_u64*>(p + g);
-    w.intent = reinterpret_cast<uint32_t*>(p + 2 * g);
-    w.step = reinterpret_cast<dsr_u64*>(p + 2 * g + in);
+    WatorInst w;
+    w.grid = reinterpret_cast<dsr_u64*>(b);
+    w.claim = reinterpret_cast<dsr_u64*>(b + g);
+    w.intent = reinterpret_cast<uint32_t*>(b + 2 * g);
+    w.step = reinterpret_cast<dsr_u64*>(b + 2 * g + in);
+    w.p = p;
     return w;
+}
+
+int launch_init(const dsr_heap* heap, const WatorInst& I, const void* kind0_dev, cudaStream_t s) {
+    const uint32_t n = (uint32_t)I.p.W * (uint32_t)I.p.H;
+    unsigned ctas = (n + 255) / 256;
+    if (ctas > (unsigned)heap->sm_count * 8) ctas = (unsigned)heap->sm_count * 8;
+    k_wator_init<<<ctas, 256, 0, s>>>(heap->dev, static_cast<const uint8_t*>(kind0_dev), I);
+    return dsr__check_launch("k_wator_init");
+}
+
+int launch_kinds(const dsr_heap* heap, const WatorInst& I, void* out, cudaStream_t s) {
+    const uint32_t n = (uint32_t)I.p.W * (uint32_t)I.p.H;
+    unsigned ctas = (n + 255) / 256;
+    if (ctas > (unsigned)heap->sm_count * 8) ctas = (unsigned)heap->sm_count * 8;
+    k_wator_kinds<<<ctas, 256, 0, s>>>(I.grid, static_cast<uint8_t*>(out), n);
+    return dsr__check_launch("k_wator_kinds");
 }
 }  // namespace
 
+// ===========================================================================
+// plain form
+// ===========================================================================
 struct dsr_wator {
     dsr_heap* heap;
-    WatorArgs args;
+    WatorInst inst;
 };
 
 extern "C" int dsr_wator_types(dsr_type_desc* out) {
@@ -255,21 +345,12 @@ extern "C" int dsr_wator_workspace_bytes(int W, int H, size_t* out) {
 
 extern "C" int dsr_wator_create(dsr_heap* heap, const dsr_wator_params* p, const void* kind0_dev,
                                 void* workspace_dev, void* stream, dsr_wator** out) {
-    size_t ws;
-    if (!heap || !p || !kind0_dev || !workspace_dev || !out || dsr_wator_workspace_bytes(p->W, p->H, &ws))
-        return DSR_E_INVALID;
+    if (!heap || !params_ok(p) || !kind0_dev || !workspace_dev || !out) return DSR_E_INVALID;
     if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255) || !heap_matches(heap)) return DSR_E_INVALID;
-    if (p->fish_breed < 1 || p->shark_breed < 1 || p->shark_energy0 < 1 || p->shark_gain < 0) return DSR_E_INVALID;
     dsr_wator* w = new dsr_wator;
     w->heap = heap;
-    w->args.ws = carve(workspace_dev, p->W, p->H);
-    w->args.p = *p;
-    const uint32_t n = (uint32_t)p->W * (uint32_t)p->H;
-    unsigned ctas = (n + 255) / 256;
-    if (ctas > (unsigned)heap->sm_count * 8) ctas = (unsigned)heap->sm_count * 8;
-    k_wator_init<<<ctas, 256, 0, dsr__stream(stream)>>>(heap->dev, static_cast<const uint8_t*>(kind0_dev),
-                                                         w->args.ws, *p);
-    int rc = dsr__check_launch("k_wator_init");
+    w->inst = carve(workspace_dev, *p);
+    int rc = launch_init(heap, w->inst, kind0_dev, dsr__stream(stream));
     if (rc) {
         delete w;
         return rc;
@@ -283,11 +364,11 @@ extern "C" int dsr_wator_step(dsr_wator* w, int n_steps, void* stream) {
     cudaStream_t s = dsr__stream(stream);
     dsr_heap* h = w->heap;
     for (int i = 0; i < n_steps; ++i) {
-        int rc = dsr__doall<MFishChoose>(h, FISH, w->args, s);
-        if (!rc) rc = dsr__doall<MFishMove>(h, FISH, w->args, s);
-        if (!rc) rc = dsr__doall<MSharkStarve>(h, SHARK, w->args, s);
-        if (!rc) rc = dsr__doall<MSharkChoose>(h, SHARK, w->args, s);
-        if (!rc) rc = dsr__doall<MSharkMove>(h, SHARK, w->args, s);
+        int rc = dsr__doall<MFishChoose>(h, FISH, w->inst, s);
+        if (!rc) rc = dsr__doall<MFishMove>(h, FISH, w->inst, s);
+        if (!rc) rc = dsr__doall<MSharkStarve>(h, SHARK, w->inst, s);
+        if (!rc) rc = dsr__doall<MSharkChoose>(h, SHARK, w->inst, s);
+        if (!rc) rc = dsr__doall<MSharkMove>(h, SHARK, w->inst, s);
         if (rc) return rc;
     }
     return DSR_OK;
@@ -295,11 +376,7 @@ extern "C" int dsr_wator_step(dsr_wator* w, int n_steps, void* stream) {
 
 extern "C" int dsr_wator_kinds(dsr_wator* w, void* kind_out_dev, void* stream) {
     if (!w || !kind_out_dev) return DSR_E_INVALID;
-    const uint32_t n = (uint32_t)w->args.p.W * (uint32_t)w->args.p.H;
-    unsigned ctas = (n + 255) / 256;
-    if (ctas > (unsigned)w->heap->sm_count * 8) ctas = (unsigned)w->heap->sm_count * 8;
-    k_wator_kinds<<<ctas, 256, 0, dsr__stream(stream)>>>(w->args.ws.grid, static_cast<uint8_t*>(kind_out_dev), n);
-    return dsr__check_launch("k_wator_kinds");
+    return launch_kinds(w->heap, w->inst, kind_out_dev, dsr__stream(stream));
 }
 
 extern "C" int dsr_wator_destroy(dsr_wator* w) {
@@ -317,16 +394,176 @@ int dsr__wator_method(dsr_heap* h, int type, int method, const void* args, size_
     if (!w || w->heap != h) return DSR_E_INVALID;
     switch (method) {
         case DSR_METHOD_WATOR_F1:
-            return type == FISH ? dsr__doall<MFishChoose>(h, type, w->args, s, with_scan) : DSR_E_INVALID;
+            return type == FISH ? dsr__doall<MFishChoose>(h, type, w->inst, s, with_scan) : DSR_E_INVALID;
         case DSR_METHOD_WATOR_F2:
-            return type == FISH ? dsr__doall<MFishMove>(h, type, w->args, s, with_scan) : DSR_E_INVALID;
+            return type == FISH ? dsr__doall<MFishMove>(h, type, w->inst, s, with_scan) : DSR_E_INVALID;
         case DSR_METHOD_WATOR_S0:
-            return type == SHARK ? dsr__doall<MSharkStarve>(h, type, w->args, s, with_scan) : DSR_E_INVALID;
+            return type == SHARK ? dsr__doall<MSharkStarve>(h, type, w->inst, s, with_scan) : DSR_E_INVALID;
         case DSR_METHOD_WATOR_S1:
-            return type == SHARK ? dsr__doall<MSharkChoose>(h, type, w->args, s, with_scan) : DSR_E_INVALID;
+            return type == SHARK ? dsr__doall<MSharkChoose>(h, type, w->inst, s, with_scan) : DSR_E_INVALID;
         case DSR_METHOD_WATOR_S2:
-            return type == SHARK ? dsr__doall<MSharkMove>(h, type, w->args, s, with_scan) : DSR_E_INVALID;
+            return type == SHARK ? dsr__doall<MSharkMove>(h, type, w->inst, s, with_scan) : DSR_E_INVALID;
         default:
             return DSR_E_INVALID;
     }
+}
+
+// ===========================================================================
+// batched form
+// ===========================================================================
+struct dsr_wator_batch {
+    dsr_group* group;
+    WatorInst* table_d;              // [max_instances] device views
+    std::vector<WatorInst> table_h;  // host mirror
+    cudaStream_t capture;            // private stream used only to capture the step graph
+    cudaGraphExec_t exec = nullptr;
+    uint64_t exec_epoch = ~0ull;
+};
+
+static size_t table_bytes(int max_instances) { return ((size_t)max_instances * sizeof(WatorInst) + 1023) / 1024 * 1024; }
+
+extern "C" int dsr_wator_batch_create(void* arena_dev, size_t arena_bytes, int max_instances, const dsr_tuning* tune,
+                                      void* stream, dsr_wator_batch** out) {
+    if (!arena_dev || !out || max_instances < 1 || (reinterpret_cast<uintptr_t>(arena_dev) & 255)) return DSR_E_INVALID;
+    const size_t tb = table_bytes(max_instances);
+    if (arena_bytes <= tb) return DSR_E_OOM;
+    dsr_type_desc types[2];
+    dsr_wator_types(types);
+    dsr_wator_batch* b = new dsr_wator_batch;
+    int rc = dsr_group_create(types, 2, static_cast<uint8_t*>(arena_dev) + tb, arena_bytes - tb, max_instances, tune,
+                              stream, &b->group);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    b->table_d = static_cast<WatorInst*>(arena_dev);
+    b->table_h.assign(max_instances, WatorInst{});
+    cudaError_t e = cudaMemsetAsync(b->table_d, 0, tb, dsr__stream(stream));
+    if (!e) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_wator_batch_create");
+        dsr_group_destroy(b->group);
+        delete b;
+        return DSR_E_CUDA;
+    }
+    *out = b;
+    return DSR_OK;
+}
+
+extern "C" int dsr_wator_batch_instance_bytes(const dsr_wator_batch* b, int W, int H, uint64_t n_blocks, size_t* out) {
+    if (!b || !out || W < 3 || H < 3) return DSR_E_INVALID;
+    return dsr_group_heap_bytes(b->group, n_blocks, ws_bytes(W, H), out);
+}
+
+extern "C" int dsr_wator_batch_add(dsr_wator_batch* b, const dsr_wator_params* p, uint64_t n_blocks,
+                                   const void* kind0_dev, void* stream, int* inst_out) {
+    if (!b || !params_ok(p) || !kind0_dev || !inst_out || n_blocks == 0) return DSR_E_INVALID;
+    int slot = -1;
+    dsr_heap* heap = nullptr;
+    void* extra = nullptr;
+    int rc = dsr_group_add_heap(b->group, n_blocks, ws_bytes(p->W, p->H), stream, &slot, &heap, &extra);
+    if (rc) return rc;
+    cudaStream_t s = dsr__stream(stream);
+    WatorInst I = carve(extra, *p);
+    rc = launch_init(heap, I, kind0_dev, s);
+    if (rc) return rc;
+    b->table_h[slot] = I;
+    cudaError_t e = cudaMemcpyAsync(b->table_d + slot, &b->table_h[slot], sizeof(WatorInst), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_wator_batch_add");
+        return DSR_E_CUDA;
+    }
+    *inst_out = slot;
+    return DSR_OK;
+}
+
+extern "C" int dsr_wator_batch_remove(dsr_wator_batch* b, int inst) {
+    if (!b || inst < 0 || inst >= (int)b->table_h.size() || !b->table_h[inst].step) return DSR_E_INVALID;
+    b->table_h[inst] = WatorInst{};
+    cudaError_t e = cudaMemcpy(b->table_d + inst, &b->table_h[inst], sizeof(WatorInst), cudaMemcpyHostToDevice);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_wator_batch_remove");
+        return DSR_E_CUDA;
+    }
+    return dsr_group_remove_heap(b->group, inst);
+}
+
+static int issue_batch_step(dsr_wator_batch* b, cudaStream_t s) {
+    dsr_group* g = b->group;
+    BatchArgs a{b->table_d};
+    int rc = dsr__group_doall<GFishChoose>(g, FISH, a, s);
+    if (!rc) rc = dsr__group_doall<GFishMove>(g, FISH, a, s);
+    if (!rc) rc = dsr__group_doall<GSharkStarve>(g, SHARK, a, s);
+    if (!rc) rc = dsr__group_doall<GSharkChoose>(g, SHARK, a, s);
+    if (!rc) rc = dsr__group_doall<GSharkMove>(g, SHARK, a, s);
+    return rc;
+}
+
+// One batched step is 10 launches (5 fused scans, 5 method kernels) over all
+// instances; it is captured once into a CUDA graph and replayed until the set
+// of instances changes.
+extern "C" int dsr_wator_batch_step(dsr_wator_batch* b, int n_steps, void* stream) {
+    if (!b || n_steps < 0) return DSR_E_INVALID;
+    if (b->exec_epoch != b->group->epoch) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+        if (e) {
+            dsr__set_cuda_error(e, "dsr_wator_batch_step capture");
+            return DSR_E_CUDA;
+        }
+        const int rc = issue_batch_step(b, b->capture);
+        e = cudaStreamEndCapture(b->capture, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (!e) e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e) {
+            dsr__set_cuda_error(e, "dsr_wator_batch_step instantiate");
+            b->exec = nullptr;
+            return DSR_E_CUDA;
+        }
+        b->exec_epoch = b->group->epoch;
+    }
+    cudaStream_t s = dsr__stream(stream);
+    for (int i = 0; i < n_steps; ++i) {
+        cudaError_t e = cudaGraphLaunch(b->exec, s);
+        if (e) {
+            dsr__set_cuda_error(e, "dsr_wator_batch_step launch");
+            return DSR_E_CUDA;
+        }
+    }
+    return DSR_OK;
+}
+
+extern "C" int dsr_wator_batch_heap(dsr_wator_batch* b, int inst, dsr_heap** out) {
+    if (!b || !out || inst < 0 || inst >= (int)b->table_h.size() || !b->table_h[inst].step) return DSR_E_INVALID;
+    *out = b->group->heaps[inst];
+    return DSR_OK;
+}
+
+extern "C" int dsr_wator_batch_kinds(dsr_wator_batch* b, int inst, void* kind_out_dev, void* stream) {
+    dsr_heap* h = nullptr;
+    int rc = dsr_wator_batch_heap(b, inst, &h);
+    if (rc || !kind_out_dev) return rc ? rc : DSR_E_INVALID;
+    return launch_kinds(h, b->table_h[inst], kind_out_dev, dsr__stream(stream));
+}
+
+extern "C" int dsr_wator_batch_group(dsr_wator_batch* b, dsr_group** out) {
+    if (!b || !out) return DSR_E_INVALID;
+    *out = b->group;
+    return DSR_OK;
+}
+
+extern "C" int dsr_wator_batch_destroy(dsr_wator_batch* b) {
+    if (!b) return DSR_E_INVALID;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    cudaStreamDestroy(b->capture);
+    dsr_group_destroy(b->group);
+    delete b;
+    return DSR_OK;
 }

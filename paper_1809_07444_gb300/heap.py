@@ -64,10 +64,23 @@ class Heap:
         self.handle = h
         self._scratch = torch.zeros(2, dtype=torch.int64, device=device)
 
+    @classmethod
+    def view(cls, handle, types, arena, names=None):
+        """A non-owning wrapper of a heap that lives inside another object (a group)."""
+        h = cls.__new__(cls)
+        h.lib = L.load()
+        h.types = [list(t) for t in types]
+        h.names = names
+        h.arena = arena  # a tensor whose memory begins with the heap (for snapshot offsets)
+        h.handle = C.c_void_p(handle.value if isinstance(handle, C.c_void_p) else handle)
+        h._owner = False
+        h._scratch = torch.zeros(2, dtype=torch.int64, device="cuda")
+        return h
+
     def close(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and getattr(self, "_owner", True):
             self.lib.dsr_heap_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:

@@ -1,0 +1,136 @@
+"""Serving: continuous batching of game-of-life and wa-tor jobs on one GPU.
+
+Jobs arrive over time (a Poisson stream), each with its application, grid
+side, step count and seed. A job is admitted as soon as its heap and
+workspace fit in the free bytes of its application's arena (first fit; jobs
+that do not fit wait, later smaller jobs may pass them). Admitted jobs stay
+resident on the device and advance together: one tick is one batched step of
+every resident wa-tor job and one batched generation of every resident
+game-of-life job (group do-alls replayed from a CUDA graph). A job that has
+done its steps leaves at the tick boundary: its final state hash is queued on
+the stream and its bytes are returned, so the next waiting job can start on
+the following tick.
+
+Host code here only schedules (admission, retirement, bookkeeping); every
+step runs in libdsr.so.
+"""
+import collections
+import time
+
+import numpy as np
+import torch
+
+from . import workloads as WL
+from .apps import GolBatch, WatorBatch
+
+WATOR, GOL = 1, 0
+
+
+class Server:
+    def __init__(self, arena_bytes=64 << 30, gol_fraction=0.4, max_jobs=4096, tuning=None):
+        self.wb = WatorBatch(int(arena_bytes * (1 - gol_fraction)) // 1024 * 1024, max_instances=max_jobs,
+                             tuning=tuning)
+        self.gb = GolBatch(int(arena_bytes * gol_fraction) // 1024 * 1024, max_instances=max_jobs, tuning=tuning)
+        self.stream = torch.cuda.current_stream()
+
+    def _admit(self, job):
+        side, seed = int(job["side"]), int(job["seed"])
+        if job["app"] == WATOR:
+            return self.wb.add(side, side, WL.wator_initial(side, side, seed), seed)
+        return self.gb.add(side, side, WL.gol_initial(side, side, seed))
+
+    def _batch(self, app):
+        return self.wb if app == WATOR else self.gb
+
+    def run(self, jobs, time_limit=None, realtime=True, max_admit_per_tick=64, keep_hashes=True):
+        """Serve `jobs` (a list of dicts with id, arrival, app, side, steps, seed).
+
+        Returns a report: per completed job its arrival, admission, completion
+        (seconds since start), ticks and final state hashes; per tick its
+        device time; the objects visited; and jobs left unfinished when
+        `time_limit` (seconds of wall time) ran out. With realtime=False,
+        arrivals are not waited for (every job counts as arrived at start).
+        """
+        order = sorted(jobs, key=lambda j: j["arrival"])
+        pending = collections.deque(order)
+        waiting = collections.deque()
+        resident = {}  # (app, slot) -> [job, steps_left, admitted_at]
+        done = []
+        ticks = []  # (start event, end event, resident count)
+        t0 = time.perf_counter()
+        visits = 0
+
+        def now():
+            return time.perf_counter() - t0
+
+        while pending or waiting or resident:
+            t = now()
+            if time_limit is not None and t > time_limit:
+                break
+            while pending and (not realtime or pending[0]["arrival"] <= t):
+                waiting.append(pending.popleft())
+            # admission: first fit in arrival order, bounded per tick
+            admitted = 0
+            kept = collections.deque()
+            while waiting and admitted < max_admit_per_tick:
+                job = waiting.popleft()
+                slot = self._admit(job)
+                if slot is None:
+                    kept.append(job)
+                    continue
+                resident[(job["app"], slot)] = [job, int(job["steps"]), now()]
+                admitted += 1
+            kept.extend(waiting)
+            waiting = kept
+            if not resident:
+                if pending and realtime:
+                    time.sleep(max(0.0, min(pending[0]["arrival"] - now(), 0.05)))
+                continue
+            # one tick: a batched step of each application that has jobs
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            if self.wb.inst:
+                self.wb.step(1)
+            if self.gb.inst:
+                self.gb.step(1)
+            b.record(self.stream)
+            ticks.append((a, b, len(resident)))
+            finished = []
+            for key, rec in resident.items():
+                rec[1] -= 1
+                if rec[1] == 0:
+                    finished.append(key)
+            if finished:
+                b.synchronize()
+                t_done = now()
+                for key in finished:
+                    app, slot = key
+                    job, _, t_adm = resident.pop(key)
+                    batch = self._batch(app)
+                    heap = batch.heap(slot)
+                    visits += heap.counters()["visits"]
+                    h = batch.hash(slot) if keep_hashes else None
+                    batch.remove(slot)
+                    done.append({"id": job["id"], "app": app, "side": int(job["side"]), "steps": int(job["steps"]),
+                                 "seed": int(job["seed"]), "arrival": float(job["arrival"]), "admitted": t_adm,
+                                 "completed": t_done, "hash": h})
+        torch.cuda.synchronize()
+        wall = now()
+        step_ms = [x.elapsed_time(y) for x, y, _ in ticks]
+        for key, rec in resident.items():  # count the work of jobs still resident
+            visits += self._batch(key[0]).heap(key[1]).counters()["visits"]
+        return {"done": done, "step_ms": step_ms, "wall_s": wall, "visits": visits,
+                "unfinished": len(resident) + len(waiting) + len(pending)}
+
+
+def summarize(report):
+    """p50/p99 per-step and per-job latency, throughput."""
+    step = np.array(report["step_ms"]) if report["step_ms"] else np.zeros(1)
+    lat = np.array([d["completed"] - d["arrival"] for d in report["done"]]) if report["done"] else np.zeros(1)
+    return {
+        "jobs_done": len(report["done"]), "jobs_unfinished": report["unfinished"], "ticks": len(report["step_ms"]),
+        "step_ms_p50": float(np.percentile(step, 50)), "step_ms_p99": float(np.percentile(step, 99)),
+        "job_s_p50": float(np.percentile(lat, 50)), "job_s_p99": float(np.percentile(lat, 99)),
+        "object_updates_per_s": report["visits"] / report["wall_s"] if report["wall_s"] else 0.0,
+        "wall_s": report["wall_s"],
+    }
