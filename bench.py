@@ -403,20 +403,25 @@ def bench_batched(n_inst=256, steps=20, one_by_one_steps=3):
             "speedup_vs_one_by_one": vb / vp if vp else None, "launches_per_step": 10, "graph": True}
 
 
-def bench_served(seconds=20.0, n_jobs=10000, arena_gb=64):
+def bench_served(seconds=20.0, n_jobs=10000, arena_gb=64, lo=128, hi=4096, steps_lo=50, steps_hi=1000,
+                 label="the 10,000-job stream"):
     """The served workload (Poisson 200 jobs/s, game-of-life and wa-tor, sides
-    log-uniform in [128, 4096], 50-1000 steps, 64 GB of arenas), in real time
-    for a bounded number of seconds."""
+    log-uniform in [lo, hi], steps uniform in [steps_lo, steps_hi], arenas of
+    arena_gb GB), in real time for at most `seconds` of wall time."""
+    import torch
     from paper_1809_07444_gb300 import workloads as WL
     from paper_1809_07444_gb300.serve import Server, summarize
 
-    s = WL.served_jobs(n_jobs, 2024)
+    s = WL.served_jobs(n_jobs, 2024, lo=lo, hi=hi, steps_lo=steps_lo, steps_hi=steps_hi)
     jobs = [{"id": i, "arrival": float(s["arrival"][i]), "app": int(s["app"][i]), "side": int(s["side"][i]),
              "steps": int(s["steps"][i]), "seed": int(s["seed"][i])} for i in range(n_jobs)]
     srv = Server(arena_bytes=arena_gb << 30, max_jobs=4096)
     rep = srv.run(jobs, time_limit=seconds, realtime=True, keep_hashes=False)
     out = summarize(rep)
-    out["sample"] = "first %.0f s of wall time of the 10,000-job stream (arrival seed 2024)" % seconds
+    out["jobs"] = n_jobs
+    out["sample"] = "first %.0f s of wall time of %s (arrival seed 2024)" % (seconds, label)
+    del srv
+    torch.cuda.empty_cache()
     return out
 
 
@@ -488,6 +493,11 @@ def main():
         line["streaming_doall"] = bench_streaming_doall()
         if args.served_seconds > 0:
             line["served"] = bench_served(args.served_seconds)
+            # the same arrival process with jobs small enough to finish inside
+            # the bench's budget, so that job latencies exist
+            line["served_small"] = bench_served(args.served_seconds, n_jobs=2000, arena_gb=16, lo=64, hi=512,
+                                                steps_lo=50, steps_hi=200,
+                                                label="a 2,000-job stream with sides in [64, 512] and 50-200 steps")
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

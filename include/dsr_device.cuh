@@ -348,6 +348,7 @@ __device__ inline dsr_grab dsr_init_block(const dsr_dev_heap& H, int T, int k, u
  * clear), initialise it for T with the first slots already taken, publish
  * its bitmap, then set allocated[T] and, if slots remain, active[T]. */
 __device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsigned hint) {
+    unsigned empty_rounds = 0;  // slow paths that found no free block
     for (unsigned a = 0; a < DSR_ALLOC_CAP; ++a) {
         long long b = dsr_hb_find(H.active_bm[T], hint + a * 0x61C88647u);
         if (b < 0) {
@@ -373,12 +374,12 @@ __device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsi
             const dsr_grab g = dsr_init_block(H, T, k, hint ^ (a * 0x9E3779B9u));
             if (counted) atomicSub(H.slow + T, 1u);
             if (g.status == 0) return g;
-            // No free block (or an injected failure). Active blocks may be in
-            // flight (a release between its slot return and its
-            // active[T].set): retry a few times before reporting
-            // out-of-memory.
-            if (g.status != DSR_ERR_RETRY || a >= 16) return {0, 0, DSR_ERR_OOM};
-            dsr_backoff(a + 9);
+            // No free block (or an injected failure). Slots may still be in
+            // flight: a block another leader just initialised, or a release
+            // between its slot return and its active[T].set. Retry the fast
+            // path a few times before reporting out-of-memory.
+            if (g.status != DSR_ERR_RETRY || ++empty_rounds >= 16) return {0, 0, DSR_ERR_OOM};
+            dsr_backoff(empty_rounds + 9);
             continue;
         }
         // Take the lowest free slots of a snapshot; while the block still has

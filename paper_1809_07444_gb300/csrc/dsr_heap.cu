@@ -302,10 +302,10 @@ static void build_dev_view(dsr_heap* h) {
     D.R_done = reinterpret_cast<uint32_t*>(a + DSR_HDR_RDONE);
     D.ctr = reinterpret_cast<dsr_u64*>(a + DSR_HDR_CTR);
     D.slow = reinterpret_cast<uint32_t*>(a + DSR_HDR_SLOW);
-    // At most one block initialisation in flight per SM per type, and no more
-    // than one per 64 blocks of the heap, so that a small heap is not carved
-    // into nearly empty blocks by a burst of concurrent leaders.
-    uint64_t sm = (uint64_t)(h->sm_count > 0 ? h->sm_count : 1), by_size = L.n_blocks / 64;
+    // At most four block initialisations in flight per SM per type, and no
+    // more than one per 64 blocks of the heap, so that a small heap is not
+    // carved into nearly empty blocks by a burst of concurrent leaders.
+    uint64_t sm = 4 * (uint64_t)(h->sm_count > 0 ? h->sm_count : 1), by_size = L.n_blocks / 64;
     D.slow_max = (uint32_t)(by_size < 1 ? 1 : (by_size < sm ? by_size : sm));
     D.dbg = reinterpret_cast<dsr_u64*>(a + DSR_HDR_DBG);
     D.R_mask = reinterpret_cast<dsr_u64*>(a + off_rmask(L));

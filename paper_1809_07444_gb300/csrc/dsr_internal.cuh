@@ -52,12 +52,11 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
     const int threads = h->tune.threads;
     int& grid = grid_cache[threads / 64];
     if (grid == 0 || h->tune.ctas_per_sm > 0) grid = dsr__persistent_grid(h, (const void*)dsr_doall_kernel<M>, threads);
-    // Without an explicit CTAs-per-SM setting the grid is 16 times what fits
-    // on the GPU at once (capped by the work a do-all over this heap can
-    // list): CTAs whose slots hold slow objects (allocation, long chains of
-    // dependent loads) then do not hold up the rest, which finish and make
-    // room for further CTAs.
-    dsr_u64 g64 = (dsr_u64)grid * (h->tune.ctas_per_sm > 0 ? 1 : 16);
+    // Persistent grid: the CTAs that fit on the GPU at once, capped by the
+    // work a do-all over this heap can list. (Every CTA ends with one atomic
+    // on the completion counter, so a much larger grid costs more in those
+    // serialised atomics than it gains in balance.)
+    dsr_u64 g64 = (dsr_u64)grid;
     const dsr_u64 cap_grid = (h->dev.M * 64 + threads - 1) / threads;
     if (g64 > cap_grid) g64 = cap_grid;
     int g = (int)g64;

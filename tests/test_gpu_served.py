@@ -30,7 +30,7 @@ def _oracle_hash(job):
 def test_served_jobs_match_oracle_and_queue_for_memory():
     jobs = _jobs(30, 3)
     # small arenas: not every job fits at once, so jobs wait for others to leave
-    srv = Server(arena_bytes=24 << 20, gol_fraction=0.4, max_jobs=64)
+    srv = Server(arena_bytes=6 << 20, gol_fraction=0.4, max_jobs=64)
     rep = srv.run(jobs, realtime=False)
     assert rep["unfinished"] == 0 and len(rep["done"]) == len(jobs)
     waited = [d for d in rep["done"] if d["admitted"] > 0.0 and d["admitted"] > min(x["completed"] for x in rep["done"])]
