@@ -12,9 +12,14 @@ and deaths, i.e. every row of the hot path.
              pinned host memory: host->device copy, heap reset, agent
              creation, the K steps and the device->host read of the final
              state hash all inside the timed region;
-  roofline   the fish-choice method kernel (the largest share of a step),
-             algorithmic bytes / its CUDA-event time, against the measured
-             HBM copy peak;
+  roofline   the method kernel with the largest share of a step: its
+             algorithmic bytes (per-object and per-event byte counts of the
+             wa-tor rules, see phase_bytes) over its CUDA-event time, both
+             summed over the timed steps, against the measured HBM copy
+             peak. Times come from events recorded around every scan and
+             method kernel inside the timed region; the event counts
+             (objects, blocks, moves, births, deaths) from a replay of the
+             same steps, checked against the timed window's visit count;
   cpu_baseline  the oracle (single-threaded C++) on the same workload.
 
 L2 (129 MB) is flushed by writing a 512 MB buffer before every timed step,
@@ -150,15 +155,80 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
-def fish_choice_bytes(n_fish, n_blocks, cells):
-    """Algorithmic bytes of one fish-choice (F1) method kernel launch.
+PHASES = ("F1", "F2", "S0", "S1", "S2")
+KERNELS = {"F1": "dsr_doall_kernel<MFishChoose>", "F2": "dsr_doall_kernel<MFishMove>",
+           "S0": "dsr_doall_kernel<MSharkStarve>", "S1": "dsr_doall_kernel<MSharkChoose>",
+           "S2": "dsr_doall_kernel<MSharkMove>"}
 
-    Per fish: x, y, timer read (12 B) and timer written (4 B), the intent
-    word written (4 B), one claim word read-modify-written (16 B, at most one
-    per fish); per listed block its R entry (12 B); and the grid read once
-    (8 B per cell), since every cell neighbours some fish at this density.
+
+def phase_bytes(phase, objs, blocks, moves, births, deaths):
+    """Algorithmic bytes of one wa-tor method kernel: what its rules read and
+    write per visited object and per event, plus the 12-byte R entry (block id
+    and live mask) of every listed block. Fields are int32, grid and claim
+    words uint64, intent uint32.
+
+      F1  per fish: x, y, timer read, timer written (16), four neighbour grid
+          words (32), intent written (4), claim read-modify-written (16; an
+          upper bound, as fish with no empty neighbour claim nothing)   = 68
+      F2  per fish: x, y (8), intent (4), claim (8)                      = 20
+          per move: target and own grid words written (16), x, y written
+          (8), timer read (4)                                            = 28
+          per birth: timer reset (4), the new fish's three fields (12)   = 16
+      S0  per shark: energy read and written                             = 8
+          per death: x, y read (8), grid word cleared (8)                = 16
+      S1  as F1                                                          = 68
+      S2  per shark as F2                                                = 20
+          per move: target grid word read and written (16), own grid word
+          written (8), x, y written (8), timer read (4)                  = 36
+          per fish eaten: energy read and written                        = 8
+          per birth: timer reset (4), the new shark's four fields (16)   = 20
     """
-    return n_fish * (12 + 4 + 4 + 16) + n_blocks * 12 + cells * 8
+    per_obj = {"F1": 68, "F2": 20, "S0": 8, "S1": 68, "S2": 20}[phase]
+    b = per_obj * objs + 12 * blocks
+    if phase == "F2":
+        b += 28 * moves + 16 * births
+    elif phase == "S0":
+        b += 16 * deaths
+    elif phase == "S2":
+        b += 36 * moves + 8 * deaths + 20 * births
+    return b
+
+
+def replay_phase_counts(lib, k0, seed, warmup, steps, L):
+    """Event counts of each phase over steps [warmup, warmup + steps) of a
+    fresh run of the same simulation (wa-tor is deterministic, so this is the
+    timed window's work): objects visited, blocks listed, moves, births and
+    deaths, summed per phase. Host synchronisation between phases; not timed."""
+    import torch
+    from paper_1809_07444_gb300.apps import Wator
+    from paper_1809_07444_gb300.heap import _stream_ptr
+
+    w = Wator(W_SIDE, W_SIDE, k0, seed)
+    sp = _stream_ptr()
+    wh = C.c_void_p(w.handle.value)
+    methods = {"F1": (0, L.METHOD_WATOR_F1), "F2": (0, L.METHOD_WATOR_F2), "S0": (1, L.METHOD_WATOR_S0),
+               "S1": (1, L.METHOD_WATOR_S1), "S2": (1, L.METHOD_WATOR_S2)}
+    w.step(warmup)
+    tot = {p: dict(objs=0, blocks=0, moves=0, births=0, deaths=0) for p in PHASES}
+    for _ in range(steps):
+        for p in PHASES:
+            t, m = methods[p]
+            c0 = w.heap.counters()
+            L.check(lib.dsr_doall_scan(w.heap.handle, t, sp), "dsr_doall_scan")
+            torch.cuda.synchronize()
+            nblocks = int(w.heap.arena[8:12].cpu().view(torch.int32).item())  # R length in the heap header
+            L.check(lib.dsr_doall_run(w.heap.handle, t, m, C.byref(wh), C.sizeof(wh), sp), "dsr_doall_run")
+            c1 = w.heap.counters()
+            d = tot[p]
+            d["objs"] += c1["visits"] - c0["visits"]
+            d["blocks"] += nblocks
+            d["moves"] += c1["app0"] - c0["app0"]
+            d["births"] += c1["allocs"] - c0["allocs"]
+            d["deaths"] += c1["frees"] - c0["frees"]
+    if w.heap.stats()["error_flags"]:
+        raise RuntimeError("device error flags in the replay")
+    del w
+    return tot
 
 
 def run_gpu(args, rank, world):
@@ -191,6 +261,7 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     c0 = sim.heap.counters()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sim.phase_timing(args.steps)
     barrier()
     with Clocks(dev) as clk:
         for k in range(args.steps):
@@ -207,31 +278,21 @@ def run_gpu(args, rank, world):
     if st["error_flags"]:
         raise RuntimeError("device error flags %d" % st["error_flags"])
 
-    # Per-phase method-kernel timing, after the timed region (the state keeps
-    # advancing): L2 flushed before each step, scan outside the events, the
-    # objects visited and blocks listed read back between scan and run.
-    methods = [(0, L.METHOD_WATOR_F1), (0, L.METHOD_WATOR_F2), (1, L.METHOD_WATOR_S0), (1, L.METHOD_WATOR_S1),
-               (1, L.METHOD_WATOR_S2)]
-    wh = C.c_void_p(sim.handle.value)
-    phases = {i: [] for i in range(len(methods))}
-    for rep in range(5):
-        flush.fill_(rep)
-        for i, (t, m) in enumerate(methods):
-            v0 = sim.heap.counters()["visits"]
-            L.check(lib.dsr_doall_scan(sim.heap.handle, t, sp), "dsr_doall_scan")
-            torch.cuda.synchronize()
-            objs = sim.heap.counters()["visits"] - v0
-            nblocks = int(sim.heap.arena[8:12].cpu().view(torch.int32).item())  # R length in the heap header
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            L.check(lib.dsr_doall_run(sim.heap.handle, t, m, C.byref(wh), C.sizeof(wh), sp), "dsr_doall_run")
-            b.record(stream)
-            b.synchronize()
-            phases[i].append((a.elapsed_time(b), objs, nblocks))
-    med = {i: statistics.median(x[0] for x in v) for i, v in phases.items()}
-    f1 = phases[0]
-    f1_gbs = statistics.median(fish_choice_bytes(o, nb, W_SIDE * W_SIDE) / (ms * 1e-3) / 1e9 for ms, o, nb in f1)
-    f1_bytes = statistics.median(fish_choice_bytes(o, nb, W_SIDE * W_SIDE) for ms, o, nb in f1)
+    phase_ms, scan_ms, n_rec = sim.phase_times()
+    sim.phase_timing(0)
+    if n_rec != args.steps:
+        raise RuntimeError("phase timing recorded %d of %d steps" % (n_rec, args.steps))
+    counts = replay_phase_counts(lib, k0, seed, args.warmup, args.steps, L)
+    replay_visits = sum(c["objs"] for c in counts.values())
+    if replay_visits != visits:
+        raise RuntimeError("replay visited %d objects, the timed window %d" % (replay_visits, visits))
+    phases = {}
+    for p in PHASES:
+        c = counts[p]
+        by = phase_bytes(p, **c)
+        phases[p] = dict(c, kernel=KERNELS[p], method_ms_per_step=phase_ms[p] / args.steps,
+                         scan_ms_per_step=scan_ms[p] / args.steps, bytes_per_launch=by / args.steps,
+                         gbs=by / (phase_ms[p] * 1e-3) / 1e9 if phase_ms[p] > 0 else None)
 
     # e2e through the C ABI with host buffers
     k0_host = torch.from_numpy(np.ascontiguousarray(k0.reshape(-1))).pin_memory()
@@ -261,7 +322,7 @@ def run_gpu(args, rank, world):
     hashed = sim.heap.stats()["live_objects"][0]  # objects the final hash do-all visited
     return {
         "dev_s": dev_s, "visits": visits, "allocfree": allocfree, "clocks": clk.summary(),
-        "phase_ms": med, "f1_gbs": f1_gbs, "f1_bytes": f1_bytes, "f1_ms": med[0], "e2e_s": e2e_s, "e2e_visits": c2["visits"] - hashed,
+        "phases": phases, "e2e_s": e2e_s, "e2e_visits": c2["visits"] - hashed,
         "h2d": k0_host.numel(), "d2h": 16, "stats": st,
     }
 
@@ -274,18 +335,26 @@ def _ev():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def bench_alloc_free(n=1 << 24, n_types=2, reps=3):
-    """Allocation microbenchmark: n threads each create one object (types by a
-    hash of the thread index), then every object is deleted; fresh heap, L2
-    flushed before each timed kernel."""
-    import torch
-    from paper_1809_07444_gb300.heap import Heap, heap_bytes_for_blocks
+TYPES4 = [[4, 4], [4, 4, 4], [4, 4, 4, 4], [4] * 8]  # capacities 64, 42, 32, 16
 
-    types = [[4, 4], [4, 4, 4, 4]]
-    h = Heap(types, heap_bytes_for_blocks(types, int(n / 32 * 1.3) + 4096))
+
+def bench_alloc_free(n=1 << 24, n_types=2, reps=2, churn=False):
+    """Allocation microbenchmark: n threads each create one object (type by a
+    hash of the thread index, among the first n_types of TYPES4), then one
+    kernel deletes every object; with churn, a kernel in between where half
+    of the threads delete their object and create a replacement. Fresh heap
+    each round, L2 flushed before each timed kernel, first round untimed."""
+    import torch
+    from paper_1809_07444_gb300 import _lib as L
+    from paper_1809_07444_gb300.heap import Heap, heap_bytes_for_blocks, _stream_ptr
+
+    caps = [64, 42, 32, 16][:n_types]
+    blocks = int(n * sum(1.0 / c for c in caps) / n_types * 1.6) + 4096
+    h = Heap(TYPES4, heap_bytes_for_blocks(TYPES4, blocks))
     refs = torch.empty(n, dtype=torch.int64, device="cuda")
+    nrep = torch.zeros(1, dtype=torch.int64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    ta, tf = [], []
+    ta, tf, tc, replaced = [], [], [], 0
     for r in range(reps + 1):
         h.reset()
         flush.fill_(r)
@@ -293,6 +362,14 @@ def bench_alloc_free(n=1 << 24, n_types=2, reps=3):
         a0.record()
         h.bench_alloc(refs, n_types, 77 + r)
         a1.record()
+        if churn:
+            nrep.zero_()
+            flush.fill_(r + 2)
+            c0, c1 = _ev()
+            c0.record()
+            L.check(h.lib.dsr_bench_churn(h.handle, n, n_types, 1000 + r, C.c_void_p(refs.data_ptr()),
+                                          C.c_void_p(nrep.data_ptr()), _stream_ptr()), "dsr_bench_churn")
+            c1.record()
         flush.fill_(r + 1)
         f0, f1 = _ev()
         f0.record()
@@ -302,58 +379,164 @@ def bench_alloc_free(n=1 << 24, n_types=2, reps=3):
         if r:  # first round warms up
             ta.append(a0.elapsed_time(a1) / 1e3)
             tf.append(f0.elapsed_time(f1) / 1e3)
+            if churn:
+                tc.append(c0.elapsed_time(c1) / 1e3)
+                replaced = int(nrep.item())
     st = h.stats()
     ok = st["error_flags"] == 0 and st["free_blocks"] == st["n_blocks"]
-    return {"objects": n, "types": n_types, "allocs_per_s": n / statistics.median(ta),
-            "frees_per_s": n / statistics.median(tf), "alloc_free_per_s": 2 * n / (statistics.median(ta) + statistics.median(tf)),
-            "heap_consistent_after": ok, "l2": "flushed before each kernel"}
+    ma, mf = statistics.median(ta), statistics.median(tf)
+    out = {"objects": n, "types": n_types, "allocs_per_s": n / ma, "frees_per_s": n / mf,
+           "alloc_free_per_s": 2 * n / (ma + mf), "heap_consistent_after": ok}
+    if churn:
+        out["churn"] = {"replaced": replaced, "ops_per_s": 2 * replaced / statistics.median(tc),
+                        "ms": statistics.median(tc) * 1e3}
+    del h, refs, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_alloc_sweep():
+    """M1: 2^24 objects with 1..4 types, 2^26 and 2^28 with 2 types, and the
+    50% churn mix at 2^26."""
+    rows = [bench_alloc_free(1 << 24, t) for t in (1, 2, 3, 4)]
+    rows.append(bench_alloc_free(1 << 26, 2, churn=True))
+    rows.append(bench_alloc_free(1 << 28, 2, reps=1))
+    return {"rows": rows, "l2": "flushed before each kernel",
+            "types": "first n of 4 types with capacities 64, 42, 32, 16"}
 
 
 def bench_streaming_doall(n=1 << 28, fields=4, reps=5):
-    """Streaming do-all: one type with `fields` int32 fields, n objects (>> L2);
-    method field f += field f+1 (reads every field, writes every field)."""
+    """M2: one type with `fields` int32 fields, n objects (>> L2), method
+    field f += field f+1 (every field read and written). Timed at full blocks,
+    then again after a do-all deleted every fourth object (75% fill)."""
     import torch
     from paper_1809_07444_gb300 import _lib as L
     from paper_1809_07444_gb300.heap import Heap, heap_bytes_for_blocks, _stream_ptr
 
     types = [[4] * fields]
-    blocks = n // 64
-    h = Heap(types, heap_bytes_for_blocks(types, blocks + 1024))
+    h = Heap(types, heap_bytes_for_blocks(types, n // 64 + 1024))
     refs = torch.empty(n, dtype=torch.int64, device="cuda")
     h.bench_alloc(refs, 1, 5)
     del refs
     torch.cuda.synchronize()
     lib, sp = h.lib, _stream_ptr()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    ms, ms_full = [], []
-    for r in range(reps + 1):
-        flush.fill_(r)
-        L.check(lib.dsr_doall_scan(h.handle, 0, sp), "dsr_doall_scan")
-        a0, a1 = _ev()
-        a0.record()
-        L.check(lib.dsr_doall_run(h.handle, 0, L.METHOD_STREAM_ADD, None, 0, sp), "dsr_doall_run")
-        a1.record()
-        flush.fill_(r + 1)
-        b0, b1 = _ev()
-        b0.record()
-        h.parallel_do(0, L.METHOD_STREAM_ADD, None)
-        b1.record()
-        torch.cuda.synchronize()
-        if r:
-            ms.append(a0.elapsed_time(a1))
-            ms_full.append(b0.elapsed_time(b1))
-    st = h.stats()
-    live = st["live_objects"][0]
-    alloc_blocks = st["allocated_blocks"][0]
-    # algorithmic bytes: every field read and written once, plus the R entry
-    # (12 B) of each listed block
-    bytes_method = live * fields * 4 * 2 + alloc_blocks * 12
-    t = statistics.median(ms) * 1e-3
     peak, kind = _peaks()
-    return {"objects": live, "fields": fields, "method_ms": t * 1e3, "doall_ms": statistics.median(ms_full),
-            "object_updates_per_s": live / t, "achieved_gbs": bytes_method / t / 1e9, "peak_gbs": peak,
-            "frac": bytes_method / t / 1e9 / peak, "peak_source": kind,
-            "algorithmic_bytes": bytes_method, "fill": live / (alloc_blocks * 64)}
+    out = {}
+    for fill in ("100%", "75%"):
+        if fill == "75%":
+            h.parallel_do(0, L.METHOD_DELETE_IF, L.DeleteIfArgs(4, 0))
+        ms, ms_full = [], []
+        for r in range(reps + 1):
+            flush.fill_(r)
+            L.check(lib.dsr_doall_scan(h.handle, 0, sp), "dsr_doall_scan")
+            a0, a1 = _ev()
+            a0.record()
+            L.check(lib.dsr_doall_run(h.handle, 0, L.METHOD_STREAM_ADD, None, 0, sp), "dsr_doall_run")
+            a1.record()
+            flush.fill_(r + 1)
+            b0, b1 = _ev()
+            b0.record()
+            h.parallel_do(0, L.METHOD_STREAM_ADD, None)
+            b1.record()
+            torch.cuda.synchronize()
+            if r:
+                ms.append(a0.elapsed_time(a1))
+                ms_full.append(b0.elapsed_time(b1))
+        st = h.stats()
+        live = st["live_objects"][0]
+        alloc_blocks = st["allocated_blocks"][0]
+        # algorithmic bytes: every live object's fields read and written
+        # once, plus the R entry (12 B) of each listed block
+        bytes_method = live * fields * 4 * 2 + alloc_blocks * 12
+        t = statistics.median(ms) * 1e-3
+        out[fill] = {"objects": live, "method_ms": t * 1e3, "doall_ms": statistics.median(ms_full),
+                     "object_updates_per_s": live / t, "achieved_gbs": bytes_method / t / 1e9,
+                     "frac": bytes_method / t / 1e9 / peak, "algorithmic_bytes": bytes_method,
+                     "fill": live / (alloc_blocks * 64)}
+    out.update(fields=fields, peak_gbs=peak, peak_source=kind)
+    del h, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_streaming_sweep(n=1 << 28):
+    """M2 for K = 2, 4, 8 fields."""
+    return {"K%d" % k: bench_streaming_doall(n, k) for k in (2, 4, 8)}
+
+
+def bench_gol(W=64, gens=100, reps=3):
+    """C1: game of life 64 x 64 for 100 generations (three do-alls each);
+    latency-bound (the state stays in L2): generations/s and the per-
+    generation latency from events around every generation."""
+    import torch
+    from paper_1809_07444_gb300 import workloads as WL
+    from paper_1809_07444_gb300.apps import Gol
+
+    lat, rates = [], []
+    for r in range(reps + 1):
+        g = Gol(W, W, WL.gol_initial(W, W, 1))
+        g.step(1)
+        torch.cuda.synchronize()
+        evs = [_ev() for _ in range(gens)]
+        for k in range(gens):
+            evs[k][0].record()
+            g.step(1)
+            evs[k][1].record()
+        torch.cuda.synchronize()
+        per = [a.elapsed_time(b) for a, b in evs]
+        tot = evs[0][0].elapsed_time(evs[-1][1])
+        if r:
+            lat.extend(per)
+            rates.append(gens / (tot * 1e-3))
+        del g
+    lat.sort()
+    return {"workload": "game of life %dx%d, %d generations" % (W, W, gens), "gens_per_s": statistics.median(rates),
+            "gen_ms_p50": lat[len(lat) // 2], "gen_ms_p99": lat[int(len(lat) * 0.99)], "launches_per_gen": 6}
+
+
+def bench_nbody(n=65536, steps=5):
+    """C3: n-body with merging, 65,536 bodies, FP32 on the GPU. FLOPs counted
+    as 20 per pair for the force (softened inverse-cube, three FMAs into the
+    acceleration) and 8 per pair for the merge-partner distance test, against
+    the FP32 FMA ceiling measured by dsr_bench_fma."""
+    import torch
+    from paper_1809_07444_gb300 import _lib as L
+    from paper_1809_07444_gb300 import workloads as WL
+    from paper_1809_07444_gb300.apps import NBody
+    from paper_1809_07444_gb300.heap import _stream_ptr
+
+    rows, _ = WL.nbody_initial(n, 1)
+    nb = NBody(rows)
+    nb.step(2)
+    torch.cuda.synchronize()
+    live0 = nb.heap.stats()["live_objects"][0]
+    e0, e1 = _ev()
+    e0.record()
+    nb.step(steps)
+    e1.record()
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    flop = 28.0 * live0 * live0
+    lib = L.load()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ctas, iters = sms * 8, 1 << 16
+    out_buf = torch.empty(ctas * 256, dtype=torch.float32, device="cuda")
+    fl = []
+    for r in range(4):
+        a, b = _ev()
+        a.record()
+        L.check(lib.dsr_bench_fma(C.c_void_p(out_buf.data_ptr()), ctas, iters, _stream_ptr()), "dsr_bench_fma")
+        b.record()
+        b.synchronize()
+        if r:
+            fl.append(ctas * 256 * 8 * iters * 2 / (a.elapsed_time(b) * 1e-3))
+    peak = statistics.median(fl)
+    del nb
+    torch.cuda.empty_cache()
+    return {"workload": "n-body %d bodies (FP32), steps 3-%d" % (n, 2 + steps), "ms_per_step": t * 1e3,
+            "bodies": live0, "tflops": flop / t / 1e12, "fp32_fma_peak_tflops": peak / 1e12,
+            "frac_of_fma_peak": flop / t / peak, "bound": "alu", "flop_per_pair": 28}
 
 
 def bench_batched(n_inst=256, steps=20, one_by_one_steps=3):
@@ -425,6 +608,23 @@ def bench_served(seconds=20.0, n_jobs=10000, arena_gb=64, lo=128, hi=4096, steps
     return out
 
 
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel on this workload (None until captured for the kernel as it is).
+TRAFFIC = {}
+
+
+def roofline(phases, peak, peak_kind):
+    """HBM roofline of the method kernel with the largest share of the step."""
+    p = max(PHASES, key=lambda q: phases[q]["method_ms_per_step"])
+    ph = phases[p]
+    achieved = ph["gbs"]
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": TRAFFIC.get(p), "kernel": ph["kernel"], "phase": p,
+            "algorithmic_bytes_per_launch": ph["bytes_per_launch"], "launch_ms": ph["method_ms_per_step"],
+            "timing": "CUDA events on the launching stream around every launch of the timed steps",
+            "peak_source": ("measured hbm_gbs" if peak_kind == "measured" else "fallback 6.8 TB/s")}
+
+
 def main():
     args = _args()
     rank = int(os.environ.get("RANK", 0))
@@ -470,16 +670,11 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single"),
         "alloc_free_per_s": allocfree / dev_s,
-        "phase_ms": r["phase_ms"], "clocks": r["clocks"],
+        "phases": r["phases"], "clocks": r["clocks"],
         "e2e": {"value": e2e_visits / e2e_s, "unit": UNIT, "h2d_bytes_per_step": r["h2d"] / args.steps,
                 "d2h_bytes_per_step": r["d2h"] / args.steps},
         "gpu_launches": 10 * args.steps,
-        "roofline": {"bound": "hbm", "achieved": r["f1_gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": r["f1_gbs"] / peak, "traffic": None,
-                     "kernel": "dsr_doall_kernel<MFishChoose> (fish-choice method kernel)",
-                     "algorithmic_bytes_per_launch": r["f1_bytes"], "launch_ms": r["f1_ms"],
-                     "peak_source": peak_kind + " hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
-                     else "fallback 6.8 TB/s"},
+        "roofline": roofline(r["phases"], peak, peak_kind),
     }
     if not args.no_cpu_baseline:
         rate, n, el = oracle_wator_rate(args.cpu_seconds)
@@ -489,8 +684,10 @@ def main():
         # the other halves of the metric: batched vs plain, alloc+free/s, the
         # streaming do-all against the HBM roofline, and the served form
         line["batched"] = bench_batched()
-        line["alloc_free_microbench"] = bench_alloc_free()
-        line["streaming_doall"] = bench_streaming_doall()
+        line["alloc_free_microbench"] = bench_alloc_sweep()
+        line["streaming_doall"] = bench_streaming_sweep()
+        line["gol_64"] = bench_gol()
+        line["nbody_65536"] = bench_nbody()
         if args.served_seconds > 0:
             line["served"] = bench_served(args.served_seconds)
             # the same arrival process with jobs small enough to finish inside

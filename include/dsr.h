@@ -55,6 +55,8 @@ enum {
 #define DSR_CTR_ALLOCS 1u  /* objects created by dsr_new */
 #define DSR_CTR_FREES 2u   /* objects deleted by dsr_delete */
 #define DSR_CTR_BLOCKS 3u  /* blocks taken from the free bitmap (slow path) */
+#define DSR_CTR_APP0 4u    /* 4 .. 7: counted by applications (wa-tor: successful moves) */
+#define DSR_CTR_COUNT 8u
 
 /* Device-side sticky error bits (dsr_stats.error_flags). */
 #define DSR_ERR_OOM 1u          /* dsr_new found no free block; it returned DSR_NULL */
@@ -207,7 +209,7 @@ int dsr_row_words(const dsr_heap* heap, int type);
  * is the sum of object hashes modulo 2^64. */
 int dsr_heap_hash(dsr_heap* heap, int type, void* hash_dev, void* stream);
 
-/* Event counters (DSR_CTR_* order) summed over SMs: out[4]. Synchronises
+/* Event counters (DSR_CTR_* order) summed over SMs: out[DSR_CTR_COUNT]. Synchronises
  * `stream`. */
 int dsr_heap_counters(dsr_heap* heap, void* stream, uint64_t* out);
 
@@ -267,6 +269,18 @@ const char* dsr_last_cuda_error(void);
 int dsr_bench_alloc(dsr_heap* heap, uint64_t n_threads, int n_types_used, uint64_t seed, void* refs_dev,
                     void* stream);
 int dsr_bench_free(dsr_heap* heap, uint64_t n_threads, const void* refs_dev, void* stream);
+/* dsr_bench_churn: a mixed kernel over the handles of dsr_bench_alloc. Thread
+ * i with mix(seed, i) odd (half of them) deletes refs_dev[i] and creates a
+ * replacement of type (mix(seed + 1, i) mod n_types_used) holding i in field
+ * 0, so deletes and creates of many warps run interleaved. *n_replaced_dev
+ * (uint64, device, caller-zeroed) receives the number of replacements. */
+int dsr_bench_churn(dsr_heap* heap, uint64_t n_threads, int n_types_used, uint64_t seed, void* refs_dev,
+                    void* n_replaced_dev, void* stream);
+/* dsr_bench_fma: an FP32 FMA throughput probe, the ALU ceiling of the n-body
+ * force kernel. Every thread runs 8 independent FMA chains of `iters` steps
+ * and writes one float to out_dev[thread]; the grid is `ctas` x 256 threads.
+ * FLOPs = ctas * 256 * 8 * iters * 2. */
+int dsr_bench_fma(float* out_dev, int ctas, int iters, void* stream);
 
 #ifdef __cplusplus
 }

@@ -76,7 +76,8 @@ int dsr_gol_batch_destroy(dsr_gol_batch* b);
  *               shark_gain; timer >= shark_breed: leave a new Shark (timer 0,
  *               energy shark_energy0) behind and reset timer.
  * Workspace: uint64 grid (0 empty, else (handle << 2) | kind), uint64 claim
- * and uint32 intent per cell, plus the step counter. */
+ * and uint32 intent per cell, plus the step counter. Each successful move (F2
+ * and S2 winners) adds one to the heap's DSR_CTR_APP0 event counter. */
 enum {
     DSR_METHOD_WATOR_F1 = 200,
     DSR_METHOD_WATOR_F2 = 201,
@@ -103,6 +104,18 @@ int dsr_wator_step(dsr_wator* w, int n_steps, void* stream);
 /* Device uint8[W*H] occupancy snapshot (0/1/2) of the current state. */
 int dsr_wator_kinds(dsr_wator* w, void* kind_out_dev, void* stream);
 int dsr_wator_destroy(dsr_wator* w);
+/* Per-phase timing (a measurement aid; the paper times whole runs). With
+ * max_steps > 0, creates 11 CUDA events per step for the next max_steps
+ * steps (device current = the heap's); each of those steps then records them
+ * on its stream at its start and after every scan and method kernel. 0 frees
+ * them. Events cost a few microseconds of host time per step and nothing on
+ * the device. DSR_E_CUDA if an event cannot be created (none are kept). */
+int dsr_wator_phase_timing(dsr_wator* w, int max_steps);
+/* Waits for the last recorded step, then writes the summed device
+ * milliseconds of the steps recorded since the last call: out_ms[0..4] the
+ * method kernels of F1, F2, S0, S1, S2, out_ms[5..9] their scans; *steps =
+ * the number of steps. Starts a new window (the events are reused). */
+int dsr_wator_phase_times(dsr_wator* w, double* out_ms /* 10 */, int* steps);
 
 /* ---- batched wa-tor ----------------------------------------------------------
  * Many independent wa-tor instances (each with its own sizes, parameters and

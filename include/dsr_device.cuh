@@ -67,7 +67,7 @@ struct dsr_dev_heap {
     dsr_u64* R_mask;      /* do-all block list: occupied-slot snapshot */
     uint32_t* R_count;    /* entries in R (zero between do-alls) */
     uint32_t* R_done;     /* CTAs of the current method kernel that finished */
-    dsr_u64* ctr;         /* [DSR_CTR_SLOTS][4] event counters, one row per SM */
+    dsr_u64* ctr;         /* [DSR_CTR_SLOTS][DSR_CTR_COUNT] event counters, one row per SM */
     uint32_t* slow;       /* [DSR_MAX_TYPES] slow-path block initialisations in flight */
     dsr_u64* dbg;         /* first failed device check (code << 48 | value), checked builds only */
     uint32_t slow_max;    /* at most this many in flight per type before leaders wait */
@@ -147,7 +147,14 @@ __device__ __forceinline__ unsigned dsr_lane() {
 __device__ __forceinline__ void dsr_count(dsr_u64* ctr, unsigned k, dsr_u64 n) {
     unsigned smid;
     asm("mov.u32 %0, %%smid;" : "=r"(smid));
-    atomicAdd(ctr + (smid % DSR_CTR_SLOTS) * 4 + k, n);
+    atomicAdd(ctr + (smid % DSR_CTR_SLOTS) * DSR_CTR_COUNT + k, n);
+}
+
+/* Count one event per calling lane: one atomic per warp and heap. */
+__device__ __forceinline__ void dsr_count_lanes(dsr_u64* ctr, unsigned k) {
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, (dsr_u64)reinterpret_cast<uintptr_t>(ctr));
+    if (dsr_lane() == (unsigned)(__ffs(peers) - 1)) dsr_count(ctr, k, (dsr_u64)__popc(peers));
 }
 
 __device__ __forceinline__ void dsr_backoff(unsigned tries) {

@@ -251,8 +251,9 @@ class Wator:
             self._h = None
 
     def step(self, n=1):
-        """Advance n steps; returns int64[n, 4] events (fish births, eaten, shark births, starved)."""
-        ev = np.zeros((max(n, 1), 4), dtype=np.int64)
+        """Advance n steps; returns int64[n, 6] events (fish births, eaten, shark
+        births, starved, fish moves, shark moves)."""
+        ev = np.zeros((max(n, 1), 6), dtype=np.int64)
         lib().orc_wator_step(self._h, n, _ptr(ev))
         return ev[:n]
 

@@ -95,8 +95,8 @@ typedef struct orc_wator orc_wator;
 /* kind0[W*H]: 0 empty, 1 fish, 2 shark. */
 orc_wator* orc_wator_create(const orc_wator_params* p, const uint8_t* kind0);
 void       orc_wator_destroy(orc_wator* w);
-/* events_out (may be NULL) receives, per step, 4 counts:
- * fish births, fish eaten, shark births, sharks starved. */
+/* events_out (may be NULL) receives, per step, 6 counts: fish births, fish
+ * eaten, shark births, sharks starved, fish moves, shark moves. */
 void       orc_wator_step(orc_wator* w, int n_steps, int64_t* events_out);
 void       orc_wator_counts(const orc_wator* w, int64_t* n_fish, int64_t* n_shark);
 void       orc_wator_hash(const orc_wator* w, uint64_t* fish_hash, uint64_t* shark_hash);

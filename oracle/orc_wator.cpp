@@ -104,7 +104,7 @@ extern "C" void orc_wator_step(orc_wator* w, int n_steps, int64_t* events_out) {
     const auto& P = w->p;
     for (int s = 0; s < n_steps; ++s) {
         const uint64_t t = (uint64_t)w->step;
-        int64_t fish_births = 0, eaten = 0, shark_births = 0, starved = 0;
+        int64_t fish_births = 0, eaten = 0, shark_births = 0, starved = 0, fish_moves = 0, shark_moves = 0;
 
         // ---- F1: fish choose a target among empty neighbours and claim it.
         std::vector<int64_t> fl = w->fish.live();
@@ -129,6 +129,7 @@ extern "C" void orc_wator_step(orc_wator* w, int n_steps, int64_t* events_out) {
             auto& f = w->fish.obj[fl[k]];
             int64_t c = w->cell_of(f[0], f[1]);
             if (w->claim[tgt] != c) continue;
+            ++fish_moves;
             w->kind[tgt] = FISH;
             w->occupant[tgt] = fl[k];
             f[0] = (int32_t)(tgt % P.W);
@@ -186,6 +187,7 @@ extern "C" void orc_wator_step(orc_wator* w, int n_steps, int64_t* events_out) {
             auto& sh = w->shark.obj[sl[k]];
             int64_t c = w->cell_of(sh[0], sh[1]);
             if (w->claim[tgt] != c) continue;
+            ++shark_moves;
             if (w->kind[tgt] == FISH) {
                 w->fish.remove(w->occupant[tgt]);
                 sh[3] += P.shark_gain;
@@ -210,10 +212,13 @@ extern "C" void orc_wator_step(orc_wator* w, int n_steps, int64_t* events_out) {
             if (tgt >= 0) w->claim[tgt] = LLONG_MAX;
 
         if (events_out) {
-            events_out[4 * s + 0] = fish_births;
-            events_out[4 * s + 1] = eaten;
-            events_out[4 * s + 2] = shark_births;
-            events_out[4 * s + 3] = starved;
+            int64_t* e = events_out + 6 * s;
+            e[0] = fish_births;
+            e[1] = eaten;
+            e[2] = shark_births;
+            e[3] = starved;
+            e[4] = fish_moves;
+            e[5] = shark_moves;
         }
         w->step += 1;
     }

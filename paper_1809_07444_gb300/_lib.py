@@ -16,6 +16,7 @@ MAX_LEVELS = 6
 
 OK, E_INVALID, E_OOM, E_CUDA, E_DEVICE, E_TOO_LARGE = 0, 1, 2, 3, 4, 5
 NOALLOC_MAX_SLOTS = 16384
+CTR_COUNT = 8  # event counters per heap (DSR_CTR_COUNT)
 ERR_OOM, ERR_RETRY, ERR_DOUBLE_FREE, ERR_BAD_HANDLE, ERR_CAPACITY = 1, 2, 4, 8, 16
 
 METHOD_COUNT, METHOD_STREAM_ADD, METHOD_DELETE_IF, METHOD_CLONE = 1, 2, 3, 4
@@ -99,6 +100,8 @@ SIGNATURES = {
     "dsr_last_cuda_error": (C.c_char_p, []),
     "dsr_bench_alloc": (_i, [_vp, _u64, _i, _u64, _vp, _vp]),
     "dsr_bench_free": (_i, [_vp, _u64, _vp, _vp]),
+    "dsr_bench_churn": (_i, [_vp, _u64, _i, _u64, _vp, _vp, _vp]),
+    "dsr_bench_fma": (_i, [_vp, _i, _i, _vp]),
     "dsr_gol_types": (_i, [C.POINTER(TypeDesc)]),
     "dsr_gol_workspace_bytes": (_i, [_i, _i, C.POINTER(_sz)]),
     "dsr_gol_create": (_i, [_vp, _i, _i, _vp, _vp, _vp, C.POINTER(_vp)]),
@@ -110,6 +113,8 @@ SIGNATURES = {
     "dsr_wator_step": (_i, [_vp, _i, _vp]),
     "dsr_wator_kinds": (_i, [_vp, _vp, _vp]),
     "dsr_wator_destroy": (_i, [_vp]),
+    "dsr_wator_phase_timing": (_i, [_vp, _i]),
+    "dsr_wator_phase_times": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i)]),
     "dsr_nbody_types": (_i, [C.POINTER(TypeDesc)]),
     "dsr_nbody_workspace_bytes": (_i, [_vp, _u64, C.POINTER(_sz)]),
     "dsr_nbody_create": (_i, [_vp, C.POINTER(NBodyParams), _vp, _i, _vp, _u64, _vp, C.POINTER(_vp)]),

@@ -100,6 +100,22 @@ class Wator:
         st = self.heap.stats()
         return st["live_objects"][0], st["live_objects"][1]
 
+    PHASES = ("F1", "F2", "S0", "S1", "S2")
+
+    def phase_timing(self, max_steps):
+        """Record CUDA events around every scan and method kernel of the next
+        max_steps steps (0 turns it off)."""
+        L.check(self.lib.dsr_wator_phase_timing(self.handle, int(max_steps)), "dsr_wator_phase_timing")
+
+    def phase_times(self):
+        """({phase: method-kernel ms}, {phase: scan ms}, steps) summed over the
+        steps recorded since the last call."""
+        out = (C.c_double * 10)()
+        n = C.c_int(0)
+        L.check(self.lib.dsr_wator_phase_times(self.handle, out, C.byref(n)), "dsr_wator_phase_times")
+        return ({p: out[i] for i, p in enumerate(self.PHASES)}, {p: out[5 + i] for i, p in enumerate(self.PHASES)},
+                n.value)
+
     def dump(self):
         """(fish int32[n, 3] sorted, sharks int32[m, 4] sorted)."""
         f, _ = self.heap.dump(0)

@@ -460,14 +460,14 @@ extern "C" int dsr_heap_stats(dsr_heap* h, void* stream, dsr_stats* out) {
 
 extern "C" int dsr_heap_counters(dsr_heap* h, void* stream, uint64_t* out) {
     if (!h || !out) return DSR_E_INVALID;
-    dsr_u64 rows[DSR_CTR_SLOTS][4];
+    dsr_u64 rows[DSR_CTR_SLOTS][DSR_CTR_COUNT];
     cudaError_t e = cudaMemcpyAsync(rows, h->dev.ctr, sizeof rows, cudaMemcpyDeviceToHost, dsr__stream(stream));
     if (!e) e = cudaStreamSynchronize(dsr__stream(stream));
     if (e) {
         dsr__set_cuda_error(e, "dsr_heap_counters");
         return DSR_E_CUDA;
     }
-    for (int k = 0; k < 4; ++k) {
+    for (unsigned k = 0; k < DSR_CTR_COUNT; ++k) {
         out[k] = 0;
         for (unsigned r = 0; r < DSR_CTR_SLOTS; ++r) out[k] += rows[r][k];
     }
@@ -705,6 +705,60 @@ __global__ void k_bench_alloc(const __grid_constant__ dsr_dev_heap H, dsr_u64 n,
 __global__ void k_bench_free(const __grid_constant__ dsr_dev_heap H, dsr_u64 n, const dsr_ref* refs) {
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
     for (dsr_u64 i = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dsr_delete(H, refs[i]);
+}
+
+__global__ void k_bench_churn(const __grid_constant__ dsr_dev_heap H, dsr_u64 n, int n_types, dsr_u64 seed,
+                              dsr_ref* refs, unsigned long long* n_replaced) {
+    const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
+    unsigned long long mine = 0;
+    for (dsr_u64 i = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (!(dsr_mix64(seed ^ (i * DSR_GAMMA)) & 1)) continue;
+        dsr_delete(H, refs[i]);
+        const int T = (int)(dsr_mix64((seed + 1) ^ (i * DSR_GAMMA)) % (dsr_u64)n_types);
+        const dsr_ref r = dsr_new(H, T);
+        if (r != DSR_NULL) *dsr_field<int32_t>(H, T, r, 0) = (int32_t)i;
+        refs[i] = r;
+        ++mine;
+    }
+    // one atomic per warp
+    for (int o = 16; o; o >>= 1) mine += __shfl_down_sync(0xFFFFFFFFu, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(n_replaced, mine);
+}
+
+// 8 independent chains per thread keep the FMA pipes busy; the result is
+// written so that nothing is eliminated.
+__global__ void k_bench_fma(float* out, int iters) {
+    const float b = 0.999999f, c = 1e-7f;
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], b, c);
+    }
+    float sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += a[k];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
+extern "C" int dsr_bench_churn(dsr_heap* h, uint64_t n, int n_types_used, uint64_t seed, void* refs_dev,
+                               void* n_replaced_dev, void* stream) {
+    if (!h || !refs_dev || !n_replaced_dev || n_types_used < 1 || n_types_used > (int)h->layout.n_types || n == 0)
+        return DSR_E_INVALID;
+    for (int t = 0; t < n_types_used; ++t)
+        if (h->layout.field_bytes[t][0] != 4) return DSR_E_INVALID;
+    uint64_t ctas = (n + 255) / 256;
+    if (ctas > (uint64_t)h->sm_count * 8) ctas = (uint64_t)h->sm_count * 8;
+    k_bench_churn<<<(unsigned)ctas, 256, 0, dsr__stream(stream)>>>(
+        h->dev, n, n_types_used, seed, static_cast<dsr_ref*>(refs_dev), static_cast<unsigned long long*>(n_replaced_dev));
+    return dsr__check_launch("k_bench_churn");
+}
+
+extern "C" int dsr_bench_fma(float* out_dev, int ctas, int iters, void* stream) {
+    if (!out_dev || ctas < 1 || iters < 1) return DSR_E_INVALID;
+    k_bench_fma<<<ctas, 256, 0, dsr__stream(stream)>>>(out_dev, iters);
+    return dsr__check_launch("k_bench_fma");
 }
 
 extern "C" int dsr_bench_alloc(dsr_heap* h, uint64_t n, int n_types_used, uint64_t seed, void* refs_dev,

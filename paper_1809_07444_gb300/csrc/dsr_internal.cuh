@@ -21,7 +21,7 @@ struct dsr_heap {
 };
 
 // Arena header (first DSR_HEADER_BYTES bytes of the arena).
-#define DSR_HEADER_BYTES 16384u
+#define DSR_HEADER_BYTES 32768u
 #define DSR_HDR_ERR 0u
 #define DSR_HDR_INJECT 4u
 #define DSR_HDR_RCOUNT 8u
@@ -29,7 +29,7 @@ struct dsr_heap {
 #define DSR_HDR_STATS 256u  // dsr_u64[1 + 3 * DSR_MAX_TYPES]
 #define DSR_HDR_SLOW 192u   // uint32[DSR_MAX_TYPES] slow paths in flight
 #define DSR_HDR_DBG 224u    // dsr_u64 first failed device check + 24 scratch bytes
-#define DSR_HDR_CTR 4096u   // dsr_u64[DSR_CTR_SLOTS][4] event counters
+#define DSR_HDR_CTR 4096u   // dsr_u64[DSR_CTR_SLOTS][DSR_CTR_COUNT] event counters (16 KB)
 
 void dsr__set_cuda_error(cudaError_t e, const char* where);
 int dsr__check_launch(const char* where);
@@ -44,10 +44,14 @@ void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s);
 
 // Run a do-all: scan + compaction of allocated[type] into R, then the method
 // kernel over the listed blocks.
+// ev_scan / ev_run (optional): recorded on s after the scan and after the
+// method kernel, for per-phase timing.
 template <class M>
-int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t s, bool with_scan = true) {
+int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t s, bool with_scan = true,
+               cudaEvent_t ev_scan = nullptr, cudaEvent_t ev_run = nullptr) {
     if (type < 0 || type >= h->dev.n_types) return DSR_E_INVALID;
     if (with_scan) dsr__launch_scan(h, type, s);
+    if (ev_scan) cudaEventRecord(ev_scan, s);
     static int grid_cache[17] = {0};
     const int threads = h->tune.threads;
     int& grid = grid_cache[threads / 64];
@@ -63,7 +67,9 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
     if ((dsr_u64)g > cap_grid) g = (int)cap_grid;
     if (g < 1) g = 1;
     dsr_doall_kernel<M><<<g, threads, 0, s>>>(h->dev, type, args);
-    return dsr__check_launch("dsr_doall_kernel");
+    const int rc = dsr__check_launch("dsr_doall_kernel");
+    if (ev_run) cudaEventRecord(ev_run, s);
+    return rc;
 }
 
 // Application method dispatch (defined in the application files).

@@ -81,6 +81,7 @@ __device__ __forceinline__ void fish_move(const dsr_dev_heap& H, const WatorInst
     const uint32_t tgt = I.intent[c];
     if (tgt != NO_MOVE && !cell_ok(H, I, tgt, 7)) return;
     if (tgt == NO_MOVE || I.claim[tgt] != claim_key(t, 0, c)) return;
+    dsr_count_lanes(H.ctr, DSR_CTR_APP0);
     I.grid[tgt] = (self << 2) | K_FISH;
     *px = (int32_t)(tgt % (uint32_t)I.p.W);
     *py = (int32_t)(tgt / (uint32_t)I.p.W);
@@ -143,6 +144,7 @@ __device__ __forceinline__ void shark_move(const dsr_dev_heap& H, const WatorIns
     const uint32_t tgt = I.intent[c];
     if (tgt != NO_MOVE && !cell_ok(H, I, tgt, 7)) return;
     if (tgt == NO_MOVE || I.claim[tgt] != claim_key(t, 1, c)) return;
+    dsr_count_lanes(H.ctr, DSR_CTR_APP0);
     const dsr_u64 g = I.grid[tgt];
     int32_t* energy = dsr_field<int32_t>(H, SHARK, self, ENERGY);
     if ((g & 3) == K_FISH) {
@@ -328,7 +330,17 @@ int launch_kinds(const dsr_heap* heap, const WatorInst& I, void* out, cudaStream
 struct dsr_wator {
     dsr_heap* heap;
     WatorInst inst;
+    // phase timing: kPhaseEvents events per step, created when enabled
+    std::vector<cudaEvent_t> ev;
+    int ev_steps = 0;  // steps recorded in the current window
 };
+constexpr int kPhaseEvents = 11;  // step start, then after each scan and each method kernel
+
+static void free_events(dsr_wator* w) {
+    for (cudaEvent_t e : w->ev) cudaEventDestroy(e);
+    w->ev.clear();
+    w->ev_steps = 0;
+}
 
 extern "C" int dsr_wator_types(dsr_type_desc* out) {
     if (!out) return DSR_E_INVALID;
@@ -364,13 +376,60 @@ extern "C" int dsr_wator_step(dsr_wator* w, int n_steps, void* stream) {
     cudaStream_t s = dsr__stream(stream);
     dsr_heap* h = w->heap;
     for (int i = 0; i < n_steps; ++i) {
-        int rc = dsr__doall<MFishChoose>(h, FISH, w->inst, s);
-        if (!rc) rc = dsr__doall<MFishMove>(h, FISH, w->inst, s);
-        if (!rc) rc = dsr__doall<MSharkStarve>(h, SHARK, w->inst, s);
-        if (!rc) rc = dsr__doall<MSharkChoose>(h, SHARK, w->inst, s);
-        if (!rc) rc = dsr__doall<MSharkMove>(h, SHARK, w->inst, s);
+        cudaEvent_t* e = nullptr;
+        if ((size_t)(w->ev_steps + 1) * kPhaseEvents <= w->ev.size()) {
+            e = w->ev.data() + (size_t)w->ev_steps++ * kPhaseEvents;
+            cudaEventRecord(e[0], s);
+        }
+        auto E = [&](int k) { return e ? e[k] : nullptr; };
+        int rc = dsr__doall<MFishChoose>(h, FISH, w->inst, s, true, E(1), E(2));
+        if (!rc) rc = dsr__doall<MFishMove>(h, FISH, w->inst, s, true, E(3), E(4));
+        if (!rc) rc = dsr__doall<MSharkStarve>(h, SHARK, w->inst, s, true, E(5), E(6));
+        if (!rc) rc = dsr__doall<MSharkChoose>(h, SHARK, w->inst, s, true, E(7), E(8));
+        if (!rc) rc = dsr__doall<MSharkMove>(h, SHARK, w->inst, s, true, E(9), E(10));
         if (rc) return rc;
     }
+    return DSR_OK;
+}
+
+extern "C" int dsr_wator_phase_timing(dsr_wator* w, int max_steps) {
+    if (!w || max_steps < 0) return DSR_E_INVALID;
+    free_events(w);
+    for (size_t k = 0; k < (size_t)max_steps * kPhaseEvents; ++k) {
+        cudaEvent_t e;
+        const cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) {
+            free_events(w);
+            dsr__set_cuda_error(err, "cudaEventCreate");
+            return DSR_E_CUDA;
+        }
+        w->ev.push_back(e);
+    }
+    return DSR_OK;
+}
+
+extern "C" int dsr_wator_phase_times(dsr_wator* w, double* out_ms, int* steps) {
+    if (!w || !out_ms || !steps) return DSR_E_INVALID;
+    for (int k = 0; k < 10; ++k) out_ms[k] = 0;
+    *steps = w->ev_steps;
+    if (w->ev_steps) {
+        cudaError_t err = cudaEventSynchronize(w->ev[(size_t)w->ev_steps * kPhaseEvents - 1]);
+        for (int i = 0; i < w->ev_steps && err == cudaSuccess; ++i) {
+            const cudaEvent_t* e = w->ev.data() + (size_t)i * kPhaseEvents;
+            for (int p = 0; p < 5 && err == cudaSuccess; ++p) {
+                float scan = 0, run = 0;
+                err = cudaEventElapsedTime(&scan, e[2 * p], e[2 * p + 1]);
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&run, e[2 * p + 1], e[2 * p + 2]);
+                out_ms[p] += run;
+                out_ms[5 + p] += scan;
+            }
+        }
+        if (err != cudaSuccess) {
+            dsr__set_cuda_error(err, "dsr_wator_phase_times");
+            return DSR_E_CUDA;
+        }
+    }
+    w->ev_steps = 0;
     return DSR_OK;
 }
 
@@ -380,6 +439,7 @@ extern "C" int dsr_wator_kinds(dsr_wator* w, void* kind_out_dev, void* stream) {
 }
 
 extern "C" int dsr_wator_destroy(dsr_wator* w) {
+    if (w) free_events(w);
     delete w;
     return DSR_OK;
 }

@@ -112,10 +112,15 @@ class Heap:
         }
 
     def counters(self, stream=None):
-        """Cumulative event counts: visits, allocs, frees, blocks taken from free."""
-        out = (C.c_uint64 * 4)()
+        """Cumulative event counts: visits, allocs, frees, blocks taken from
+        free, and the application counters app0..app3 (wa-tor: app0 counts
+        successful moves)."""
+        out = (C.c_uint64 * L.CTR_COUNT)()
         L.check(self.lib.dsr_heap_counters(self.handle, _stream_ptr(stream), out), "dsr_heap_counters")
-        return {"visits": int(out[0]), "allocs": int(out[1]), "frees": int(out[2]), "new_blocks": int(out[3])}
+        d = {"visits": int(out[0]), "allocs": int(out[1]), "frees": int(out[2]), "new_blocks": int(out[3])}
+        for k in range(4, L.CTR_COUNT):
+            d["app%d" % (k - 4)] = int(out[k])
+        return d
 
     def snapshot(self):
         """Metadata of a quiescent heap as numpy arrays (for the invariant checker)."""

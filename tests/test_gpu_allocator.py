@@ -203,3 +203,36 @@ def test_three_level_bitmaps_stay_consistent():
     st = h.stats()
     assert st["free_blocks"] == st["n_blocks"] and st["error_flags"] == 0
     check_invariants(h, [0])
+
+
+def test_churn_kernel_replaces_half_and_keeps_the_heap_consistent():
+    # deletes and creates interleaved in one kernel: the live set is the
+    # thread indices again (replacements hold the same index)
+    h = _heap(20000)
+    n = 200_000
+    refs = torch.empty(n, dtype=torch.int64, device="cuda")
+    h.bench_alloc(refs, 3, 21)
+    nrep = torch.zeros(1, dtype=torch.int64, device="cuda")
+    L.check(h.lib.dsr_bench_churn(h.handle, n, 3, 99, C.c_void_p(refs.data_ptr()), C.c_void_p(nrep.data_ptr()),
+                                  None), "dsr_bench_churn")
+    torch.cuda.synchronize()
+    import oracle as O
+    G = 0x9E3779B97F4A7C15
+    want = sum(O.mix64(99 ^ ((i * G) & 0xFFFFFFFFFFFFFFFF)) & 1 for i in range(n))
+    assert int(nrep.item()) == want
+    r = refs.cpu().numpy().view(np.uint64)
+    assert (r != np.uint64(L.NULL_REF)).all() and len(np.unique(r)) == n
+    live = check_invariants(h)
+    assert live.sum() == n
+    ids = np.concatenate([h.dump(t)[0][:, 0].astype(np.int64) for t in range(3)])
+    assert np.array_equal(np.sort(ids), np.arange(n))
+    h.bench_free(refs)
+    st = h.stats()
+    assert st["error_flags"] == 0 and st["free_blocks"] == st["n_blocks"]
+
+
+def test_fma_probe_runs():
+    out = torch.empty(4 * 256, dtype=torch.float32, device="cuda")
+    L.check(L.load().dsr_bench_fma(C.c_void_p(out.data_ptr()), 4, 1000, None), "dsr_bench_fma")
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()

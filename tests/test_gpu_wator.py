@@ -15,8 +15,14 @@ def _run_pair(W, H, kind0, seed, steps, full_every=1, invariants_every=None):
     gpu, ref = Wator(W, H, kind0, seed), O.Wator(W, H, kind0, seed)
     assert gpu.hash() == ref.hash()
     for t in range(1, steps + 1):
+        c0 = gpu.heap.counters()
         gpu.step(1)
-        ref.step(1)
+        ev = ref.step(1)[0]
+        c1 = gpu.heap.counters()
+        # event counters: moves, births and deaths of the step
+        assert c1["app0"] - c0["app0"] == ev[4] + ev[5], "moves at step %d" % t
+        assert c1["allocs"] - c0["allocs"] == ev[0] + ev[2], "births at step %d" % t
+        assert c1["frees"] - c0["frees"] == ev[1] + ev[3], "deaths at step %d" % t
         hg, hr = gpu.hash(), ref.hash()
         assert hg == hr, "step %d: hash %s vs oracle %s" % (t, hg, hr)
         if t % full_every == 0 or t == steps:
@@ -52,6 +58,19 @@ def test_wator_extinction_and_degenerate_starts():
     k = np.zeros((32, 32), np.uint8)
     k[5, 5] = 1
     _run_pair(32, 32, k, 3, 40, full_every=5)
+
+
+def test_wator_phase_timing_records_every_step():
+    w = Wator(64, 64, WL.wator_initial(64, 64, 1), 1)
+    w.phase_timing(4)
+    w.step(6)  # events for the first four only
+    run, scan, n = w.phase_times()
+    assert n == 4 and all(v > 0 for v in run.values()) and all(v > 0 for v in scan.values())
+    w.step(2)
+    assert w.phase_times()[2] == 2  # a new window reuses the events
+    w.phase_timing(0)
+    w.step(1)
+    assert w.phase_times()[2] == 0
 
 
 def test_wator_2048_full_size_hash_parity():

@@ -65,7 +65,7 @@ def test_shark_prefers_fish_and_gains_energy():
     k[0, 0] = S
     w = O.Wator(4, 4, k, seed=11)
     ev = w.step(1)
-    assert ev[0].tolist() == [0, 1, 0, 0]
+    assert ev[0].tolist() == [0, 1, 0, 0, 0, 1]  # no fish can move; the shark moves once
     assert w.counts() == (14, 1)
     _, sh = w.dump()
     assert sh[0, 3] == 5 - 1 + 3 and sh[0, 2] == 1
@@ -85,6 +85,15 @@ def test_shark_breeds_on_tenth_step_among_plenty_of_fish():
     assert ev[0, 1] == 1 and ev[0, 2] == 1
     _, sh = w.dump()
     assert sorted((r[2], r[3]) for r in sh) == [(0, 5), (0, 5 + 10 * 2)]
+
+
+def test_lone_fish_moves_every_step_and_breeds_on_the_third():
+    k = np.zeros((5, 5), np.uint8)
+    k[2, 2] = F
+    w = O.Wator(5, 5, k, seed=3)
+    ev = w.step(3)
+    assert ev[:, 4].tolist() == [1, 1, 1] and ev[:, 0].tolist() == [0, 0, 1]
+    assert w.counts() == (2, 0)
 
 
 def test_fish_only_full_grid_never_moves():
@@ -108,6 +117,8 @@ def test_conservation_exclusivity_and_locality(W, H, seed, steps):
         f2, s2 = w.counts()
         assert f2 == nf + ev[0] - ev[1]
         assert s2 == ns + ev[2] - ev[3]
+        # births happen only on a move; a shark eats only by moving; nobody moves twice
+        assert ev[0] <= ev[4] <= nf and ev[2] <= ev[5] and ev[1] <= ev[5] <= ns - ev[3]
         nf, ns = f2, s2
         g = w.grid()
         f, s = w.dump()
