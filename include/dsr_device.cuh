@@ -47,6 +47,7 @@ typedef dsr_u64 dsr_ref;
 #endif
 #define DSR_CTR_SLOTS 256u       /* event-counter rows (indexed by SM id) */
 #define DSR_SLOW_WAITS 64u       /* rounds a leader may wait for another initialisation */
+#define DSR_CHASE_ROUNDS 4       /* atomics on one block per search before searching again */
 
 /* One hierarchical bitmap: level l has nwords[l] 64-bit containers. */
 struct dsr_hbm {
@@ -176,6 +177,9 @@ __device__ __forceinline__ int dsr_nth_bit(dsr_u64 m, int n) {
     return pos;
 }
 
+__device__ __forceinline__ dsr_u64 dsr_rotr(dsr_u64 m, unsigned r) { return r ? (m >> r) | (m << (64 - r)) : m; }
+__device__ __forceinline__ dsr_u64 dsr_rotl(dsr_u64 m, unsigned r) { return r ? (m << r) | (m >> (64 - r)) : m; }
+
 /* The lowest min(k, popc(m)) set bits of m. */
 __device__ __forceinline__ dsr_u64 dsr_lowest_bits(dsr_u64 m, int k) {
     if (k >= __popcll(m)) return m;
@@ -237,19 +241,32 @@ __device__ __forceinline__ bool dsr_hb_clear(const dsr_hbm& b, dsr_u64 pos, bool
     return true;
 }
 
+/* 32-bit integer hash (the "lowbias32" finalizer published by C. Wellons,
+ * 2018): spreads consecutive or similar hints over all 32 bits. */
+__device__ __forceinline__ unsigned dsr_hash32(unsigned x) {
+    x ^= x >> 16;
+    x *= 0x7FEB352Du;
+    x ^= x >> 15;
+    x *= 0x846CA68Bu;
+    x ^= x >> 16;
+    return x;
+}
+
 /* try_find_set (Section 2.1, Section 2.4): descend from the top level, one
- * container read per level. At each level the search starts at a bit
- * position derived from `hint` and wraps, so that concurrent searchers spread
- * over the set bits. Returns -1 (FAIL) if a container on the way is empty,
- * which can happen while the bitmap is temporarily inconsistent. */
+ * container read per level. At each level the searcher takes one of the
+ * container's set bits, chosen uniformly by a hash of (hint, level), so that
+ * concurrent searchers with different hints spread evenly over the set bits
+ * (a "first set bit after an offset" rule would favour bits that follow long
+ * runs of zeros, and the first bit of a container whose high bits are zero).
+ * Returns -1 (FAIL) if a container on the way is empty, which can happen
+ * while the bitmap is temporarily inconsistent. */
 __device__ __forceinline__ long long dsr_hb_find(const dsr_hbm& b, unsigned hint) {
     dsr_u64 pos = 0;
     for (int l = b.n_levels - 1; l >= 0; --l) {
         const dsr_u64 w = dsr_ld_relaxed(b.lvl[l] + pos);
         if (w == 0) return -1;
-        const unsigned r = (hint >> (5 * (l & 3))) & 63;
-        const dsr_u64 rot = r ? ((w >> r) | (w << (64 - r))) : w;
-        const int k = (__ffsll((long long)rot) - 1 + (int)r) & 63;
+        const unsigned h = dsr_hash32(hint ^ ((unsigned)l * 0x9E3779B9u));
+        const int k = dsr_nth_bit(w, (int)__umulhi(h, (unsigned)__popcll(w)));
         pos = pos * 64 + (dsr_u64)k;
     }
     return (long long)pos;
@@ -389,19 +406,22 @@ __device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsi
             dsr_backoff(empty_rounds + 9);
             continue;
         }
-        // Take the lowest free slots of a snapshot; while the block still has
-        // free slots (as the atomic's return value shows) and more are
-        // wanted, take those too, without searching again.
+        // Take free slots of a snapshot, the first ones at or after a slot
+        // offset drawn from the hint (leaders that meet on one block then
+        // mostly ask for different slots); while the block still has free
+        // slots (as the atomic's return value shows) and more are wanted,
+        // take those too, for a few rounds, without searching again.
         dsr_u64* w = H.obj + b;
         dsr_u64 snap = dsr_ld_relaxed(w);
         if (snap == 0) {
             dsr_backoff(a);
             continue;
         }
+        const unsigned rot = dsr_hash32(hint + a) >> 26;
         dsr_u64 got = 0;
         bool emptied = false;
-        for (int r = 0; r < 64 && snap; ++r) {
-            const dsr_u64 want = dsr_lowest_bits(snap, k - __popcll(got));
+        for (int r = 0; r < DSR_CHASE_ROUNDS && snap; ++r) {
+            const dsr_u64 want = dsr_rotl(dsr_lowest_bits(dsr_rotr(snap, rot), k - __popcll(got)), rot);
             const dsr_u64 prev = dsr_atom_and_acq_rel(w, ~want);
             got |= prev & want;
             snap = prev & ~want;
@@ -567,6 +587,12 @@ __global__ void dsr_doall_kernel(const __grid_constant__ dsr_dev_heap H, int T,
     const dsr_u64 total = (dsr_u64)(*(volatile uint32_t*)H.R_count) << sh;
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
     for (dsr_u64 g = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        // total and stride are multiples of 32, so every lane of a warp runs
+        // the same iterations. Reconverge the warp at each one: lanes that
+        // drifted apart in a method's divergent code would otherwise reach
+        // dsr_new in smaller groups, and aggregation would serve fewer lanes
+        // per search.
+        __syncwarp();
         const dsr_u64 i = g >> sh;
         const unsigned s = (unsigned)(g & ((1u << sh) - 1));
         if (((H.R_mask[i] >> s) & 1ull) && dsr_check(H.R_bid[i] < H.M, H.err, H.dbg, 10, i))
@@ -622,6 +648,7 @@ __global__ void dsr_group_doall_kernel(const __grid_constant__ dsr_group_dev G, 
     const dsr_u64 total = (dsr_u64)(*(volatile uint32_t*)G.R_count) << sh;
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
     for (dsr_u64 g = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        __syncwarp();  // warp-uniform loop: reconverge as in dsr_doall_kernel
         const dsr_u64 i = g >> sh;
         const unsigned s = (unsigned)(g & ((1u << sh) - 1));
         if ((G.R_mask[i] >> s) & 1ull) {

@@ -2,8 +2,11 @@
  * Oracle for the DynaSOAr hot path (Springer, "DynaSOAr: Accelerating
  * Single-Method Multiple-Objects Applications on GPUs").
  *
- * TEST INFRASTRUCTURE ONLY. Plain, slow, single-threaded C++ that states what
- * the GPU path must compute. Only the test suite, the smoke check and the
+ * TEST INFRASTRUCTURE ONLY. Plain, slow C++ that states what the GPU path
+ * must compute. Single-threaded, except that the n-body force and partner
+ * loops may hand whole rows to std::thread workers (orc_set_threads): each
+ * row is still summed by one thread in index order, so the result does not
+ * depend on the thread count. Only the test suite, the smoke check and the
  * bench's CPU-baseline leg may load it. It shares no code, header, table or
  * constant generator with the CUDA library; it implements its own copy of the
  * counter-based generator from the published SplitMix64 definition.

@@ -70,7 +70,10 @@ struct MBirth {
 __global__ void k_gol_init(const __grid_constant__ dsr_dev_heap H, const uint8_t* alive0, dsr_ref* cell_ref,
                            int W, int Hh) {
     const int n = W * Hh;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int n32 = (n + 31) & ~31;  // warp-uniform trip count
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {
+        __syncwarp();  // whole-warp groups for dsr_new
+        if (i >= n) continue;
         const int alive = alive0[i] ? 1 : 0;
         const dsr_ref c = dsr_new(H, CELL);
         cell_ref[i] = c;

@@ -691,10 +691,16 @@ extern "C" int dsr_doall_run(dsr_heap* h, int type, int method, const void* args
 // ---------------------------------------------------------------------------
 // allocation microbenchmark kernels
 // ---------------------------------------------------------------------------
+// The microbenchmark loops run warp-uniform trip counts (the bound is
+// rounded up to whole warps) and reconverge the warp at every iteration, so
+// that each dsr_new / dsr_delete call sees the whole warp.
 __global__ void k_bench_alloc(const __grid_constant__ dsr_dev_heap H, dsr_u64 n, int n_types, dsr_u64 seed,
                               dsr_ref* refs) {
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
-    for (dsr_u64 i = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const dsr_u64 n32 = (n + 31) & ~31ull;
+    for (dsr_u64 i = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += stride) {
+        __syncwarp();
+        if (i >= n) continue;
         const int T = (int)(dsr_mix64(seed ^ (i * DSR_GAMMA)) % (dsr_u64)n_types);
         const dsr_ref r = dsr_new(H, T);
         if (r != DSR_NULL) *dsr_field<int32_t>(H, T, r, 0) = (int32_t)i;
@@ -704,15 +710,21 @@ __global__ void k_bench_alloc(const __grid_constant__ dsr_dev_heap H, dsr_u64 n,
 
 __global__ void k_bench_free(const __grid_constant__ dsr_dev_heap H, dsr_u64 n, const dsr_ref* refs) {
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
-    for (dsr_u64 i = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dsr_delete(H, refs[i]);
+    const dsr_u64 n32 = (n + 31) & ~31ull;
+    for (dsr_u64 i = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += stride) {
+        __syncwarp();
+        if (i < n) dsr_delete(H, refs[i]);
+    }
 }
 
 __global__ void k_bench_churn(const __grid_constant__ dsr_dev_heap H, dsr_u64 n, int n_types, dsr_u64 seed,
                               dsr_ref* refs, unsigned long long* n_replaced) {
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
+    const dsr_u64 n32 = (n + 31) & ~31ull;
     unsigned long long mine = 0;
-    for (dsr_u64 i = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        if (!(dsr_mix64(seed ^ (i * DSR_GAMMA)) & 1)) continue;
+    for (dsr_u64 i = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += stride) {
+        __syncwarp();
+        if (i >= n || !(dsr_mix64(seed ^ (i * DSR_GAMMA)) & 1)) continue;
         dsr_delete(H, refs[i]);
         const int T = (int)(dsr_mix64((seed + 1) ^ (i * DSR_GAMMA)) % (dsr_u64)n_types);
         const dsr_ref r = dsr_new(H, T);

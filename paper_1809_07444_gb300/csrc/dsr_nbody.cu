@@ -198,7 +198,10 @@ __global__ void k_merge(const __grid_constant__ dsr_dev_heap H, NbArgs a) {
 }
 
 __global__ void k_nbody_init(const __grid_constant__ dsr_dev_heap H, const float* rows, int n) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int n32 = (n + 31) & ~31;  // warp-uniform trip count
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n32; i += gridDim.x * blockDim.x) {
+        __syncwarp();  // whole-warp groups for dsr_new
+        if (i >= n) continue;
         const dsr_ref r = dsr_new(H, BODY);
         if (r == DSR_NULL) continue;
         *dsr_field<int32_t>(H, BODY, r, ID) = i;

@@ -238,7 +238,10 @@ struct GSharkMove {
 // One thread per cell: create the initial agents and clear the claim state.
 __global__ void k_wator_init(const __grid_constant__ dsr_dev_heap H, const uint8_t* kind0, WatorInst I) {
     const uint32_t n = (uint32_t)I.p.W * (uint32_t)I.p.H;
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const uint32_t n32 = (n + 31u) & ~31u;  // warp-uniform trip count
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n32; c += gridDim.x * blockDim.x) {
+        __syncwarp();  // whole-warp groups for dsr_new
+        if (c >= n) continue;
         const uint8_t k = kind0[c];
         dsr_u64 g = K_EMPTY;
         if (k == 1) {
