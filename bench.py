@@ -547,9 +547,18 @@ def bench_batched(n_inst=256, steps=20, one_by_one_steps=3):
     from paper_1809_07444_gb300 import workloads as WL
     from paper_1809_07444_gb300.apps import Wator, WatorBatch
 
+    from paper_1809_07444_gb300 import autotune as AT
+
     sides = [int(s) for s in WL.batched_sides(n_inst, 1)]
-    need = sum(WatorBatch.blocks_for(s, s) * 1000 + s * s * 24 for s in sides)
-    b = WatorBatch(need + (256 << 20), max_instances=n_inst)
+    # autotune threads / cap_min / fan-out on every fourth instance
+    sub = list(range(0, n_inst, 4))
+    t0 = time.perf_counter()
+    tun, tun_v, table = AT.tuned("%s/wator-batched-%d" % (torch.cuda.get_device_name(), n_inst),
+                                 AT.wator_batch_measure([sides[i] for i in sub], [1000 + i for i in sub]),
+                                 refresh=True)
+    tune_s = time.perf_counter() - t0
+    need = sum(WatorBatch.blocks_for(s, s) * 1100 + s * s * 24 for s in sides)
+    b = WatorBatch(need + (256 << 20), max_instances=n_inst, tuning=tun)
     slots = [b.add(s, s, WL.wator_initial(s, s, 1000 + i), 1000 + i) for i, s in enumerate(sides)]
     b.step(3)
     torch.cuda.synchronize()
@@ -583,7 +592,10 @@ def bench_batched(n_inst=256, steps=20, one_by_one_steps=3):
             "object_updates_per_s": vb, "one_by_one": {"object_updates_per_s": vp, "steps": one_by_one_steps,
                                                        "ms_per_step": t_p * 1e3 / one_by_one_steps,
                                                        "launches_per_step": 10 * n_inst},
-            "speedup_vs_one_by_one": vb / vp if vp else None, "launches_per_step": 10, "graph": True}
+            "speedup_vs_one_by_one": vb / vp if vp else None, "launches_per_step": 10, "graph": True,
+            "tuning": tun, "tuning_s": tune_s,
+            "tuning_table": {",".join(str(x) for x in k): v for k, v in (table or {}).items()},
+            "tuning_sample": "every fourth instance (%d), 5 timed steps per setting" % len(sub)}
 
 
 def bench_served(seconds=20.0, n_jobs=10000, arena_gb=64, lo=128, hi=4096, steps_lo=50, steps_hi=1000,

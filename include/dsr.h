@@ -79,6 +79,8 @@ typedef struct {
     int cap_min;        /* slots per block of the smallest type: 64 (paper, default) or 32 */
     int threads;        /* threads per CTA of do-all kernels: 64..1024, multiple of 64 (default 256) */
     int ctas_per_sm;    /* persistent do-all grid = ctas_per_sm x SM count (0 = occupancy limit) */
+    int fanout;         /* bits used per bitmap container (Section 2.1): 64 (paper, default), 32 or 16;
+                           0 = default. Smaller containers mean more levels but fewer searchers per word. */
 } dsr_tuning;
 
 typedef struct dsr_heap dsr_heap;
@@ -97,8 +99,10 @@ typedef struct {
 
 /* Where each metadata array lives inside the arena (byte offsets from the
  * arena base), for inspection of a quiescent heap. Every bitmap has the same
- * level structure: level l has words_per_level[l] 64-bit words, levels are
- * stored back to back (level 0 first), bitmap_words in total. The
+ * level structure: level l has words_per_level[l] 64-bit words, of which the
+ * low `fanout` bits are used (bit p of level l lives in word p / fanout, bit
+ * p % fanout), levels are stored back to back (level 0 first), bitmap_words
+ * in total. The
  * allocated[T] bitmaps are stored back to back in type order, as are the
  * active[T] bitmaps. */
 typedef struct {
@@ -119,6 +123,8 @@ typedef struct {
     uint32_t n_fields[DSR_MAX_TYPES];
     uint32_t field_bytes[DSR_MAX_TYPES][DSR_MAX_FIELDS];
     uint32_t field_offset[DSR_MAX_TYPES][DSR_MAX_FIELDS]; /* byte offset of field f's SOA array in a block */
+    uint32_t fanout;         /* bits used per bitmap word: 64, 32 or 16 */
+    uint32_t pad_;
 } dsr_layout;
 
 /* Built-in do-all methods (dsr_parallel_do). Application methods are listed

@@ -49,12 +49,13 @@ typedef dsr_u64 dsr_ref;
 #define DSR_SLOW_WAITS 64u       /* rounds a leader may wait for another initialisation */
 #define DSR_CHASE_ROUNDS 4       /* atomics on one block per search before searching again */
 
-/* One hierarchical bitmap: level l has nwords[l] 64-bit containers. */
+/* One hierarchical bitmap: level l has nwords[l] 64-bit containers, of
+ * which the low 2^shift bits are used (the fan-out: 64, 32 or 16). */
 struct dsr_hbm {
     dsr_u64* lvl[DSR_MAX_LEVELS];
     uint32_t nwords[DSR_MAX_LEVELS];
     int32_t n_levels;
-    uint32_t pad_;
+    uint32_t shift;
 };
 
 /* Device view of a heap; passed by value to kernels. */
@@ -195,9 +196,10 @@ __device__ __forceinline__ dsr_u64 dsr_lowest_bits(dsr_u64 m, int k) {
  * its own atomicOr changed the bit. If the container was empty before, this
  * thread owes the nested bit, which it sets with set() (never try_set). */
 __device__ __forceinline__ bool dsr_hb_set(const dsr_hbm& b, dsr_u64 pos, bool retry, uint32_t* err) {
+    const unsigned sh = b.shift, lo = (1u << sh) - 1;
     for (int l = 0; l < b.n_levels; ++l) {
-        dsr_u64* w = b.lvl[l] + (pos >> 6);
-        const dsr_u64 m = 1ull << (pos & 63);
+        dsr_u64* w = b.lvl[l] + (pos >> sh);
+        const dsr_u64 m = 1ull << (pos & lo);
         dsr_u64 prev;
         for (unsigned tries = 0;; ++tries) {
             prev = atomicOr(w, m);
@@ -211,7 +213,7 @@ __device__ __forceinline__ bool dsr_hb_set(const dsr_hbm& b, dsr_u64 pos, bool r
         }
         retry = true;
         if (prev != 0) break;  // container already non-empty: nothing owed above
-        pos >>= 6;
+        pos >>= sh;
     }
     return true;
 }
@@ -220,9 +222,10 @@ __device__ __forceinline__ bool dsr_hb_set(const dsr_hbm& b, dsr_u64 pos, bool r
  * otherwise. If this call cleared the last set bit of its container
  * (popc(prev) == 1) it clears the nested bit with clear(). */
 __device__ __forceinline__ bool dsr_hb_clear(const dsr_hbm& b, dsr_u64 pos, bool retry, uint32_t* err) {
+    const unsigned sh = b.shift, lo = (1u << sh) - 1;
     for (int l = 0; l < b.n_levels; ++l) {
-        dsr_u64* w = b.lvl[l] + (pos >> 6);
-        const dsr_u64 m = 1ull << (pos & 63);
+        dsr_u64* w = b.lvl[l] + (pos >> sh);
+        const dsr_u64 m = 1ull << (pos & lo);
         dsr_u64 prev;
         for (unsigned tries = 0;; ++tries) {
             prev = atomicAnd(w, ~m);
@@ -236,7 +239,7 @@ __device__ __forceinline__ bool dsr_hb_clear(const dsr_hbm& b, dsr_u64 pos, bool
         }
         retry = true;
         if (prev != m) break;  // other bits remain in the container
-        pos >>= 6;
+        pos >>= sh;
     }
     return true;
 }
@@ -267,7 +270,7 @@ __device__ __forceinline__ long long dsr_hb_find(const dsr_hbm& b, unsigned hint
         if (w == 0) return -1;
         const unsigned h = dsr_hash32(hint ^ ((unsigned)l * 0x9E3779B9u));
         const int k = dsr_nth_bit(w, (int)__umulhi(h, (unsigned)__popcll(w)));
-        pos = pos * 64 + (dsr_u64)k;
+        pos = (pos << b.shift) + (dsr_u64)k;
     }
     return (long long)pos;
 }

@@ -54,7 +54,7 @@ def lib():
         L.orc_hb_consistent.argtypes = [vp]
 
         L.orc_check_heap.restype = C.c_uint32
-        L.orc_check_heap.argtypes = [u64, i32, vp, vp, vp, vp, vp, vp, vp, i32, vp]
+        L.orc_check_heap.argtypes = [u64, i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp]
 
         L.orc_gol_create.restype = vp
         L.orc_gol_create.argtypes = [i32, i32, vp]
@@ -172,11 +172,12 @@ INV_RANGE = 16
 INV_STRUCTURE = 32
 
 
-def check_heap(M, capacity, obj_free, block_type, free_bm, alloc_bm, active_bm, words_per_level):
+def check_heap(M, capacity, obj_free, block_type, free_bm, alloc_bm, active_bm, words_per_level, width=64):
     """Check block-state invariants of a heap snapshot; returns (violations, live per type).
 
     free_bm: u64[total_words]; alloc_bm / active_bm: u64[n_types, total_words],
-    each the concatenation of a bitmap's levels (level 0 first).
+    each the concatenation of a bitmap's levels (level 0 first), every word
+    holding `width` bits (64, 32 or 16).
     """
     n_types = len(capacity)
     cap = np.ascontiguousarray(capacity, dtype=np.uint32)
@@ -188,7 +189,7 @@ def check_heap(M, capacity, obj_free, block_type, free_bm, alloc_bm, active_bm, 
     wpl = np.ascontiguousarray(words_per_level, dtype=np.uint64)
     live = np.zeros(n_types, dtype=np.uint64)
     bad = lib().orc_check_heap(M, n_types, _ptr(cap), _ptr(of), _ptr(bt), _ptr(fb), _ptr(ab), _ptr(cb),
-                               _ptr(wpl), len(wpl), _ptr(live))
+                               _ptr(wpl), len(wpl), int(width), _ptr(live))
     return int(bad), live.astype(np.int64)
 
 

@@ -72,7 +72,7 @@ uint32_t orc_check_heap(uint64_t M, int n_types, const uint32_t* capacity,
                         const uint64_t* obj_free, const uint8_t* block_type,
                         const uint64_t* free_bm, const uint64_t* alloc_bm,
                         const uint64_t* active_bm, const uint64_t* words_per_level,
-                        int n_levels, uint64_t* live_out);
+                        int n_levels, int width, uint64_t* live_out);
 
 /* ---- game of life (B3/S23 as an SMMO program) -------------------------- */
 typedef struct orc_gol orc_gol;

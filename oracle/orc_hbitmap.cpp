@@ -146,7 +146,10 @@ extern "C" int orc_hb_consistent(const orc_hb* h) {
 // for allocated[T] blocks with at least one free slot (active => allocated).
 // At a quiescent point (no operation in flight) every bitmap is consistent.
 // ---------------------------------------------------------------------------
-static inline int bit_of(const uint64_t* w, uint64_t i) { return (int)((w[i >> 6] >> (i & 63)) & 1u); }
+// Bit i of a bitmap level whose 64-bit words each hold `width` bits.
+static inline int bit_of(const uint64_t* w, uint64_t i, unsigned width) {
+    return (int)((w[i / width] >> (i % width)) & 1u);
+}
 
 static int popc64(uint64_t x) {
     int c = 0;
@@ -158,34 +161,40 @@ extern "C" uint32_t orc_check_heap(uint64_t M, int n_types, const uint32_t* capa
                                    const uint64_t* obj_free, const uint8_t* block_type,
                                    const uint64_t* free_bm, const uint64_t* alloc_bm,
                                    const uint64_t* active_bm, const uint64_t* words_per_level,
-                                   int n_levels, uint64_t* live_out) {
+                                   int n_levels, int width, uint64_t* live_out) {
     uint32_t bad = 0;
-    // Expected level structure for 64-bit containers.
+    if (width != 16 && width != 32 && width != 64) return 32;
+    const uint64_t W = (uint64_t)width;
+    // Expected level structure for containers of `width` bits: level l + 1
+    // has one bit per container of level l (Section 3).
     std::vector<uint64_t> bits_l, off_l;
     {
         uint64_t n = M, off = 0;
         bits_l.push_back(n);
-        while (n > 64) { n = (n + 63) / 64; bits_l.push_back(n); }
+        while (n > W) { n = (n + W - 1) / W; bits_l.push_back(n); }
         if ((int)bits_l.size() != n_levels) return 32;
         for (int l = 0; l < n_levels; ++l) {
-            if (words_per_level[l] != (bits_l[l] + 63) / 64) return 32;
+            if (words_per_level[l] != (bits_l[l] + W - 1) / W) return 32;
             off_l.push_back(off);
             off += words_per_level[l];
         }
     }
     uint64_t total_words = off_l.back() + words_per_level[n_levels - 1];
+    const uint64_t unused = W == 64 ? 0 : ~((1ull << W) - 1);  // word bits beyond the width
 
     auto check_bitmap = [&](const uint64_t* bm) {
         for (int l = 0; l < n_levels; ++l) {
             const uint64_t* w = bm + off_l[l];
-            // no bit at or beyond the level's size
-            for (uint64_t i = bits_l[l]; i < words_per_level[l] * 64; ++i)
-                if (bit_of(w, i)) bad |= 16;
+            // no bit at or beyond the level's size, none beyond a word's width
+            for (uint64_t i = bits_l[l]; i < words_per_level[l] * W; ++i)
+                if (bit_of(w, i, width)) bad |= 16;
+            for (uint64_t c = 0; c < words_per_level[l]; ++c)
+                if (w[c] & unused) bad |= 16;
             if (l + 1 < n_levels) {
                 const uint64_t* up = bm + off_l[l + 1];
                 for (uint64_t c = 0; c < words_per_level[l]; ++c) {
                     int any = w[c] != 0;
-                    if (any != bit_of(up, c)) bad |= 1;
+                    if (any != bit_of(up, c, width)) bad |= 1;
                 }
             }
         }
@@ -198,11 +207,11 @@ extern "C" uint32_t orc_check_heap(uint64_t M, int n_types, const uint32_t* capa
 
     for (int t = 0; t < n_types; ++t) live_out[t] = 0;
     for (uint64_t b = 0; b < M; ++b) {
-        int states = bit_of(free_bm, b);
+        int states = bit_of(free_bm, b, width);
         for (int t = 0; t < n_types; ++t) {
             const uint64_t* al = alloc_bm + (uint64_t)t * total_words;
             const uint64_t* ac = active_bm + (uint64_t)t * total_words;
-            int a = bit_of(al, b), act = bit_of(ac, b);
+            int a = bit_of(al, b, width), act = bit_of(ac, b, width);
             states += a;
             if (a) {
                 uint64_t valid = capacity[t] >= 64 ? ~0ull : ((1ull << capacity[t]) - 1);

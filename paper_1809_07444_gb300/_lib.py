@@ -30,7 +30,7 @@ class TypeDesc(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("cap_min", C.c_int), ("threads", C.c_int), ("ctas_per_sm", C.c_int)]
+    _fields_ = [("cap_min", C.c_int), ("threads", C.c_int), ("ctas_per_sm", C.c_int), ("fanout", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -48,7 +48,8 @@ class Layout(C.Structure):
                 ("arena_bytes_used", C.c_uint64), ("n_types", C.c_uint32),
                 ("capacity", C.c_uint32 * MAX_TYPES), ("n_fields", C.c_uint32 * MAX_TYPES),
                 ("field_bytes", (C.c_uint32 * MAX_FIELDS) * MAX_TYPES),
-                ("field_offset", (C.c_uint32 * MAX_FIELDS) * MAX_TYPES)]
+                ("field_offset", (C.c_uint32 * MAX_FIELDS) * MAX_TYPES), ("fanout", C.c_uint32),
+                ("pad_", C.c_uint32)]
 
 
 class WatorParams(C.Structure):

@@ -19,8 +19,11 @@ def _sorted_rows(a):
     return a[idx]
 
 
-def _blocks_for(cells, caps, slack=2.0):
-    return int(slack * sum(math.ceil(cells / c) for c in caps)) + 256
+def _blocks_for(cells, caps, slack=2.0, tuning=None):
+    """Blocks for `cells` objects of each type with the given capacities at
+    cap_min 64 (scaled down with a smaller cap_min), with slack."""
+    scale = int((tuning or {}).get("cap_min") or 64) / 64.0
+    return int(slack * sum(math.ceil(cells / max(1, int(c * scale))) for c in caps)) + 256
 
 
 class Gol:
@@ -30,7 +33,7 @@ class Gol:
         self.lib = L.load()
         self.W, self.H = W, H
         if heap_bytes is None:
-            heap_bytes = heap_bytes_for_blocks(GOL_TYPES, _blocks_for(W * H, [42, 64]), tuning)
+            heap_bytes = heap_bytes_for_blocks(GOL_TYPES, _blocks_for(W * H, [42, 64], tuning=tuning), tuning)
         self.heap = Heap(GOL_TYPES, heap_bytes, names=["Cell", "Alive"], tuning=tuning, stream=stream)
         ws = C.c_size_t(0)
         L.check(self.lib.dsr_gol_workspace_bytes(W, H, C.byref(ws)), "dsr_gol_workspace_bytes")
@@ -74,7 +77,7 @@ class Wator:
         self.lib = L.load()
         self.W, self.H = W, H
         if heap_bytes is None:
-            heap_bytes = heap_bytes_for_blocks(WATOR_TYPES, _blocks_for(W * H, [48]), tuning)
+            heap_bytes = heap_bytes_for_blocks(WATOR_TYPES, _blocks_for(W * H, [48], tuning=tuning), tuning)
         self.heap = Heap(WATOR_TYPES, heap_bytes, names=["Fish", "Shark"], tuning=tuning, stream=stream)
         ws = C.c_size_t(0)
         L.check(self.lib.dsr_wator_workspace_bytes(W, H, C.byref(ws)), "dsr_wator_workspace_bytes")
@@ -149,6 +152,7 @@ class WatorBatch:
         from .heap import _tuning
         self.lib = L.load()
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+        self.tuning = tuning
         tun = _tuning(tuning)
         h = C.c_void_p()
         L.check(self.lib.dsr_wator_batch_create(C.c_void_p(self.arena.data_ptr()), int(arena_bytes), max_instances,
@@ -164,12 +168,12 @@ class WatorBatch:
             self.handle = None
 
     @staticmethod
-    def blocks_for(W, H):
-        return _blocks_for(W * H, [48])
+    def blocks_for(W, H, tuning=None):
+        return _blocks_for(W * H, [48], tuning=tuning)
 
     def instance_bytes(self, W, H, n_blocks=None):
         out = C.c_size_t(0)
-        L.check(self.lib.dsr_wator_batch_instance_bytes(self.handle, W, H, n_blocks or self.blocks_for(W, H),
+        L.check(self.lib.dsr_wator_batch_instance_bytes(self.handle, W, H, n_blocks or self.blocks_for(W, H, self.tuning),
                                                         C.byref(out)), "dsr_wator_batch_instance_bytes")
         return int(out.value)
 
@@ -179,7 +183,7 @@ class WatorBatch:
         k0 = torch.as_tensor(np.ascontiguousarray(kind0, dtype=np.uint8).reshape(-1)).cuda()
         p = L.WatorParams(W, H, seed, fish_breed, shark_breed, shark_energy0, shark_gain)
         slot = C.c_int(-1)
-        rc = self.lib.dsr_wator_batch_add(self.handle, C.byref(p), n_blocks or self.blocks_for(W, H),
+        rc = self.lib.dsr_wator_batch_add(self.handle, C.byref(p), n_blocks or self.blocks_for(W, H, self.tuning),
                                           C.c_void_p(k0.data_ptr()), _stream_ptr(stream), C.byref(slot))
         if rc == L.E_OOM:
             return None
@@ -237,6 +241,7 @@ class GolBatch:
         from .heap import _tuning
         self.lib = L.load()
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+        self.tuning = tuning
         tun = _tuning(tuning)
         h = C.c_void_p()
         L.check(self.lib.dsr_gol_batch_create(C.c_void_p(self.arena.data_ptr()), int(arena_bytes), max_instances,
@@ -251,12 +256,12 @@ class GolBatch:
             self.handle = None
 
     @staticmethod
-    def blocks_for(W, H):
-        return _blocks_for(W * H, [42, 64])
+    def blocks_for(W, H, tuning=None):
+        return _blocks_for(W * H, [42, 64], tuning=tuning)
 
     def instance_bytes(self, W, H, n_blocks=None):
         out = C.c_size_t(0)
-        L.check(self.lib.dsr_gol_batch_instance_bytes(self.handle, W, H, n_blocks or self.blocks_for(W, H),
+        L.check(self.lib.dsr_gol_batch_instance_bytes(self.handle, W, H, n_blocks or self.blocks_for(W, H, self.tuning),
                                                       C.byref(out)), "dsr_gol_batch_instance_bytes")
         return int(out.value)
 
@@ -264,7 +269,7 @@ class GolBatch:
         """Add an instance; returns its slot, or None when the arena has no room."""
         a0 = torch.as_tensor(np.ascontiguousarray(alive0, dtype=np.uint8).reshape(-1)).cuda()
         slot = C.c_int(-1)
-        rc = self.lib.dsr_gol_batch_add(self.handle, W, H, n_blocks or self.blocks_for(W, H),
+        rc = self.lib.dsr_gol_batch_add(self.handle, W, H, n_blocks or self.blocks_for(W, H, self.tuning),
                                         C.c_void_p(a0.data_ptr()), _stream_ptr(stream), C.byref(slot))
         if rc == L.E_OOM:
             return None

@@ -19,7 +19,8 @@ __global__ void __launch_bounds__(256) k_group_scan(const __grid_constant__ dsr_
         const bool hok = dsr_check(h < G.n_slots, G.err, G.dbg, 1, c);
         const dsr_dev_heap& H = G.heaps[hok ? h : 0];
         const dsr_u64 b = (dsr_u64)G.chunk_base[c] + threadIdx.x;
-        const bool set = hok && b < H.M && ((H.alloc_bm[T].lvl[0][b >> 6] >> (b & 63)) & 1ull);
+        const unsigned fsh = H.alloc_bm[T].shift;
+        const bool set = hok && b < H.M && ((H.alloc_bm[T].lvl[0][b >> fsh] >> (b & ((1u << fsh) - 1))) & 1ull);
         const unsigned ballot = __ballot_sync(0xFFFFFFFFu, set);
         if (lane == 0) warp_n[warp] = __popc(ballot);
         __syncthreads();
@@ -166,7 +167,7 @@ extern "C" int dsr_group_create(const dsr_type_desc* types, int n_types, void* a
         g->types[t].field_bytes = nullptr;  // re-pointed below, after the vectors are in place
     }
     for (int t = 0; t < n_types; ++t) g->types[t].field_bytes = g->fields[t].data();
-    g->tune = tune ? *tune : dsr_tuning{0, 0, 0};
+    g->tune = tune ? *tune : dsr_tuning{0, 0, 0, 0};
     g->heaps.assign(max_heaps, nullptr);
     g->offsets.assign(max_heaps, 0);
     g->sizes.assign(max_heaps, 0);

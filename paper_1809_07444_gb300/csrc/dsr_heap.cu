@@ -54,7 +54,9 @@ static uint64_t type_bytes(const dsr_layout& L, int t, uint32_t cap) {
 static int geometry(const dsr_type_desc* types, int n_types, const dsr_tuning& tune, dsr_layout* L) {
     if (!types || n_types < 1 || n_types > DSR_MAX_TYPES) return DSR_E_INVALID;
     if (tune.cap_min != 32 && tune.cap_min != 64) return DSR_E_INVALID;
+    if (tune.fanout != 16 && tune.fanout != 32 && tune.fanout != 64) return DSR_E_INVALID;
     memset(L, 0, sizeof *L);
+    L->fanout = (uint32_t)tune.fanout;
     L->n_types = (uint32_t)n_types;
     uint64_t smin = ~0ull;
     int tmin = 0;
@@ -91,18 +93,21 @@ static int geometry(const dsr_type_desc* types, int n_types, const dsr_tuning& t
     return DSR_OK;
 }
 
-// Offsets of every metadata array for M blocks; returns the arena bytes used.
+// Offsets of every metadata array for M blocks; returns the arena bytes used,
+// or UINT64_MAX if the bitmaps would need more than DSR_MAX_LEVELS levels.
 static uint64_t place(dsr_layout* L, uint64_t M) {
     L->n_blocks = M;
+    const uint64_t f = L->fanout;
     uint64_t n = M;
     int lv = 0;
     uint64_t words = 0;
     for (;;) {
-        L->words_per_level[lv] = (n + 63) / 64;
+        if (lv == DSR_MAX_LEVELS) return ~0ull;
+        L->words_per_level[lv] = (n + f - 1) / f;
         words += L->words_per_level[lv];
         ++lv;
-        if (n <= 64) break;
-        n = (n + 63) / 64;
+        if (n <= f) break;
+        n = (n + f - 1) / f;
     }
     L->n_levels = (uint32_t)lv;
     L->bitmap_words = words;
@@ -139,11 +144,12 @@ static uint64_t off_rmask(const dsr_layout& L) { return round_up(L.off_obj + L.n
 static uint64_t off_rbid(const dsr_layout& L) { return round_up(off_rmask(L) + L.n_blocks * 8, 256); }
 
 static dsr_tuning resolve_tuning(const dsr_tuning* t) {
-    dsr_tuning r{64, 256, 0};
+    dsr_tuning r{64, 256, 0, 64};
     if (t) {
         if (t->cap_min) r.cap_min = t->cap_min;
         if (t->threads) r.threads = t->threads;
         r.ctas_per_sm = t->ctas_per_sm;
+        if (t->fanout) r.fanout = t->fanout;
     }
     return r;
 }
@@ -154,7 +160,9 @@ extern "C" int dsr_heap_bytes_for_blocks(const dsr_type_desc* types, int n_types
     dsr_layout L;
     int rc = geometry(types, n_types, resolve_tuning(tune), &L);
     if (rc) return rc;
-    *out_bytes = (size_t)place(&L, n_blocks);
+    const uint64_t bytes = place(&L, n_blocks);
+    if (bytes == ~0ull) return DSR_E_INVALID;
+    *out_bytes = (size_t)bytes;
     return DSR_OK;
 }
 
@@ -164,7 +172,7 @@ extern "C" int dsr_heap_plan(const dsr_type_desc* types, int n_types, uint64_t n
     dsr_layout L;
     int rc = geometry(types, n_types, resolve_tuning(tune), &L);
     if (rc) return rc;
-    place(&L, n_blocks);
+    if (place(&L, n_blocks) == ~0ull) return DSR_E_INVALID;
     *out = L;
     return DSR_OK;
 }
@@ -178,15 +186,16 @@ extern "C" int dsr_heap_plan(const dsr_type_desc* types, int n_types, uint64_t n
 __global__ void k_heap_mark_free(const __grid_constant__ dsr_dev_heap H, dsr_u64 M) {
     const dsr_u64 tid = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x;
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
+    const dsr_u64 f = 1ull << H.free_bm.shift;
     dsr_u64 n = M;
     for (int l = 0; l < H.free_bm.n_levels; ++l) {
         const dsr_u64 nw = H.free_bm.nwords[l];
         for (dsr_u64 i = tid; i < nw; i += stride) {
-            const dsr_u64 lo = i * 64;
-            const dsr_u64 k = n - lo >= 64 ? 64 : n - lo;
+            const dsr_u64 lo = i * f;
+            const dsr_u64 k = n - lo >= f ? f : n - lo;
             H.free_bm.lvl[l][i] = k >= 64 ? ~0ull : ((1ull << k) - 1);
         }
-        n = (n + 63) / 64;
+        n = (n + f - 1) / f;
     }
     for (dsr_u64 b = tid; b < M; b += stride) H.btype[b] = 0xFF;
 }
@@ -203,13 +212,14 @@ __global__ void __launch_bounds__(256) k_scan(const __grid_constant__ dsr_dev_he
     __shared__ unsigned warp_n[8];
     __shared__ unsigned run_base;
     const dsr_u64* leaf = H.alloc_bm[T].lvl[0];
+    const unsigned fsh = H.alloc_bm[T].shift, flo = (1u << fsh) - 1;
     const dsr_u64 v = H.valid[T];
     const dsr_u64 M = H.M;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned objs = 0;
     for (dsr_u64 base = (dsr_u64)blockIdx.x * 256; base < M; base += (dsr_u64)gridDim.x * 256) {
         const dsr_u64 b = base + threadIdx.x;
-        const bool set = b < M && ((leaf[b >> 6] >> (b & 63)) & 1ull);
+        const bool set = b < M && ((leaf[b >> fsh] >> (b & flo)) & 1ull);
         const unsigned ballot = __ballot_sync(0xFFFFFFFFu, set);
         if (lane == 0) warp_n[warp] = __popc(ballot);
         __syncthreads();
@@ -315,6 +325,7 @@ static void build_dev_view(dsr_heap* h) {
     D.n_types = (int32_t)L.n_types;
     auto fill = [&](dsr_hbm& b, uint64_t off) {
         b.n_levels = (int32_t)L.n_levels;
+        b.shift = L.fanout == 16 ? 4u : L.fanout == 32 ? 5u : 6u;
         uint64_t o = off;
         for (uint32_t l = 0; l < L.n_levels; ++l) {
             b.lvl[l] = reinterpret_cast<dsr_u64*>(a + o);

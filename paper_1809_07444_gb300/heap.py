@@ -29,7 +29,8 @@ def _descs(types, names=None):
 def _tuning(t):
     if t is None:
         return None
-    return L.Tuning(int(t.get("cap_min", 0)), int(t.get("threads", 0)), int(t.get("ctas_per_sm", 0)))
+    return L.Tuning(int(t.get("cap_min", 0)), int(t.get("threads", 0)), int(t.get("ctas_per_sm", 0)),
+                    int(t.get("fanout", 0)))
 
 
 def heap_bytes_for_blocks(types, n_blocks, tuning=None):
@@ -141,6 +142,7 @@ class Heap:
             "alloc_bm": u64(lay.off_alloc_bm, T * W).reshape(T, W),
             "active_bm": u64(lay.off_active_bm, T * W).reshape(T, W),
             "words_per_level": np.array([lay.words_per_level[l] for l in range(lay.n_levels)], dtype=np.uint64),
+            "width": int(lay.fanout),
         }
 
     # -- do-all -------------------------------------------------------------

@@ -42,13 +42,13 @@ def test_binding_covers_declarations():
     assert set(_lib.SIGNATURES) <= _declared()
 
 
-def _plan(lib, types, n_blocks, cap_min=0):
+def _plan(lib, types, n_blocks, cap_min=0, fanout=0):
     from paper_1809_07444_gb300 import _lib as L
     from paper_1809_07444_gb300.heap import _descs
 
     descs, _keep = _descs(types)
     lay = L.Layout()
-    tun = L.Tuning(cap_min, 0, 0)
+    tun = L.Tuning(cap_min, 0, 0, fanout)
     rc = lib.dsr_heap_plan(descs, len(types), n_blocks, C.byref(tun), C.byref(lay))
     return rc, lay
 
@@ -107,3 +107,21 @@ def test_product_path_fails_loudly_without_library(tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
         finally:
             _lib._lib = None
+
+
+@pytest.mark.parametrize("fanout,words", [(0, [79, 2, 1]), (64, [79, 2, 1]), (32, [157, 5, 1]),
+                                          (16, [313, 20, 2, 1])])
+def test_bitmap_fanout_sets_the_level_structure(lib, fanout, words):
+    rc, lay = _plan(lib, [[4, 4]], 5000, fanout=fanout)
+    assert rc == 0
+    assert lay.fanout == (fanout or 64)
+    assert [lay.words_per_level[l] for l in range(lay.n_levels)] == words
+    assert lay.bitmap_words == sum(words)
+
+
+def test_bitmap_fanout_rejects_bad_widths_and_too_many_levels(lib):
+    from paper_1809_07444_gb300 import _lib as L
+    assert _plan(lib, [[4, 4]], 5000, fanout=8)[0] == L.E_INVALID
+    # 16-bit containers reach DSR_MAX_LEVELS (6) levels at 16^6 blocks
+    assert _plan(lib, [[4, 4]], 16 ** 6, fanout=16)[0] == 0
+    assert _plan(lib, [[4, 4]], 16 ** 6 + 1, fanout=16)[0] == L.E_INVALID

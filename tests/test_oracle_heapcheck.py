@@ -5,28 +5,31 @@ import pytest
 import oracle as O
 
 
-def _levels(M):
+def _levels(M, width=64):
     bits = [M]
-    while bits[-1] > 64:
-        bits.append(-(-bits[-1] // 64))
-    return bits, [-(-b // 64) for b in bits]
+    while bits[-1] > width:
+        bits.append(-(-bits[-1] // width))
+    return bits, [-(-b // width) for b in bits]
 
 
-def _bitmap(flags, M):
-    """Hierarchical bitmap words (levels concatenated) for per-position flags."""
-    bits, words = _levels(M)
+def _bitmap(flags, M, width=64):
+    """Hierarchical bitmap words (levels concatenated) for per-position flags:
+    position p of a level is bit p % width of word p // width."""
+    bits, words = _levels(M, width)
     out = []
     cur = np.asarray(flags, dtype=bool)
     for l, w in enumerate(words):
-        padded = np.zeros(w * 64, dtype=bool)
+        padded = np.zeros(w * width, dtype=bool)
         padded[:len(cur)] = cur
-        ws = np.packbits(padded.reshape(w, 64)[:, ::-1], axis=1).view(">u8").reshape(w).astype(np.uint64)
+        full = np.zeros((w, 64), dtype=bool)
+        full[:, :width] = padded.reshape(w, width)
+        ws = np.packbits(full[:, ::-1], axis=1).view(">u8").reshape(w).astype(np.uint64)
         out.append(ws)
-        cur = padded.reshape(w, 64).any(axis=1)
+        cur = padded.reshape(w, width).any(axis=1)
     return np.concatenate(out), np.array(words, dtype=np.uint64)
 
 
-def _heap(seed=0, M=300, caps=(64, 40)):
+def _heap(seed=0, M=300, caps=(64, 40), width=64):
     rng = np.random.default_rng(seed)
     T = len(caps)
     state = rng.integers(-1, T, M)  # -1 free
@@ -48,19 +51,41 @@ def _heap(seed=0, M=300, caps=(64, 40)):
                 fr |= 1 << s
         obj_free[b] = np.uint64(fr)
         btype[b] = t
-    free_bm, wpl = _bitmap(state < 0, M)
-    alloc = np.stack([_bitmap(state == t, M)[0] for t in range(T)])
-    active = np.stack([_bitmap((state == t) & (obj_free != 0), M)[0] for t in range(T)])
+    free_bm, wpl = _bitmap(state < 0, M, width)
+    alloc = np.stack([_bitmap(state == t, M, width)[0] for t in range(T)])
+    active = np.stack([_bitmap((state == t) & (obj_free != 0), M, width)[0] for t in range(T)])
     return dict(M=M, capacity=np.array(caps), obj_free=obj_free, block_type=btype, free_bm=free_bm,
-                alloc_bm=alloc, active_bm=active, words_per_level=wpl), live
+                alloc_bm=alloc, active_bm=active, words_per_level=wpl, width=width), live
 
 
 @pytest.mark.parametrize("seed,M", [(0, 300), (1, 64), (2, 5000), (3, 64 * 64 + 7)])
-def test_consistent_heap_passes(seed, M):
-    h, live = _heap(seed, M)
+@pytest.mark.parametrize("width", [64, 32, 16])
+def test_consistent_heap_passes(seed, M, width):
+    h, live = _heap(seed, M, width=width)
     bad, got = O.check_heap(**h)
     assert bad == 0
     assert np.array_equal(got, live)
+
+
+def test_level_counts_follow_the_width():
+    # 5000 blocks: 64-bit containers give 79 + 2 + 1 words, 16-bit ones
+    # 313 + 20 + 2 + 1
+    assert _levels(5000, 64)[1] == [79, 2, 1]
+    assert _levels(5000, 16)[1] == [313, 20, 2, 1]
+    h, _ = _heap(2, 5000, width=16)
+    assert O.check_heap(**dict(h, width=64))[0] & O.INV_STRUCTURE  # read with the wrong width
+
+
+@pytest.mark.parametrize("width", [32, 16])
+def test_narrow_width_flags_bits_beyond_the_width_and_nesting(width):
+    h, _ = _heap(7, 3000, width=width)
+    g = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in h.items()}
+    g["free_bm"][0] |= np.uint64(1) << np.uint64(width)  # a bit past the container width
+    assert O.check_heap(**g)[0] & O.INV_RANGE
+    g = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in h.items()}
+    n0 = int(g["words_per_level"][0])
+    g["alloc_bm"][1][n0] ^= np.uint64(1 << 2)  # level-1 bit out of step with its container
+    assert O.check_heap(**g)[0] & O.INV_CONTAINER
 
 
 def test_flags_each_planted_violation():
