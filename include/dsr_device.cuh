@@ -604,6 +604,40 @@ __global__ void dsr_doall_kernel(const __grid_constant__ dsr_dev_heap H, int T,
     if (dsr_doall_finish(H)) dsr_call_finish<Method>(H, T, args, 0);
 }
 
+/* Vector method kernel: a method may also provide
+ *   static __device__ void run4(const dsr_dev_heap&, int T, const Args&,
+ *                               uint32_t block, unsigned slot0, unsigned live4);
+ * which handles the four slots slot0 .. slot0 + 3 of one block at once
+ * (live4: which of them were occupied in the snapshot; never 0), so that
+ * each thread moves 16 bytes of a field column per access. The do-all uses
+ * it when every field array of T starts on a 16-byte boundary (capacity a
+ * multiple of 4 for 4-byte fields); otherwise it runs `run`. A quad of
+ * threads per 16 slots: a warp covers two 64-slot blocks (or four of 32). */
+template <class M, class = void>
+struct dsr_has_run4 {
+    static constexpr bool value = false;
+};
+template <class M>
+struct dsr_has_run4<M, decltype(M::run4(*(const dsr_dev_heap*)nullptr, 0, *(const typename M::Args*)nullptr, 0u, 0u,
+                                        0u), void())> {
+    static constexpr bool value = true;
+};
+
+template <class Method>
+__global__ void dsr_doall_kernel_vec4(const __grid_constant__ dsr_dev_heap H, int T,
+                                      const __grid_constant__ typename Method::Args args) {
+    const unsigned sh = dsr_span_shift(H, T) - 2;  // quads per listed block: 16 (or 8)
+    const dsr_u64 total = (dsr_u64)(*(volatile uint32_t*)H.R_count) << sh;
+    const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
+    for (dsr_u64 g = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        const dsr_u64 i = g >> sh;
+        const unsigned q = (unsigned)(g & ((1u << sh) - 1));
+        const unsigned live = (unsigned)(H.R_mask[i] >> (4 * q)) & 0xFu;
+        if (live && dsr_check(H.R_bid[i] < H.M, H.err, H.dbg, 10, i)) Method::run4(H, T, args, H.R_bid[i], 4 * q, live);
+    }
+    if (dsr_doall_finish(H)) dsr_call_finish<Method>(H, T, args, 0);
+}
+
 /* ------------------------------------------------------------------------ */
 /* heap groups: one do-all over many heaps                                  */
 /* ------------------------------------------------------------------------ */

@@ -274,6 +274,14 @@ __global__ void k_stats(const __grid_constant__ dsr_dev_heap H, dsr_u64* out) {
     }
 }
 
+bool dsr__vec4_ok(const dsr_heap* h, int type) {
+    const dsr_layout& L = h->layout;
+    if (L.capacity[type] % 4 || L.block_bytes % 16) return false;
+    for (uint32_t f = 0; f < L.n_fields[type]; ++f)
+        if (L.field_offset[type][f] % 16 || L.field_bytes[type][f] != 4) return false;
+    return true;
+}
+
 int dsr__scan_grid(const dsr_heap* h, int type) {
     (void)type;
     uint64_t ctas = (h->dev.M + 255) / 256;
@@ -523,6 +531,7 @@ struct MCount {
     }
 };
 
+// field f += field f + 1 for every field but the last, which gets + 1.
 struct MStreamAdd {
     struct Args { int dummy; };
     static __device__ void run(const dsr_dev_heap& H, int T, const Args&, dsr_ref r) {
@@ -532,6 +541,48 @@ struct MStreamAdd {
             *p += *dsr_field<int32_t>(H, T, r, f + 1);
         }
         *dsr_field<int32_t>(H, T, r, nf - 1) += 1;
+    }
+    // Four slots at once: all NF field vectors are loaded before any store,
+    // so a thread has NF 16-byte loads in flight.
+    template <int NF>
+    static __device__ __forceinline__ void quad(const dsr_dev_heap& H, int T, uint32_t bid, unsigned s0, unsigned live) {
+        uint8_t* base = H.data + (dsr_u64)bid * H.block_bytes + 4 * s0;
+        int4 v[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) v[f] = *reinterpret_cast<const int4*>(base + H.foff[T][f]);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            int4 o = v[f];
+            if (f + 1 < NF) {
+                o.x += v[f + 1].x, o.y += v[f + 1].y, o.z += v[f + 1].z, o.w += v[f + 1].w;
+            } else {
+                o.x += 1, o.y += 1, o.z += 1, o.w += 1;
+            }
+            int32_t* p = reinterpret_cast<int32_t*>(base + H.foff[T][f]);
+            if (live == 0xFu) {
+                *reinterpret_cast<int4*>(p) = o;
+            } else {
+                if (live & 1u) p[0] = o.x;
+                if (live & 2u) p[1] = o.y;
+                if (live & 4u) p[2] = o.z;
+                if (live & 8u) p[3] = o.w;
+            }
+        }
+    }
+    static __device__ void run4(const dsr_dev_heap& H, int T, const Args&, uint32_t bid, unsigned s0, unsigned live) {
+        switch (H.n_fields[T]) {
+            case 1: quad<1>(H, T, bid, s0, live); break;
+            case 2: quad<2>(H, T, bid, s0, live); break;
+            case 3: quad<3>(H, T, bid, s0, live); break;
+            case 4: quad<4>(H, T, bid, s0, live); break;
+            case 5: quad<5>(H, T, bid, s0, live); break;
+            case 6: quad<6>(H, T, bid, s0, live); break;
+            case 7: quad<7>(H, T, bid, s0, live); break;
+            case 8: quad<8>(H, T, bid, s0, live); break;
+            default:  // wider types: one slot at a time
+                for (unsigned k = 0; k < 4; ++k)
+                    if (live & (1u << k)) run(H, T, Args{0}, ((dsr_u64)bid << 6) | (s0 + k));
+        }
     }
 };
 

@@ -40,6 +40,9 @@ inline cudaStream_t dsr__stream(void* s) { return reinterpret_cast<cudaStream_t>
 // capped by the most work a do-all over this heap can list.
 int dsr__persistent_grid(const dsr_heap* h, const void* kernel, int threads);
 int dsr__scan_grid(const dsr_heap* h, int type);
+// True if every field array of `type` starts on a 16-byte boundary within a
+// block and the capacity is a multiple of 4 (vector methods may run).
+bool dsr__vec4_ok(const dsr_heap* h, int type);
 void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s);
 
 // Run a do-all: scan + compaction of allocated[type] into R, then the method
@@ -66,8 +69,21 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
     int g = (int)g64;
     if ((dsr_u64)g > cap_grid) g = (int)cap_grid;
     if (g < 1) g = 1;
+    int rc;
+    if constexpr (dsr_has_run4<M>::value) {
+        if (dsr__vec4_ok(h, type)) {
+            static int vgrid = 0;
+            if (vgrid == 0 || h->tune.ctas_per_sm > 0)
+                vgrid = dsr__persistent_grid(h, (const void*)dsr_doall_kernel_vec4<M>, threads);
+            int gv = vgrid < g ? vgrid : g;
+            dsr_doall_kernel_vec4<M><<<gv, threads, 0, s>>>(h->dev, type, args);
+            rc = dsr__check_launch("dsr_doall_kernel_vec4");
+            if (ev_run) cudaEventRecord(ev_run, s);
+            return rc;
+        }
+    }
     dsr_doall_kernel<M><<<g, threads, 0, s>>>(h->dev, type, args);
-    const int rc = dsr__check_launch("dsr_doall_kernel");
+    rc = dsr__check_launch("dsr_doall_kernel");
     if (ev_run) cudaEventRecord(ev_run, s);
     return rc;
 }

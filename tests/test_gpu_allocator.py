@@ -171,21 +171,37 @@ def test_churn_mixed_delete_and_new_in_one_kernel():
     assert h.stats()["error_flags"] == 0
 
 
-def test_stream_add_method_updates_every_field():
-    h = _heap(2000, types=[[4, 4, 4, 4]])
+@pytest.mark.parametrize("types,t,holes", [
+    ([[4, 4, 4, 4]], 0, False),          # 128-bit vector path, full quads
+    ([[4, 4, 4, 4]], 0, True),           # vector path, partly live quads
+    ([[4], [4] * 8], 1, True),           # vector path, 8 fields, capacity 8
+    ([[4, 4], [4, 4, 4]], 1, True),      # capacity 42: scalar path
+    ([[4, 4]], 0, True),                 # 2 fields
+])
+def test_stream_add_method_updates_every_field(types, t, holes):
+    h = _heap(6000, types=types)
     refs = torch.empty(40_000, dtype=torch.int64, device="cuda")
-    h.bench_alloc(refs, 1, 2)
-    f_before, hd = h.dump(0)
+    h.bench_alloc(refs, len(types), 2)
+    if holes:
+        h.parallel_do(t, L.METHOD_DELETE_IF, L.DeleteIfArgs(3, 1))
+    _check_stream_add(h, t)
+
+
+def _check_stream_add(h, t):
+    f_before, hd = h.dump(t)
     order = np.argsort(hd)
     f_before = f_before[order].view(np.int32)
-    h.parallel_do(0, L.METHOD_STREAM_ADD, None)
-    f_after, hd2 = h.dump(0)
+    h.parallel_do(t, L.METHOD_STREAM_ADD, None)
+    f_after, hd2 = h.dump(t)
     f_after = f_after[np.argsort(hd2)].view(np.int32)
+    assert np.array_equal(np.sort(hd), np.sort(hd2))  # same objects, nothing moved
+    k = f_before.shape[1]
     want = f_before.copy()  # int32 arithmetic wraps like the kernel's
-    for f in range(3):
+    for f in range(k - 1):
         want[:, f] = f_before[:, f] + f_before[:, f + 1]
-    want[:, 3] = f_before[:, 3] + 1
+    want[:, k - 1] = f_before[:, k - 1] + 1
     assert np.array_equal(f_after, want)
+    assert h.stats()["error_flags"] == 0
 
 
 def test_three_level_bitmaps_stay_consistent():
