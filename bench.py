@@ -156,6 +156,9 @@ class Clocks:
 # the GPU arm
 # ---------------------------------------------------------------------------
 PHASES = ("F1", "F2", "S0", "S1", "S2")
+# kernels of one wa-tor step: a scan and a method kernel for F1, S0 and S1; a
+# method kernel alone for F2 and S2 (they run over the lists of F1 and S1)
+LAUNCHES_PER_STEP = 8
 KERNELS = {"F1": "dsr_doall_kernel<MFishChoose>", "F2": "dsr_doall_kernel<MFishMove>",
            "S0": "dsr_doall_kernel<MSharkStarve>", "S1": "dsr_doall_kernel<MSharkChoose>",
            "S2": "dsr_doall_kernel<MSharkMove>"}
@@ -591,8 +594,8 @@ def bench_batched(n_inst=256, steps=20, one_by_one_steps=3):
             "cells": int(sum(s * s for s in sides)), "steps": steps, "ms_per_step": t_b * 1e3 / steps,
             "object_updates_per_s": vb, "one_by_one": {"object_updates_per_s": vp, "steps": one_by_one_steps,
                                                        "ms_per_step": t_p * 1e3 / one_by_one_steps,
-                                                       "launches_per_step": 10 * n_inst},
-            "speedup_vs_one_by_one": vb / vp if vp else None, "launches_per_step": 10, "graph": True,
+                                                       "launches_per_step": LAUNCHES_PER_STEP * n_inst},
+            "speedup_vs_one_by_one": vb / vp if vp else None, "launches_per_step": LAUNCHES_PER_STEP, "graph": True,
             "tuning": tun, "tuning_s": tune_s,
             "tuning_table": {",".join(str(x) for x in k): v for k, v in (table or {}).items()},
             "tuning_sample": "every fourth instance (%d), 5 timed steps per setting" % len(sub)}
@@ -685,7 +688,7 @@ def main():
         "phases": r["phases"], "clocks": r["clocks"],
         "e2e": {"value": e2e_visits / e2e_s, "unit": UNIT, "h2d_bytes_per_step": r["h2d"] / args.steps,
                 "d2h_bytes_per_step": r["d2h"] / args.steps},
-        "gpu_launches": 10 * args.steps,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "roofline": roofline(r["phases"], peak, peak_kind),
     }
     if not args.no_cpu_baseline:

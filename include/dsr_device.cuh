@@ -191,12 +191,24 @@ __device__ __forceinline__ dsr_u64 dsr_lowest_bits(dsr_u64 m, int k) {
 /* hierarchical bitmap operations (Section 2.1, Alg. 2)                     */
 /* ------------------------------------------------------------------------ */
 
+/* The bitmap operations are written once over a compile-time container
+ * shift SH (6: 64-bit fan-out); SH == 0 reads the shift from the bitmap at
+ * run time. The public entry points take the constant-shift path for the
+ * default fan-out, where 64-bit shifts by constants are single
+ * instructions, and the run-time path for 32 and 16. */
+template <unsigned SH>
+__device__ __forceinline__ unsigned dsr_hb_shift(const dsr_hbm& b) {
+    return SH ? SH : b.shift;
+}
+
 /* Set bit pos of level l. With retry == false this is try_set: it fails if
  * the bit is already set. With retry == true it is set(pos): it retries until
  * its own atomicOr changed the bit. If the container was empty before, this
  * thread owes the nested bit, which it sets with set() (never try_set). */
-__device__ __forceinline__ bool dsr_hb_set(const dsr_hbm& b, dsr_u64 pos, bool retry, uint32_t* err) {
-    const unsigned sh = b.shift, lo = (1u << sh) - 1;
+template <unsigned SH>
+__device__ __forceinline__ bool dsr_hb_set_t(const dsr_hbm& b, dsr_u64 pos, bool retry, uint32_t* err) {
+    const unsigned sh = dsr_hb_shift<SH>(b);
+    const dsr_u64 lo = (1ull << sh) - 1;
     for (int l = 0; l < b.n_levels; ++l) {
         dsr_u64* w = b.lvl[l] + (pos >> sh);
         const dsr_u64 m = 1ull << (pos & lo);
@@ -221,8 +233,10 @@ __device__ __forceinline__ bool dsr_hb_set(const dsr_hbm& b, dsr_u64 pos, bool r
 /* Clear bit pos of level l (Alg. 2). try_clear when retry == false, clear(pos)
  * otherwise. If this call cleared the last set bit of its container
  * (popc(prev) == 1) it clears the nested bit with clear(). */
-__device__ __forceinline__ bool dsr_hb_clear(const dsr_hbm& b, dsr_u64 pos, bool retry, uint32_t* err) {
-    const unsigned sh = b.shift, lo = (1u << sh) - 1;
+template <unsigned SH>
+__device__ __forceinline__ bool dsr_hb_clear_t(const dsr_hbm& b, dsr_u64 pos, bool retry, uint32_t* err) {
+    const unsigned sh = dsr_hb_shift<SH>(b);
+    const dsr_u64 lo = (1ull << sh) - 1;
     for (int l = 0; l < b.n_levels; ++l) {
         dsr_u64* w = b.lvl[l] + (pos >> sh);
         const dsr_u64 m = 1ull << (pos & lo);
@@ -244,6 +258,13 @@ __device__ __forceinline__ bool dsr_hb_clear(const dsr_hbm& b, dsr_u64 pos, bool
     return true;
 }
 
+__device__ __forceinline__ bool dsr_hb_set(const dsr_hbm& b, dsr_u64 pos, bool retry, uint32_t* err) {
+    return b.shift == 6 ? dsr_hb_set_t<6>(b, pos, retry, err) : dsr_hb_set_t<0>(b, pos, retry, err);
+}
+__device__ __forceinline__ bool dsr_hb_clear(const dsr_hbm& b, dsr_u64 pos, bool retry, uint32_t* err) {
+    return b.shift == 6 ? dsr_hb_clear_t<6>(b, pos, retry, err) : dsr_hb_clear_t<0>(b, pos, retry, err);
+}
+
 /* 32-bit integer hash (the "lowbias32" finalizer published by C. Wellons,
  * 2018): spreads consecutive or similar hints over all 32 bits. */
 __device__ __forceinline__ unsigned dsr_hash32(unsigned x) {
@@ -263,16 +284,21 @@ __device__ __forceinline__ unsigned dsr_hash32(unsigned x) {
  * runs of zeros, and the first bit of a container whose high bits are zero).
  * Returns -1 (FAIL) if a container on the way is empty, which can happen
  * while the bitmap is temporarily inconsistent. */
-__device__ __forceinline__ long long dsr_hb_find(const dsr_hbm& b, unsigned hint) {
+template <unsigned SH>
+__device__ __forceinline__ long long dsr_hb_find_t(const dsr_hbm& b, unsigned hint) {
+    const unsigned sh = dsr_hb_shift<SH>(b);
     dsr_u64 pos = 0;
     for (int l = b.n_levels - 1; l >= 0; --l) {
         const dsr_u64 w = dsr_ld_relaxed(b.lvl[l] + pos);
         if (w == 0) return -1;
         const unsigned h = dsr_hash32(hint ^ ((unsigned)l * 0x9E3779B9u));
         const int k = dsr_nth_bit(w, (int)__umulhi(h, (unsigned)__popcll(w)));
-        pos = (pos << b.shift) + (dsr_u64)k;
+        pos = (pos << sh) + (dsr_u64)k;
     }
     return (long long)pos;
+}
+__device__ __forceinline__ long long dsr_hb_find(const dsr_hbm& b, unsigned hint) {
+    return b.shift == 6 ? dsr_hb_find_t<6>(b, hint) : dsr_hb_find_t<0>(b, hint);
 }
 
 /* clear() of Section 2.1: find a set bit and clear it. The printed loop is
@@ -551,14 +577,14 @@ __device__ __forceinline__ unsigned dsr_span_shift(const dsr_dev_heap& H, int T)
 /* End of every kernel that consumes R: the last CTA to finish resets the
  * block-list counter for the next do-all. Returns true in thread 0 of that
  * last CTA. */
-__device__ __forceinline__ bool dsr_doall_finish(const dsr_dev_heap& H) {
+__device__ __forceinline__ bool dsr_doall_finish(const dsr_dev_heap& H, bool keep_list = false) {
     __syncthreads();
     bool last = false;
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned t = atomicAdd(H.R_done, 1u);
         if (t == gridDim.x - 1) {
-            *(volatile uint32_t*)H.R_count = 0;
+            if (!keep_list) *(volatile uint32_t*)H.R_count = 0;
             *(volatile uint32_t*)H.R_done = 0;
             __threadfence();
             last = true;
@@ -582,10 +608,13 @@ __device__ __forceinline__ void dsr_call_finish(const dsr_dev_heap&, int, const 
  *   static __device__ void run(const dsr_dev_heap&, int T, const Args&, dsr_ref self);
  *   optionally static __device__ void finish(const dsr_dev_heap&, int T, const Args&);
  * Persistent grid-stride loop over (listed block, slot); a slot runs the
- * method iff it was occupied in the snapshot taken by the scan. */
+ * method iff it was occupied in the snapshot taken by the scan. With
+ * keep_list the block list R survives the kernel, for a following do-all
+ * over the same live set (one whose predecessor created and deleted no
+ * object of T) that then skips its scan. */
 template <class Method>
 __global__ void dsr_doall_kernel(const __grid_constant__ dsr_dev_heap H, int T,
-                                 const __grid_constant__ typename Method::Args args) {
+                                 const __grid_constant__ typename Method::Args args, int keep_list = 0) {
     const unsigned sh = dsr_span_shift(H, T);
     const dsr_u64 total = (dsr_u64)(*(volatile uint32_t*)H.R_count) << sh;
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
@@ -601,7 +630,7 @@ __global__ void dsr_doall_kernel(const __grid_constant__ dsr_dev_heap H, int T,
         if (((H.R_mask[i] >> s) & 1ull) && dsr_check(H.R_bid[i] < H.M, H.err, H.dbg, 10, i))
             Method::run(H, T, args, ((dsr_u64)H.R_bid[i] << 6) | s);
     }
-    if (dsr_doall_finish(H)) dsr_call_finish<Method>(H, T, args, 0);
+    if (dsr_doall_finish(H, keep_list != 0)) dsr_call_finish<Method>(H, T, args, 0);
 }
 
 /* Vector method kernel: a method may also provide
@@ -625,7 +654,7 @@ struct dsr_has_run4<M, decltype(M::run4(*(const dsr_dev_heap*)nullptr, 0, *(cons
 
 template <class Method>
 __global__ void dsr_doall_kernel_vec4(const __grid_constant__ dsr_dev_heap H, int T,
-                                      const __grid_constant__ typename Method::Args args) {
+                                      const __grid_constant__ typename Method::Args args, int keep_list = 0) {
     const unsigned sh = dsr_span_shift(H, T) - 2;  // quads per listed block: 16 (or 8)
     const dsr_u64 total = (dsr_u64)(*(volatile uint32_t*)H.R_count) << sh;
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
@@ -635,7 +664,7 @@ __global__ void dsr_doall_kernel_vec4(const __grid_constant__ dsr_dev_heap H, in
         const unsigned live = (unsigned)(H.R_mask[i] >> (4 * q)) & 0xFu;
         if (live && dsr_check(H.R_bid[i] < H.M, H.err, H.dbg, 10, i)) Method::run4(H, T, args, H.R_bid[i], 4 * q, live);
     }
-    if (dsr_doall_finish(H)) dsr_call_finish<Method>(H, T, args, 0);
+    if (dsr_doall_finish(H, keep_list != 0)) dsr_call_finish<Method>(H, T, args, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -680,7 +709,7 @@ __device__ __forceinline__ void dsr_call_finish_group(const dsr_group_dev&, int,
 
 template <class Method>
 __global__ void dsr_group_doall_kernel(const __grid_constant__ dsr_group_dev G, int T, unsigned sh,
-                                       const __grid_constant__ typename Method::Args args) {
+                                       const __grid_constant__ typename Method::Args args, int keep_list = 0) {
     __shared__ bool last;
     const dsr_u64 total = (dsr_u64)(*(volatile uint32_t*)G.R_count) << sh;
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
@@ -700,7 +729,7 @@ __global__ void dsr_group_doall_kernel(const __grid_constant__ dsr_group_dev G, 
         __threadfence();
         last = atomicAdd(G.R_done, 1u) == gridDim.x - 1;
         if (last) {
-            *(volatile uint32_t*)G.R_count = 0;
+            if (!keep_list) *(volatile uint32_t*)G.R_count = 0;
             *(volatile uint32_t*)G.R_done = 0;
             __threadfence();
         }

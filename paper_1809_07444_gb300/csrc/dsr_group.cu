@@ -10,7 +10,8 @@
 // fused scan: as the single-heap scan, over chunks of 256 block ids of any
 // heap of the group; every listed block is tagged with its heap index
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_group_scan(const __grid_constant__ dsr_group_dev G, int T) {
+__global__ void __launch_bounds__(256) k_group_scan(const __grid_constant__ dsr_group_dev G, int T,
+                                                    unsigned visits_mult) {
     __shared__ unsigned warp_n[8];
     __shared__ unsigned run_base;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(256) k_group_scan(const __grid_constant__ dsr_
             objs = __popcll(live);
         }
         objs = __reduce_add_sync(0xFFFFFFFFu, objs);
-        if (lane == 0 && objs) dsr_count(H.ctr, DSR_CTR_VISITS, objs);
+        if (lane == 0 && objs) dsr_count(H.ctr, DSR_CTR_VISITS, (dsr_u64)objs * visits_mult);
         __syncthreads();
     }
 }
@@ -65,12 +66,12 @@ extern "C" int dsr_group_check_record(dsr_group* g, uint32_t* err_out, uint64_t*
     return DSR_OK;
 }
 
-void dsr__group_launch_scan(const dsr_group* g, int type, cudaStream_t s) {
+void dsr__group_launch_scan(const dsr_group* g, int type, cudaStream_t s, unsigned visits_per_object) {
     if (g->n_chunks == 0) return;
     unsigned ctas = g->n_chunks;
     const unsigned cap = (unsigned)g->sm_count * 8;
     if (ctas > cap) ctas = cap;
-    k_group_scan<<<ctas, 256, 0, s>>>(g->dev, type);
+    k_group_scan<<<ctas, 256, 0, s>>>(g->dev, type, visits_per_object);
 }
 
 int dsr__group_grid(const dsr_group* g, const void* kernel, int threads) {

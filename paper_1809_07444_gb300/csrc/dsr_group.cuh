@@ -31,7 +31,7 @@ struct dsr_group {
     dsr_group_dev dev;
 };
 
-void dsr__group_launch_scan(const dsr_group* g, int type, cudaStream_t s);
+void dsr__group_launch_scan(const dsr_group* g, int type, cudaStream_t s, unsigned visits_per_object = 1);
 int dsr__group_grid(const dsr_group* g, const void* kernel, int threads);
 
 // Slots of a block of type T covered per listed block (log2): 5 for
@@ -43,12 +43,17 @@ inline unsigned dsr__group_span(const dsr_group* g, int type) {
 }
 
 // A group do-all: fused scan over every heap, then the method kernel.
+// with_scan / reuse as in dsr__doall: reuse > 0 keeps the block list for
+// that many following do-alls over the same live set, which pass
+// with_scan = false.
 template <class M>
-int dsr__group_doall(dsr_group* g, int type, const typename M::Args& args, cudaStream_t s) {
+int dsr__group_doall(dsr_group* g, int type, const typename M::Args& args, cudaStream_t s, bool with_scan = true,
+                     int reuse = 0) {
     if (type < 0 || type >= g->n_types) return DSR_E_INVALID;
-    dsr__group_launch_scan(g, type, s);
+    if (with_scan) dsr__group_launch_scan(g, type, s, 1u + (unsigned)reuse);
     const int threads = g->tune.threads > 0 ? g->tune.threads : 256;
     const int grid = dsr__group_grid(g, (const void*)dsr_group_doall_kernel<M>, threads);
-    dsr_group_doall_kernel<M><<<grid, threads, 0, s>>>(g->dev, type, dsr__group_span(g, type), args);
+    dsr_group_doall_kernel<M><<<grid, threads, 0, s>>>(g->dev, type, dsr__group_span(g, type), args,
+                                                       reuse > 0 ? 1 : 0);
     return dsr__check_launch("dsr_group_doall_kernel");
 }

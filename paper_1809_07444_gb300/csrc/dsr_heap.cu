@@ -208,7 +208,7 @@ __global__ void k_heap_mark_free(const __grid_constant__ dsr_dev_heap H, dsr_u64
 // and reserves its run of R with one atomicAdd; every listed block gets its
 // id and the snapshot of its occupied slots. Runs of R follow block order
 // within a round, so consecutive entries are usually neighbouring blocks.
-__global__ void __launch_bounds__(256) k_scan(const __grid_constant__ dsr_dev_heap H, int T) {
+__global__ void __launch_bounds__(256) k_scan(const __grid_constant__ dsr_dev_heap H, int T, unsigned visits_mult) {
     __shared__ unsigned warp_n[8];
     __shared__ unsigned run_base;
     const dsr_u64* leaf = H.alloc_bm[T].lvl[0];
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) k_scan(const __grid_constant__ dsr_dev_he
         __syncthreads();
     }
     objs = __reduce_add_sync(0xFFFFFFFFu, objs);
-    if (lane == 0 && objs) dsr_count(H.ctr, DSR_CTR_VISITS, objs);
+    if (lane == 0 && objs) dsr_count(H.ctr, DSR_CTR_VISITS, (dsr_u64)objs * visits_mult);
 }
 
 // Statistics: out[0] free blocks; out[1 + 3T + {0,1,2}] allocated blocks,
@@ -290,8 +290,8 @@ int dsr__scan_grid(const dsr_heap* h, int type) {
     return ctas < 1 ? 1 : (int)ctas;
 }
 
-void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s) {
-    k_scan<<<dsr__scan_grid(h, type), 256, 0, s>>>(h->dev, type);
+void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s, unsigned visits_per_object) {
+    k_scan<<<dsr__scan_grid(h, type), 256, 0, s>>>(h->dev, type, visits_per_object);
 }
 
 int dsr__persistent_grid(const dsr_heap* h, const void* kernel, int threads) {

@@ -43,17 +43,19 @@ int dsr__scan_grid(const dsr_heap* h, int type);
 // True if every field array of `type` starts on a 16-byte boundary within a
 // block and the capacity is a multiple of 4 (vector methods may run).
 bool dsr__vec4_ok(const dsr_heap* h, int type);
-void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s);
+void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s, unsigned visits_per_object = 1);
 
 // Run a do-all: scan + compaction of allocated[type] into R, then the method
 // kernel over the listed blocks.
 // ev_scan / ev_run (optional): recorded on s after the scan and after the
-// method kernel, for per-phase timing.
+// method kernel, for per-phase timing. reuse > 0: the block list is kept for
+// `reuse` more do-alls over the same live set, and the scan counts each
+// listed object 1 + reuse times as visited (the visits those do-alls make).
 template <class M>
 int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t s, bool with_scan = true,
-               cudaEvent_t ev_scan = nullptr, cudaEvent_t ev_run = nullptr) {
+               cudaEvent_t ev_scan = nullptr, cudaEvent_t ev_run = nullptr, int reuse = 0) {
     if (type < 0 || type >= h->dev.n_types) return DSR_E_INVALID;
-    if (with_scan) dsr__launch_scan(h, type, s);
+    if (with_scan) dsr__launch_scan(h, type, s, 1u + (unsigned)reuse);
     if (ev_scan) cudaEventRecord(ev_scan, s);
     static int grid_cache[17] = {0};
     const int threads = h->tune.threads;
@@ -76,13 +78,13 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
             if (vgrid == 0 || h->tune.ctas_per_sm > 0)
                 vgrid = dsr__persistent_grid(h, (const void*)dsr_doall_kernel_vec4<M>, threads);
             int gv = vgrid < g ? vgrid : g;
-            dsr_doall_kernel_vec4<M><<<gv, threads, 0, s>>>(h->dev, type, args);
+            dsr_doall_kernel_vec4<M><<<gv, threads, 0, s>>>(h->dev, type, args, reuse > 0 ? 1 : 0);
             rc = dsr__check_launch("dsr_doall_kernel_vec4");
             if (ev_run) cudaEventRecord(ev_run, s);
             return rc;
         }
     }
-    dsr_doall_kernel<M><<<g, threads, 0, s>>>(h->dev, type, args);
+    dsr_doall_kernel<M><<<g, threads, 0, s>>>(h->dev, type, args, reuse > 0 ? 1 : 0);
     rc = dsr__check_launch("dsr_doall_kernel");
     if (ev_run) cudaEventRecord(ev_run, s);
     return rc;

@@ -385,11 +385,14 @@ extern "C" int dsr_wator_step(dsr_wator* w, int n_steps, void* stream) {
             cudaEventRecord(e[0], s);
         }
         auto E = [&](int k) { return e ? e[k] : nullptr; };
-        int rc = dsr__doall<MFishChoose>(h, FISH, w->inst, s, true, E(1), E(2));
-        if (!rc) rc = dsr__doall<MFishMove>(h, FISH, w->inst, s, true, E(3), E(4));
+        // F1 neither creates nor deletes fish, so F2 runs over F1's block
+        // list (the fish live at the start of the step); likewise S2 over
+        // S1's (the sharks that survived S0).
+        int rc = dsr__doall<MFishChoose>(h, FISH, w->inst, s, true, E(1), E(2), 1);
+        if (!rc) rc = dsr__doall<MFishMove>(h, FISH, w->inst, s, false, E(3), E(4));
         if (!rc) rc = dsr__doall<MSharkStarve>(h, SHARK, w->inst, s, true, E(5), E(6));
-        if (!rc) rc = dsr__doall<MSharkChoose>(h, SHARK, w->inst, s, true, E(7), E(8));
-        if (!rc) rc = dsr__doall<MSharkMove>(h, SHARK, w->inst, s, true, E(9), E(10));
+        if (!rc) rc = dsr__doall<MSharkChoose>(h, SHARK, w->inst, s, true, E(7), E(8), 1);
+        if (!rc) rc = dsr__doall<MSharkMove>(h, SHARK, w->inst, s, false, E(9), E(10));
         if (rc) return rc;
     }
     return DSR_OK;
@@ -555,11 +558,12 @@ extern "C" int dsr_wator_batch_remove(dsr_wator_batch* b, int inst) {
 static int issue_batch_step(dsr_wator_batch* b, cudaStream_t s) {
     dsr_group* g = b->group;
     BatchArgs a{b->table_d};
-    int rc = dsr__group_doall<GFishChoose>(g, FISH, a, s);
-    if (!rc) rc = dsr__group_doall<GFishMove>(g, FISH, a, s);
+    // F2 and S2 run over the block lists of F1 and S1 (see dsr_wator_step)
+    int rc = dsr__group_doall<GFishChoose>(g, FISH, a, s, true, 1);
+    if (!rc) rc = dsr__group_doall<GFishMove>(g, FISH, a, s, false);
     if (!rc) rc = dsr__group_doall<GSharkStarve>(g, SHARK, a, s);
-    if (!rc) rc = dsr__group_doall<GSharkChoose>(g, SHARK, a, s);
-    if (!rc) rc = dsr__group_doall<GSharkMove>(g, SHARK, a, s);
+    if (!rc) rc = dsr__group_doall<GSharkChoose>(g, SHARK, a, s, true, 1);
+    if (!rc) rc = dsr__group_doall<GSharkMove>(g, SHARK, a, s, false);
     return rc;
 }
 
