@@ -284,12 +284,24 @@ __device__ __forceinline__ unsigned dsr_hash32(unsigned x) {
  * runs of zeros, and the first bit of a container whose high bits are zero).
  * Returns -1 (FAIL) if a container on the way is empty, which can happen
  * while the bitmap is temporarily inconsistent. */
+/* The descent is preceded by a shortcut: one leaf container, drawn from the
+ * hint, is read together with the top-level container (two independent
+ * loads). If that leaf has a set bit, the search ends after one round trip
+ * instead of one per level; this is the common case when most leaves are
+ * non-empty (an allocator whose blocks of a type mostly have free slots).
+ * Otherwise the descent continues from the top-level word already read. */
 template <unsigned SH>
 __device__ __forceinline__ long long dsr_hb_find_t(const dsr_hbm& b, unsigned hint) {
     const unsigned sh = dsr_hb_shift<SH>(b);
+    const int top = b.n_levels - 1;
+    const unsigned hp = dsr_hash32(hint ^ 0x5851F42Du);
+    const dsr_u64 li = __umulhi(hp, b.nwords[0]);
+    const dsr_u64 lw = dsr_ld_relaxed(b.lvl[0] + li);
+    dsr_u64 w = dsr_ld_relaxed(b.lvl[top]);
+    if (lw != 0) return (long long)((li << sh) + (dsr_u64)dsr_nth_bit(lw, (int)__umulhi(dsr_hash32(hp), (unsigned)__popcll(lw))));
     dsr_u64 pos = 0;
-    for (int l = b.n_levels - 1; l >= 0; --l) {
-        const dsr_u64 w = dsr_ld_relaxed(b.lvl[l] + pos);
+    for (int l = top; l >= 0; --l) {
+        if (l != top) w = dsr_ld_relaxed(b.lvl[l] + pos);
         if (w == 0) return -1;
         const unsigned h = dsr_hash32(hint ^ ((unsigned)l * 0x9E3779B9u));
         const int k = dsr_nth_bit(w, (int)__umulhi(h, (unsigned)__popcll(w)));

@@ -76,6 +76,8 @@ __device__ __forceinline__ void fish_move(const dsr_dev_heap& H, const WatorInst
     const dsr_u64 t = *(volatile dsr_u64*)I.step;
     int32_t* px = dsr_field<int32_t>(H, FISH, self, X);
     int32_t* py = dsr_field<int32_t>(H, FISH, self, Y);
+    int32_t* timer = dsr_field<int32_t>(H, FISH, self, TIMER);
+    const int32_t age = *timer;  // loaded with x and y: one round trip fewer for movers
     const uint32_t c = (uint32_t)(*py * I.p.W + *px);
     if (!cell_ok(H, I, c, 6)) return;
     const uint32_t tgt = I.intent[c];
@@ -85,9 +87,8 @@ __device__ __forceinline__ void fish_move(const dsr_dev_heap& H, const WatorInst
     I.grid[tgt] = (self << 2) | K_FISH;
     *px = (int32_t)(tgt % (uint32_t)I.p.W);
     *py = (int32_t)(tgt / (uint32_t)I.p.W);
-    int32_t* timer = dsr_field<int32_t>(H, FISH, self, TIMER);
     dsr_u64 left = K_EMPTY;
-    if (*timer >= I.p.fish_breed) {
+    if (age >= I.p.fish_breed) {
         *timer = 0;
         const dsr_ref n = dsr_new(H, FISH);
         if (n != DSR_NULL) {
@@ -139,6 +140,9 @@ __device__ __forceinline__ void shark_move(const dsr_dev_heap& H, const WatorIns
     const dsr_u64 t = *(volatile dsr_u64*)I.step;
     int32_t* px = dsr_field<int32_t>(H, SHARK, self, X);
     int32_t* py = dsr_field<int32_t>(H, SHARK, self, Y);
+    int32_t* timer = dsr_field<int32_t>(H, SHARK, self, TIMER);
+    int32_t* energy = dsr_field<int32_t>(H, SHARK, self, ENERGY);
+    const int32_t age = *timer, e0 = *energy;  // loaded with x and y
     const uint32_t c = (uint32_t)(*py * I.p.W + *px);
     if (!cell_ok(H, I, c, 6)) return;
     const uint32_t tgt = I.intent[c];
@@ -146,17 +150,15 @@ __device__ __forceinline__ void shark_move(const dsr_dev_heap& H, const WatorIns
     if (tgt == NO_MOVE || I.claim[tgt] != claim_key(t, 1, c)) return;
     dsr_count_lanes(H.ctr, DSR_CTR_APP0);
     const dsr_u64 g = I.grid[tgt];
-    int32_t* energy = dsr_field<int32_t>(H, SHARK, self, ENERGY);
     if ((g & 3) == K_FISH) {
         dsr_delete(H, g >> 2);
-        *energy += I.p.shark_gain;
+        *energy = e0 + I.p.shark_gain;
     }
     I.grid[tgt] = (self << 2) | K_SHARK;
     *px = (int32_t)(tgt % (uint32_t)I.p.W);
     *py = (int32_t)(tgt / (uint32_t)I.p.W);
-    int32_t* timer = dsr_field<int32_t>(H, SHARK, self, TIMER);
     dsr_u64 left = K_EMPTY;
-    if (*timer >= I.p.shark_breed) {
+    if (age >= I.p.shark_breed) {
         *timer = 0;
         const dsr_ref n = dsr_new(H, SHARK);
         if (n != DSR_NULL) {
