@@ -498,6 +498,54 @@ def bench_gol(W=64, gens=100, reps=3):
             "gen_ms_p50": lat[len(lat) // 2], "gen_ms_p99": lat[int(len(lat) * 0.99)], "launches_per_gen": 6}
 
 
+def bench_comparators(steps=50, warmup=5):
+    """Section 4 comparators on the bench workload: wa-tor 2048 x 2048 with
+    no dynamic allocation, agents in per-cell SOA arrays and in per-cell AOS
+    structs (every phase a kernel over all 4.2 M cells), timed like the
+    headline (L2 flushed before every step, CUDA events per step). Same
+    visits as the allocator-based form, so object-updates/s compare."""
+    import torch
+    from paper_1809_07444_gb300 import workloads as WL
+    from paper_1809_07444_gb300.apps import WatorStatic
+
+    k0 = WL.wator_initial(W_SIDE, W_SIDE, SEED)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, aos in (("static_soa", False), ("static_aos", True)):
+        w = WatorStatic(W_SIDE, W_SIDE, k0, SEED, aos=aos)
+        w.step(warmup)
+        torch.cuda.synchronize()
+        v0 = w.visits()
+        evs = [_ev() for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            evs[k][0].record()
+            w.step(1)
+            evs[k][1].record()
+        torch.cuda.synchronize()
+        t = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+        v = w.visits() - v0
+        out[name] = {"ms_per_step": t * 1e3 / steps, "object_updates_per_s": v / t,
+                     "cells_per_s": W_SIDE * W_SIDE * 5 * steps / t, "launches_per_step": 5}
+        del w
+    del flush
+    torch.cuda.empty_cache()
+    out["workload"] = "wator-2048x2048, steps %d-%d, L2 flushed before every step" % (warmup + 1, warmup + steps)
+    return out
+
+
+def bench_space(heap_bytes=32 << 20, steps=100):
+    """Fig. 8: the largest wa-tor torus a 32 MB heap runs for 100 steps
+    without running out of memory, per tuning, with the peak bytes of live
+    object data as a fraction of the heap."""
+    from paper_1809_07444_gb300 import space
+
+    t0 = time.perf_counter()
+    out = space.experiment(heap_bytes, steps)
+    out["search_s"] = time.perf_counter() - t0
+    return out
+
+
 def bench_nbody(n=65536, steps=5):
     """C3: n-body with merging, 65,536 bodies, FP32 on the GPU. FLOPs counted
     as 20 per pair for the force (softened inverse-cube, three FMAs into the
@@ -703,6 +751,8 @@ def main():
         line["alloc_free_microbench"] = bench_alloc_sweep()
         line["streaming_doall"] = bench_streaming_sweep()
         line["gol_64"] = bench_gol()
+        line["space_efficiency"] = bench_space()
+        line["comparators"] = bench_comparators()
         line["nbody_65536"] = bench_nbody()
         if args.served_seconds > 0:
             line["served"] = bench_served(args.served_seconds)

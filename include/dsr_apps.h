@@ -117,6 +117,30 @@ int dsr_wator_phase_timing(dsr_wator* w, int max_steps);
  * the number of steps. Starts a new window (the events are reused). */
 int dsr_wator_phase_times(dsr_wator* w, double* out_ms /* 10 */, int* steps);
 
+/* ---- wa-tor without dynamic allocation ------------------------------------
+ * The "Baseline AOS/SOA" comparators of Section 4: the agents live in
+ * per-cell arrays (aos = 0: one array per field; aos = 1: one 12-byte struct
+ * per cell), each phase is a kernel over all cells, and a move copies the
+ * agent's data to the target cell. Same rules, random draws and claim keys
+ * as dsr_wator_*, hence the same state after every step. The workspace
+ * (device, 256-byte aligned, dsr_wator_static_bytes) holds the cells, the
+ * claim and intent arrays and a visit counter. The step number is kept on
+ * the host. */
+typedef struct dsr_wator_static dsr_wator_static;
+int dsr_wator_static_bytes(int W, int H, int aos, size_t* out);
+int dsr_wator_static_create(const dsr_wator_params* p, const void* kind0_dev, void* workspace_dev, int aos,
+                            void* stream, dsr_wator_static** out);
+int dsr_wator_static_step(dsr_wator_static* w, int n_steps, void* stream);
+/* Adds the object-state hash of dsr_heap_hash (Fish {x, y, timer}, Shark
+ * {x, y, timer, energy}) to hash_dev[0] (fish) and hash_dev[1] (sharks). */
+int dsr_wator_static_hash(dsr_wator_static* w, void* hash_dev, void* stream);
+/* Per-cell state: kind uint8 (0 empty, 1 fish, 2 shark), timer and energy
+ * int32 (0 where unused), each W*H entries in cell order. */
+int dsr_wator_static_state(dsr_wator_static* w, void* kind_dev, void* timer_dev, void* energy_dev, void* stream);
+/* Agents visited by the phase kernels so far (synchronises the device). */
+int dsr_wator_static_visits(dsr_wator_static* w, uint64_t* out);
+int dsr_wator_static_destroy(dsr_wator_static* w);
+
 /* ---- batched wa-tor ----------------------------------------------------------
  * Many independent wa-tor instances (each with its own sizes, parameters and
  * seed) advance together: every instance has its own heap in a heap group

@@ -115,6 +115,13 @@ SIGNATURES = {
     "dsr_wator_kinds": (_i, [_vp, _vp, _vp]),
     "dsr_wator_destroy": (_i, [_vp]),
     "dsr_wator_phase_timing": (_i, [_vp, _i]),
+    "dsr_wator_static_bytes": (_i, [_i, _i, _i, C.POINTER(_sz)]),
+    "dsr_wator_static_create": (_i, [_vp, _vp, _vp, _i, _vp, C.POINTER(_vp)]),
+    "dsr_wator_static_step": (_i, [_vp, _i, _vp]),
+    "dsr_wator_static_hash": (_i, [_vp, _vp, _vp]),
+    "dsr_wator_static_state": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "dsr_wator_static_visits": (_i, [_vp, C.POINTER(_u64)]),
+    "dsr_wator_static_destroy": (_i, [_vp]),
     "dsr_wator_phase_times": (_i, [_vp, C.POINTER(C.c_double), C.POINTER(_i)]),
     "dsr_nbody_types": (_i, [C.POINTER(TypeDesc)]),
     "dsr_nbody_workspace_bytes": (_i, [_vp, _u64, C.POINTER(_sz)]),

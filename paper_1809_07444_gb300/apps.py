@@ -134,6 +134,70 @@ class Wator:
         return out.cpu().numpy().reshape(self.H, self.W)
 
 
+class WatorStatic:
+    """Wa-tor without dynamic allocation (per-cell arrays; aos selects the
+    layout), the comparator of the allocator-based form."""
+
+    def __init__(self, W, H, kind0, seed, aos=False, fish_breed=3, shark_breed=10, shark_energy0=5, shark_gain=3,
+                 stream=None):
+        self.lib = L.load()
+        self.W, self.H = W, H
+        n = C.c_size_t(0)
+        L.check(self.lib.dsr_wator_static_bytes(W, H, 1 if aos else 0, C.byref(n)), "dsr_wator_static_bytes")
+        self.workspace = torch.empty(n.value, dtype=torch.uint8, device="cuda")
+        k0 = torch.as_tensor(np.ascontiguousarray(kind0, dtype=np.uint8).reshape(-1)).cuda()
+        self.params = L.WatorParams(W, H, seed, fish_breed, shark_breed, shark_energy0, shark_gain)
+        h = C.c_void_p()
+        L.check(self.lib.dsr_wator_static_create(C.byref(self.params), C.c_void_p(k0.data_ptr()),
+                                                 C.c_void_p(self.workspace.data_ptr()), 1 if aos else 0,
+                                                 _stream_ptr(stream), C.byref(h)), "dsr_wator_static_create")
+        self.handle = h
+        self._k0 = k0
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.dsr_wator_static_destroy(self.handle)
+            self.handle = None
+
+    def step(self, n=1, stream=None):
+        L.check(self.lib.dsr_wator_static_step(self.handle, n, _stream_ptr(stream)), "dsr_wator_static_step")
+
+    def hash(self):
+        out = torch.zeros(2, dtype=torch.int64, device="cuda")
+        L.check(self.lib.dsr_wator_static_hash(self.handle, C.c_void_p(out.data_ptr()), _stream_ptr()),
+                "dsr_wator_static_hash")
+        v = out.cpu().numpy().view(np.uint64)
+        return int(v[0]), int(v[1])
+
+    def state(self):
+        n = self.W * self.H
+        k = torch.empty(n, dtype=torch.uint8, device="cuda")
+        t = torch.empty(n, dtype=torch.int32, device="cuda")
+        e = torch.empty(n, dtype=torch.int32, device="cuda")
+        L.check(self.lib.dsr_wator_static_state(self.handle, C.c_void_p(k.data_ptr()), C.c_void_p(t.data_ptr()),
+                                                C.c_void_p(e.data_ptr()), _stream_ptr()), "dsr_wator_static_state")
+        return k.cpu().numpy(), t.cpu().numpy(), e.cpu().numpy()
+
+    def dump(self):
+        """(fish int32[n, 3] sorted, sharks int32[m, 4] sorted), as Wator.dump."""
+        k, t, e = self.state()
+        c = np.arange(self.W * self.H)
+        x, y = (c % self.W).astype(np.int32), (c // self.W).astype(np.int32)
+        f = k == 1
+        s = k == 2
+        fish = np.stack([x[f], y[f], t[f]], axis=1).astype(np.int32)
+        sharks = np.stack([x[s], y[s], t[s], e[s]], axis=1).astype(np.int32)
+        return _sorted_rows(fish), _sorted_rows(sharks)
+
+    def grid(self):
+        return self.state()[0].reshape(self.H, self.W)
+
+    def visits(self):
+        v = C.c_uint64(0)
+        L.check(self.lib.dsr_wator_static_visits(self.handle, C.byref(v)), "dsr_wator_static_visits")
+        return int(v.value)
+
+
 def _heap_base(lib, handle):
     """Device address of a heap's arena (its device view starts with the data pointer)."""
     n = lib.dsr_dev_heap_size()

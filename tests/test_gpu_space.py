@@ -1,0 +1,31 @@
+"""Space-efficiency search (Section 4, Fig. 8): the largest wa-tor side that a
+fixed heap runs without running out of memory."""
+import pytest
+
+from paper_1809_07444_gb300 import space
+
+pytestmark = pytest.mark.gpu
+
+
+def test_max_side_fits_and_the_next_sizes_do_not():
+    heap, steps = 2 << 20, 30
+    side, peak = space.max_wator_side(heap, steps)
+    assert side > 16
+    ok, peak2 = space.wator_fits(side, heap, steps)
+    assert ok and peak2 == peak  # deterministic
+    assert 0 < peak <= heap
+    # a clearly larger torus does not fit the same heap
+    assert not space.wator_fits(int(side * 1.25) + 2, heap, steps)[0]
+
+
+def test_smaller_blocks_hold_at_least_as_large_a_problem():
+    heap, steps = 2 << 20, 30
+    s64, _ = space.max_wator_side(heap, steps)
+    s32, _ = space.max_wator_side(heap, steps, tuning={"cap_min": 32})
+    assert s32 >= s64 * 0.95  # 32-slot blocks waste no more space at the ends of runs
+
+
+def test_experiment_reports_every_tuning():
+    out = space.experiment(heap_bytes=1 << 20, steps=10)
+    assert [r["tuning"] for r in out["rows"]] == ["default", {"cap_min": 32}, {"fanout": 16}]
+    assert all(r["max_side"] > 0 and 0 < r["efficiency"] <= 1 for r in out["rows"])
