@@ -499,20 +499,28 @@ def bench_gol(W=64, gens=100, reps=3):
 
 
 def bench_comparators(steps=50, warmup=5):
-    """Section 4 comparators on the bench workload: wa-tor 2048 x 2048 with
-    no dynamic allocation, agents in per-cell SOA arrays and in per-cell AOS
-    structs (every phase a kernel over all 4.2 M cells), timed like the
-    headline (L2 flushed before every step, CUDA events per step). Same
-    visits as the allocator-based form, so object-updates/s compare."""
+    """Section 4 comparators on the bench workload, timed like the headline
+    (L2 flushed before every step, CUDA events per step): wa-tor 2048 x 2048
+    with no dynamic allocation (agents in per-cell SOA arrays, and in
+    per-cell AOS structs; every phase a kernel over all 4.2 M cells), and
+    with the BitmapAlloc comparator (per-type object arrays of structs, flat
+    bitmaps). All make the same visits as the dsr form, so object-updates/s
+    compare."""
     import torch
     from paper_1809_07444_gb300 import workloads as WL
     from paper_1809_07444_gb300.apps import WatorStatic
 
+    from paper_1809_07444_gb300.apps import WatorBitmap
+
     k0 = WL.wator_initial(W_SIDE, W_SIDE, SEED)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     out = {}
-    for name, aos in (("static_soa", False), ("static_aos", True)):
-        w = WatorStatic(W_SIDE, W_SIDE, k0, SEED, aos=aos)
+    for name, aos in (("static_soa", False), ("static_aos", True), ("bitmap_alloc_aos", None)):
+        if aos is None:
+            w = WatorBitmap(W_SIDE, W_SIDE, k0, SEED)
+            w.visits = lambda w=w: w.heap.counters()["visits"]
+        else:
+            w = WatorStatic(W_SIDE, W_SIDE, k0, SEED, aos=aos)
         w.step(warmup)
         torch.cuda.synchronize()
         v0 = w.visits()
@@ -526,7 +534,7 @@ def bench_comparators(steps=50, warmup=5):
         t = sum(a.elapsed_time(b) for a, b in evs) / 1e3
         v = w.visits() - v0
         out[name] = {"ms_per_step": t * 1e3 / steps, "object_updates_per_s": v / t,
-                     "cells_per_s": W_SIDE * W_SIDE * 5 * steps / t, "launches_per_step": 5}
+                     "launches_per_step": 5 if aos is not None else LAUNCHES_PER_STEP}
         del w
     del flush
     torch.cuda.empty_cache()

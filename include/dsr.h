@@ -262,6 +262,27 @@ int dsr_heap_check_record(dsr_heap* heap, uint32_t* err_out, uint64_t* record_ou
 /* Group do-all with a built-in method (DSR_METHOD_COUNT). */
 int dsr_group_parallel_do(dsr_group* g, int type, int method, const void* args, size_t args_bytes, void* stream);
 
+/* ---- BitmapAlloc: the comparison allocator of Section 4 -------------------
+ * "Allocates objects in a large array and uses a bitmap to find empty
+ * slots": per type, an array of capacity[T] objects stored as structs (AOS)
+ * and a flat bitmap with one bit per slot; no blocks, no bitmap hierarchy.
+ * No counterpart in the paper's interface; it exists to compare against.
+ * capacity[T] must be a positive multiple of 64. Device code uses the
+ * dsr_new / dsr_delete / dsr_field overloads on dsr_bm_dev
+ * (paper_1809_07444_gb300/csrc/dsr_bitmap_alloc.cuh). Handles are
+ * (type << 40) | slot. Errors as for dsr heaps. */
+typedef struct dsr_bm_heap dsr_bm_heap;
+int dsr_bm_heap_bytes(const dsr_type_desc* types, int n_types, const uint64_t* capacity, size_t* out);
+int dsr_bm_heap_create(const dsr_type_desc* types, int n_types, const uint64_t* capacity, void* arena_dev,
+                       size_t arena_bytes, void* stream, dsr_bm_heap** out);
+int dsr_bm_heap_destroy(dsr_bm_heap* heap);
+/* live_out[T] = objects of type T; *err_out = sticky DSR_ERR_* bits (synchronises). */
+int dsr_bm_heap_stats(dsr_bm_heap* heap, void* stream, uint64_t* live_out, uint32_t* err_out);
+/* The object-state hash of dsr_heap_hash over the live objects of `type`
+ * (types with 4-byte fields only). */
+int dsr_bm_heap_hash(dsr_bm_heap* heap, int type, void* hash_dev, void* stream);
+int dsr_bm_heap_counters(dsr_bm_heap* heap, void* stream, uint64_t* out);
+
 /* Text for a status code; the CUDA error of the last DSR_E_CUDA. */
 const char* dsr_status_string(int status);
 const char* dsr_last_cuda_error(void);

@@ -117,6 +117,15 @@ int dsr_wator_phase_timing(dsr_wator* w, int max_steps);
  * the number of steps. Starts a new window (the events are reused). */
 int dsr_wator_phase_times(dsr_wator* w, double* out_ms /* 10 */, int* steps);
 
+/* Wa-tor on the BitmapAlloc comparator (dsr_bm_heap_* in dsr.h): the same
+ * rules and workspace as dsr_wator_*, with Fish and Shark objects in the
+ * comparator's per-type arrays (types 0 and 1 as dsr_wator_types gives). */
+typedef struct dsr_wator_bm dsr_wator_bm;
+int dsr_wator_bm_create(dsr_bm_heap* heap, const dsr_wator_params* p, const void* kind0_dev, void* workspace_dev,
+                        void* stream, dsr_wator_bm** out);
+int dsr_wator_bm_step(dsr_wator_bm* w, int n_steps, void* stream);
+int dsr_wator_bm_destroy(dsr_wator_bm* w);
+
 /* ---- wa-tor without dynamic allocation ------------------------------------
  * The "Baseline AOS/SOA" comparators of Section 4: the agents live in
  * per-cell arrays (aos = 0: one array per field; aos = 1: one 12-byte struct

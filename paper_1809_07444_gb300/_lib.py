@@ -115,6 +115,15 @@ SIGNATURES = {
     "dsr_wator_kinds": (_i, [_vp, _vp, _vp]),
     "dsr_wator_destroy": (_i, [_vp]),
     "dsr_wator_phase_timing": (_i, [_vp, _i]),
+    "dsr_bm_heap_bytes": (_i, [C.POINTER(TypeDesc), _i, C.POINTER(_u64), C.POINTER(_sz)]),
+    "dsr_bm_heap_create": (_i, [C.POINTER(TypeDesc), _i, C.POINTER(_u64), _vp, _sz, _vp, C.POINTER(_vp)]),
+    "dsr_bm_heap_destroy": (_i, [_vp]),
+    "dsr_bm_heap_stats": (_i, [_vp, _vp, C.POINTER(_u64), C.POINTER(_u32)]),
+    "dsr_bm_heap_hash": (_i, [_vp, _i, _vp, _vp]),
+    "dsr_bm_heap_counters": (_i, [_vp, _vp, C.POINTER(_u64)]),
+    "dsr_wator_bm_create": (_i, [_vp, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
+    "dsr_wator_bm_step": (_i, [_vp, _i, _vp]),
+    "dsr_wator_bm_destroy": (_i, [_vp]),
     "dsr_wator_static_bytes": (_i, [_i, _i, _i, C.POINTER(_sz)]),
     "dsr_wator_static_create": (_i, [_vp, _vp, _vp, _i, _vp, C.POINTER(_vp)]),
     "dsr_wator_static_step": (_i, [_vp, _i, _vp]),

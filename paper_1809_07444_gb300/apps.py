@@ -134,6 +134,44 @@ class Wator:
         return out.cpu().numpy().reshape(self.H, self.W)
 
 
+class WatorBitmap:
+    """Wa-tor on the BitmapAlloc comparator heap (same rules as Wator);
+    capacity per type defaults to one object per cell."""
+
+    def __init__(self, W, H, kind0, seed, capacity=None, fish_breed=3, shark_breed=10, shark_energy0=5,
+                 shark_gain=3, stream=None):
+        from .heap import BitmapHeap
+        self.lib = L.load()
+        self.W, self.H = W, H
+        n = -(-(W * H) // 64) * 64
+        self.heap = BitmapHeap(WATOR_TYPES, capacity or [n, n], stream=stream)
+        ws = C.c_size_t(0)
+        L.check(self.lib.dsr_wator_workspace_bytes(W, H, C.byref(ws)), "dsr_wator_workspace_bytes")
+        self.workspace = torch.empty(ws.value, dtype=torch.uint8, device="cuda")
+        k0 = torch.as_tensor(np.ascontiguousarray(kind0, dtype=np.uint8).reshape(-1)).cuda()
+        self.params = L.WatorParams(W, H, seed, fish_breed, shark_breed, shark_energy0, shark_gain)
+        h = C.c_void_p()
+        L.check(self.lib.dsr_wator_bm_create(self.heap.handle, C.byref(self.params), C.c_void_p(k0.data_ptr()),
+                                             C.c_void_p(self.workspace.data_ptr()), _stream_ptr(stream),
+                                             C.byref(h)), "dsr_wator_bm_create")
+        self.handle = h
+        self._k0 = k0
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.dsr_wator_bm_destroy(self.handle)
+            self.handle = None
+
+    def step(self, n=1, stream=None):
+        L.check(self.lib.dsr_wator_bm_step(self.handle, n, _stream_ptr(stream)), "dsr_wator_bm_step")
+
+    def hash(self):
+        return self.heap.hash(0), self.heap.hash(1)
+
+    def counts(self):
+        return tuple(self.heap.stats()["live_objects"])
+
+
 class WatorStatic:
     """Wa-tor without dynamic allocation (per-cell arrays; aos selects the
     layout), the comparator of the allocator-based form."""

@@ -4,6 +4,7 @@
 // view of one instance; the plain form runs them as do-alls over one heap,
 // the batched form as group do-alls over the heaps of many instances.
 #include "dsr_apps.h"
+#include "dsr_bitmap_alloc.cuh"
 #include "dsr_group.cuh"
 
 namespace {
@@ -37,7 +38,8 @@ __device__ __forceinline__ void neighbours(uint32_t c, int W, int H, uint32_t nb
 }
 
 // Checked builds only: the instance exists and c is one of its cells.
-__device__ __forceinline__ bool cell_ok(const dsr_dev_heap& H, const WatorInst& I, uint32_t c, unsigned code) {
+template <class HP>
+__device__ __forceinline__ bool cell_ok(const HP& H, const WatorInst& I, uint32_t c, unsigned code) {
     return dsr_check(I.grid != nullptr && c < (uint32_t)I.p.W * (uint32_t)I.p.H, H.err, H.dbg, code, c);
 }
 
@@ -52,7 +54,8 @@ __device__ __forceinline__ int pick(unsigned m, unsigned k) {
 }
 
 // F1: age, pick an empty neighbour, claim it.
-__device__ __forceinline__ void fish_choose(const dsr_dev_heap& H, const WatorInst& I, dsr_ref self) {
+template <class HP>
+__device__ __forceinline__ void fish_choose(const HP& H, const WatorInst& I, dsr_ref self) {
     const dsr_u64 t = *(volatile dsr_u64*)I.step;
     const int x = *dsr_field<int32_t>(H, FISH, self, X), y = *dsr_field<int32_t>(H, FISH, self, Y);
     *dsr_field<int32_t>(H, FISH, self, TIMER) += 1;
@@ -72,7 +75,8 @@ __device__ __forceinline__ void fish_choose(const dsr_dev_heap& H, const WatorIn
 }
 
 // F2: winners move and breed.
-__device__ __forceinline__ void fish_move(const dsr_dev_heap& H, const WatorInst& I, dsr_ref self) {
+template <class HP>
+__device__ __forceinline__ void fish_move(const HP& H, const WatorInst& I, dsr_ref self) {
     const dsr_u64 t = *(volatile dsr_u64*)I.step;
     int32_t* px = dsr_field<int32_t>(H, FISH, self, X);
     int32_t* py = dsr_field<int32_t>(H, FISH, self, Y);
@@ -102,7 +106,8 @@ __device__ __forceinline__ void fish_move(const dsr_dev_heap& H, const WatorInst
 }
 
 // S0: starvation.
-__device__ __forceinline__ void shark_starve(const dsr_dev_heap& H, const WatorInst& I, dsr_ref self) {
+template <class HP>
+__device__ __forceinline__ void shark_starve(const HP& H, const WatorInst& I, dsr_ref self) {
     int32_t* e = dsr_field<int32_t>(H, SHARK, self, ENERGY);
     if (--*e > 0) return;
     const int x = *dsr_field<int32_t>(H, SHARK, self, X), y = *dsr_field<int32_t>(H, SHARK, self, Y);
@@ -111,7 +116,8 @@ __device__ __forceinline__ void shark_starve(const dsr_dev_heap& H, const WatorI
 }
 
 // S1: age, prefer a neighbouring fish, else an empty cell; claim it.
-__device__ __forceinline__ void shark_choose(const dsr_dev_heap& H, const WatorInst& I, dsr_ref self) {
+template <class HP>
+__device__ __forceinline__ void shark_choose(const HP& H, const WatorInst& I, dsr_ref self) {
     const dsr_u64 t = *(volatile dsr_u64*)I.step;
     const int x = *dsr_field<int32_t>(H, SHARK, self, X), y = *dsr_field<int32_t>(H, SHARK, self, Y);
     *dsr_field<int32_t>(H, SHARK, self, TIMER) += 1;
@@ -136,7 +142,8 @@ __device__ __forceinline__ void shark_choose(const dsr_dev_heap& H, const WatorI
 }
 
 // S2: winners move, eat and breed.
-__device__ __forceinline__ void shark_move(const dsr_dev_heap& H, const WatorInst& I, dsr_ref self) {
+template <class HP>
+__device__ __forceinline__ void shark_move(const HP& H, const WatorInst& I, dsr_ref self) {
     const dsr_u64 t = *(volatile dsr_u64*)I.step;
     int32_t* px = dsr_field<int32_t>(H, SHARK, self, X);
     int32_t* py = dsr_field<int32_t>(H, SHARK, self, Y);
@@ -173,28 +180,40 @@ __device__ __forceinline__ void shark_move(const dsr_dev_heap& H, const WatorIns
 }
 
 // ---- plain form: do-all methods over one heap ------------------------------
-struct MFishChoose {
+// (HP: the heap type; dsr_dev_heap, or dsr_bm_dev for the BitmapAlloc
+// comparator)
+template <class HP>
+struct MFishChooseT {
     typedef WatorInst Args;
-    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s) { fish_choose(H, a, s); }
+    static __device__ void run(const HP& H, int, const Args& a, dsr_ref s) { fish_choose(H, a, s); }
 };
-struct MFishMove {
+template <class HP>
+struct MFishMoveT {
     typedef WatorInst Args;
-    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s) { fish_move(H, a, s); }
+    static __device__ void run(const HP& H, int, const Args& a, dsr_ref s) { fish_move(H, a, s); }
 };
-struct MSharkStarve {
+template <class HP>
+struct MSharkStarveT {
     typedef WatorInst Args;
-    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s) { shark_starve(H, a, s); }
+    static __device__ void run(const HP& H, int, const Args& a, dsr_ref s) { shark_starve(H, a, s); }
 };
-struct MSharkChoose {
+template <class HP>
+struct MSharkChooseT {
     typedef WatorInst Args;
-    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s) { shark_choose(H, a, s); }
+    static __device__ void run(const HP& H, int, const Args& a, dsr_ref s) { shark_choose(H, a, s); }
 };
 // The last CTA of the last phase advances the step counter.
-struct MSharkMove {
+template <class HP>
+struct MSharkMoveT {
     typedef WatorInst Args;
-    static __device__ void run(const dsr_dev_heap& H, int, const Args& a, dsr_ref s) { shark_move(H, a, s); }
-    static __device__ void finish(const dsr_dev_heap&, int, const Args& a) { *a.step += 1; }
+    static __device__ void run(const HP& H, int, const Args& a, dsr_ref s) { shark_move(H, a, s); }
+    static __device__ void finish(const HP&, int, const Args& a) { *a.step += 1; }
 };
+typedef MFishChooseT<dsr_dev_heap> MFishChoose;
+typedef MFishMoveT<dsr_dev_heap> MFishMove;
+typedef MSharkStarveT<dsr_dev_heap> MSharkStarve;
+typedef MSharkChooseT<dsr_dev_heap> MSharkChoose;
+typedef MSharkMoveT<dsr_dev_heap> MSharkMove;
 
 // ---- batched form: group do-all methods over the heaps of many instances ----
 // Heap index h of a group is the instance slot; table[h] is its view.
@@ -238,7 +257,8 @@ struct GSharkMove {
 };
 
 // One thread per cell: create the initial agents and clear the claim state.
-__global__ void k_wator_init(const __grid_constant__ dsr_dev_heap H, const uint8_t* kind0, WatorInst I) {
+template <class HP>
+__global__ void k_wator_init(const __grid_constant__ HP H, const uint8_t* kind0, WatorInst I) {
     const uint32_t n = (uint32_t)I.p.W * (uint32_t)I.p.H;
     const uint32_t n32 = (n + 31u) & ~31u;  // warp-uniform trip count
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n32; c += gridDim.x * blockDim.x) {
@@ -316,7 +336,7 @@ int launch_init(const dsr_heap* heap, const WatorInst& I, const void* kind0_dev,
     const uint32_t n = (uint32_t)I.p.W * (uint32_t)I.p.H;
     unsigned ctas = (n + 255) / 256;
     if (ctas > (unsigned)heap->sm_count * 8) ctas = (unsigned)heap->sm_count * 8;
-    k_wator_init<<<ctas, 256, 0, s>>>(heap->dev, static_cast<const uint8_t*>(kind0_dev), I);
+    k_wator_init<dsr_dev_heap><<<ctas, 256, 0, s>>>(heap->dev, static_cast<const uint8_t*>(kind0_dev), I);
     return dsr__check_launch("k_wator_init");
 }
 
@@ -474,6 +494,65 @@ int dsr__wator_method(dsr_heap* h, int type, int method, const void* args, size_
         default:
             return DSR_E_INVALID;
     }
+}
+
+// ===========================================================================
+// the same rules on the BitmapAlloc comparator (dsr_bitmap_alloc.cuh)
+// ===========================================================================
+struct dsr_wator_bm {
+    dsr_bm_heap* heap;
+    WatorInst inst;
+};
+
+static bool bm_heap_matches(const dsr_bm_heap* h) {
+    if (h->n_types < 2 || h->n_fields[FISH] != 3 || h->n_fields[SHARK] != 4) return false;
+    for (int f = 0; f < 3; ++f)
+        if (h->field_bytes[FISH][f] != 4) return false;
+    for (int f = 0; f < 4; ++f)
+        if (h->field_bytes[SHARK][f] != 4) return false;
+    return true;
+}
+
+extern "C" int dsr_wator_bm_create(dsr_bm_heap* heap, const dsr_wator_params* p, const void* kind0_dev,
+                                   void* workspace_dev, void* stream, dsr_wator_bm** out) {
+    if (!heap || !params_ok(p) || !kind0_dev || !workspace_dev || !out) return DSR_E_INVALID;
+    if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255) || !bm_heap_matches(heap)) return DSR_E_INVALID;
+    dsr_wator_bm* w = new dsr_wator_bm;
+    w->heap = heap;
+    w->inst = carve(workspace_dev, *p);
+    const uint32_t n = (uint32_t)p->W * (uint32_t)p->H;
+    unsigned ctas = (n + 255) / 256;
+    if (ctas > (unsigned)heap->sm_count * 8) ctas = (unsigned)heap->sm_count * 8;
+    k_wator_init<dsr_bm_dev>
+        <<<ctas, 256, 0, dsr__stream(stream)>>>(heap->dev, static_cast<const uint8_t*>(kind0_dev), w->inst);
+    const int rc = dsr__check_launch("k_wator_init");
+    if (rc) {
+        delete w;
+        return rc;
+    }
+    *out = w;
+    return DSR_OK;
+}
+
+extern "C" int dsr_wator_bm_step(dsr_wator_bm* w, int n_steps, void* stream) {
+    if (!w || n_steps < 0) return DSR_E_INVALID;
+    cudaStream_t s = dsr__stream(stream);
+    dsr_bm_heap* h = w->heap;
+    for (int i = 0; i < n_steps; ++i) {
+        // list reuse for F2 and S2 as in dsr_wator_step
+        int rc = dsr__bm_doall<MFishChooseT<dsr_bm_dev>>(h, FISH, w->inst, s, true, 1);
+        if (!rc) rc = dsr__bm_doall<MFishMoveT<dsr_bm_dev>>(h, FISH, w->inst, s, false);
+        if (!rc) rc = dsr__bm_doall<MSharkStarveT<dsr_bm_dev>>(h, SHARK, w->inst, s);
+        if (!rc) rc = dsr__bm_doall<MSharkChooseT<dsr_bm_dev>>(h, SHARK, w->inst, s, true, 1);
+        if (!rc) rc = dsr__bm_doall<MSharkMoveT<dsr_bm_dev>>(h, SHARK, w->inst, s, false);
+        if (rc) return rc;
+    }
+    return DSR_OK;
+}
+
+extern "C" int dsr_wator_bm_destroy(dsr_wator_bm* w) {
+    delete w;
+    return DSR_OK;
 }
 
 // ===========================================================================

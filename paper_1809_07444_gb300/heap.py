@@ -199,3 +199,48 @@ class Heap:
     def bench_free(self, refs, stream=None):
         L.check(self.lib.dsr_bench_free(self.handle, refs.numel(), C.c_void_p(refs.data_ptr()),
                                         _stream_ptr(stream)), "dsr_bench_free")
+
+
+class BitmapHeap:
+    """A BitmapAlloc comparator heap (dsr_bm_heap_*): per type, an array of
+    capacity[T] objects stored as structs and a flat bitmap of its slots."""
+
+    def __init__(self, types, capacity, stream=None, device="cuda"):
+        self.lib = L.load()
+        self.types = [list(t) for t in types]
+        descs, keep = _descs(self.types)
+        self._keep = (descs, keep)
+        cap = (C.c_uint64 * len(types))(*[int(c) for c in capacity])
+        self._cap = cap
+        n = C.c_size_t(0)
+        L.check(self.lib.dsr_bm_heap_bytes(descs, len(types), cap, C.byref(n)), "dsr_bm_heap_bytes")
+        self.arena = torch.empty(n.value, dtype=torch.uint8, device=device)
+        h = C.c_void_p()
+        L.check(self.lib.dsr_bm_heap_create(descs, len(types), cap, C.c_void_p(self.arena.data_ptr()), n.value,
+                                            _stream_ptr(stream), C.byref(h)), "dsr_bm_heap_create")
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.dsr_bm_heap_destroy(self.handle)
+            self.handle = None
+
+    def stats(self, stream=None):
+        live = (C.c_uint64 * len(self.types))()
+        err = C.c_uint32(0)
+        L.check(self.lib.dsr_bm_heap_stats(self.handle, _stream_ptr(stream), live, C.byref(err)), "dsr_bm_heap_stats")
+        return {"live_objects": [int(x) for x in live], "error_flags": int(err.value)}
+
+    def hash(self, type_id, stream=None):
+        out = torch.zeros(1, dtype=torch.int64, device=self.arena.device)
+        L.check(self.lib.dsr_bm_heap_hash(self.handle, type_id, C.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+                "dsr_bm_heap_hash")
+        return int(out.cpu().numpy().view(np.uint64)[0])
+
+    def counters(self, stream=None):
+        out = (C.c_uint64 * L.CTR_COUNT)()
+        L.check(self.lib.dsr_bm_heap_counters(self.handle, _stream_ptr(stream), out), "dsr_bm_heap_counters")
+        d = {"visits": int(out[0]), "allocs": int(out[1]), "frees": int(out[2]), "new_blocks": int(out[3])}
+        for k in range(4, L.CTR_COUNT):
+            d["app%d" % (k - 4)] = int(out[k])
+        return d

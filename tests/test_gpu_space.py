@@ -25,7 +25,17 @@ def test_smaller_blocks_hold_at_least_as_large_a_problem():
     assert s32 >= s64 * 0.95  # 32-slot blocks waste no more space at the ends of runs
 
 
-def test_experiment_reports_every_tuning():
+def test_experiment_reports_every_setting():
     out = space.experiment(heap_bytes=1 << 20, steps=10)
-    assert [r["tuning"] for r in out["rows"]] == ["default", {"cap_min": 32}, {"fanout": 16}]
-    assert all(r["max_side"] > 0 and 0 < r["efficiency"] <= 1 for r in out["rows"])
+    rows = out["rows"]
+    assert [r["tuning"] for r in rows[:3]] == ["default", {"cap_min": 32}, {"fanout": 16}]
+    assert [r["allocator"] for r in rows] == ["dsr"] * 3 + ["BitmapAlloc"] * 2
+    assert all(r["max_side"] > 0 and 0 < r["efficiency"] <= 1 for r in rows)
+
+
+def test_bitmap_capacities_fill_the_heap():
+    heap = 8 << 20
+    cf, cs = space.bitmap_capacities(heap, 0.8)
+    assert cf % 64 == 0 and cs % 64 == 0
+    used = cf * 12 + cs * 16
+    assert 0.97 * heap < used <= heap
