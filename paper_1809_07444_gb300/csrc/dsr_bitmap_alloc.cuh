@@ -40,8 +40,10 @@ __device__ __forceinline__ F* dsr_field(const dsr_bm_dev& H, int T, dsr_ref r, i
 
 /* new T: lanes asking for the same type of the same heap are served by one
  * leader, which probes bitmap words linearly from a hashed start and takes
- * free bits of a word with one atomicOr. DSR_NULL (and DSR_ERR_OOM) after a
- * full sweep of the type's bitmap without a free bit. */
+ * free bits of a word with atomicOr. When another leader took the bits it
+ * chose, it retries the same word with the value the atomic returned
+ * (bounded); it moves on only from a word it saw full. DSR_NULL (and
+ * DSR_ERR_OOM) once a sweep has seen every word of the type full in a row. */
 __device__ inline dsr_ref dsr_new(const dsr_bm_dev& H, int T) {
     const unsigned act = __activemask();
     const unsigned peers = __match_any_sync(act, (dsr_u64)reinterpret_cast<uintptr_t>(H.used[0]) | (dsr_u64)T);
@@ -58,23 +60,26 @@ __device__ inline dsr_ref dsr_new(const dsr_bm_dev& H, int T) {
         dsr_u64 base = 0, bits = 0;
         uint32_t st = 0;
         if ((int)lane == leader) {
-            for (dsr_u64 a = 0;; ++a) {
-                if (a > nw) {
-                    st = DSR_ERR_OOM;
+            dsr_u64 full_run = 0;  // consecutive words seen full
+            for (unsigned a = 0;; ++a) {
+                if (full_run > nw || a >= DSR_ALLOC_CAP) {
+                    st = full_run > nw ? DSR_ERR_OOM : DSR_ERR_RETRY;
                     atomicOr(H.err, st);
                     break;
                 }
                 dsr_u64* w = H.used[T] + word;
-                const dsr_u64 snap = dsr_ld_relaxed(w);
-                if (snap != ~0ull) {
+                dsr_u64 snap = dsr_ld_relaxed(w);
+                for (int r = 0; r < 64 && snap != ~0ull && !bits; ++r) {
                     const dsr_u64 want = dsr_lowest_bits(~snap, need - served);
                     const dsr_u64 prev = atomicOr(w, want);
                     bits = want & ~prev;
-                    if (bits) {
-                        base = word << 6;
-                        break;
-                    }
+                    snap = prev | want;
                 }
+                if (bits) {
+                    base = word << 6;
+                    break;
+                }
+                full_run = snap == ~0ull ? full_run + 1 : 0;
                 word = word + 1 == nw ? 0 : word + 1;
             }
             if (!st) dsr_count(H.ctr, DSR_CTR_ALLOCS, (dsr_u64)__popcll(bits));
