@@ -15,6 +15,7 @@ Host code here only schedules (admission, retirement, bookkeeping); every
 step runs in libdsr.so.
 """
 import collections
+import concurrent.futures as cf
 import time
 
 import numpy as np
@@ -33,16 +34,24 @@ class Server:
         self.gb = GolBatch(int(arena_bytes * gol_fraction) // 1024 * 1024, max_instances=max_jobs, tuning=tuning)
         self.stream = torch.cuda.current_stream()
 
-    def _admit(self, job):
+    @staticmethod
+    def _initial(job):
         side, seed = int(job["side"]), int(job["seed"])
         if job["app"] == WATOR:
-            return self.wb.add(side, side, WL.wator_initial(side, side, seed), seed)
-        return self.gb.add(side, side, WL.gol_initial(side, side, seed))
+            return WL.wator_initial(side, side, seed)
+        return WL.gol_initial(side, side, seed)
+
+    def _admit(self, job, start):
+        side, seed = int(job["side"]), int(job["seed"])
+        if job["app"] == WATOR:
+            return self.wb.add(side, side, start, seed)
+        return self.gb.add(side, side, start)
 
     def _batch(self, app):
         return self.wb if app == WATOR else self.gb
 
-    def run(self, jobs, time_limit=None, realtime=True, max_admit_per_tick=64, keep_hashes=True):
+    def run(self, jobs, time_limit=None, realtime=True, max_admit_per_tick=64, keep_hashes=True, prefetch=64,
+            workers=8):
         """Serve `jobs` (a list of dicts with id, arrival, app, side, steps, seed).
 
         Returns a report: per completed job its arrival, admission, completion
@@ -50,10 +59,24 @@ class Server:
         device time; the objects visited; and jobs left unfinished when
         `time_limit` (seconds of wall time) ran out. With realtime=False,
         arrivals are not waited for (every job counts as arrived at start).
+
+        Initial states are generated on the host by a pool of `workers`
+        threads, up to `prefetch` jobs ahead in arrival order, while the
+        device runs ticks; a waiting job is admitted once its state is ready.
         """
         order = sorted(jobs, key=lambda j: j["arrival"])
         pending = collections.deque(order)
         waiting = collections.deque()
+        pool = cf.ThreadPoolExecutor(max_workers=workers)
+        starts = {}  # job id -> future of its initial state
+        ahead = 0  # jobs of `order` submitted to the pool
+
+        def top_up():
+            nonlocal ahead
+            while ahead < len(order) and len(starts) < prefetch:
+                j = order[ahead]
+                starts[j["id"]] = pool.submit(self._initial, j)
+                ahead += 1
         resident = {}  # (app, slot) -> [job, steps_left, admitted_at]
         done = []
         ticks = []  # (start event, end event, resident count)
@@ -67,17 +90,24 @@ class Server:
             t = now()
             if time_limit is not None and t > time_limit:
                 break
+            top_up()
             while pending and (not realtime or pending[0]["arrival"] <= t):
                 waiting.append(pending.popleft())
-            # admission: first fit in arrival order, bounded per tick
+            # admission: first fit in arrival order among jobs whose initial
+            # state is ready, bounded per tick
             admitted = 0
             kept = collections.deque()
             while waiting and admitted < max_admit_per_tick:
                 job = waiting.popleft()
-                slot = self._admit(job)
+                fut = starts.get(job["id"])
+                if fut is None or not fut.done():
+                    kept.append(job)
+                    continue
+                slot = self._admit(job, fut.result())
                 if slot is None:
                     kept.append(job)
                     continue
+                del starts[job["id"]]
                 resident[(job["app"], slot)] = [job, int(job["steps"]), now()]
                 admitted += 1
             kept.extend(waiting)
@@ -85,6 +115,8 @@ class Server:
             if not resident:
                 if pending and realtime:
                     time.sleep(max(0.0, min(pending[0]["arrival"] - now(), 0.05)))
+                elif waiting:
+                    time.sleep(0.001)  # initial states still being generated
                 continue
             # one tick: a batched step of each application that has jobs
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -114,6 +146,7 @@ class Server:
                     done.append({"id": job["id"], "app": app, "side": int(job["side"]), "steps": int(job["steps"]),
                                  "seed": int(job["seed"]), "arrival": float(job["arrival"]), "admitted": t_adm,
                                  "completed": t_done, "hash": h})
+        pool.shutdown(wait=False, cancel_futures=True)
         torch.cuda.synchronize()
         wall = now()
         step_ms = [x.elapsed_time(y) for x, y, _ in ticks]
