@@ -246,7 +246,7 @@ def run_gpu(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     lib = L.load()
-    seed = SEED + rank
+    seed = replica_seed(rank)
     k0 = WL.wator_initial(W_SIDE, W_SIDE, seed)
     sim = Wator(W_SIDE, W_SIDE, k0, seed)
     stream = torch.cuda.current_stream()
@@ -398,14 +398,41 @@ def bench_alloc_free(n=1 << 24, n_types=2, reps=2, churn=False):
     return out
 
 
+def bench_atomics(n_words=1 << 24, iters=64):
+    """L2 atomic ceiling (no vendor figure): one thread per 64-bit word,
+    alternating atomicOr / atomicAnd of one bit on its own word, as
+    reductions (results unused) and as dependent atomics (results used)."""
+    import torch
+    from paper_1809_07444_gb300 import _lib as L
+    from paper_1809_07444_gb300.heap import _stream_ptr
+
+    lib = L.load()
+    words = torch.zeros(n_words, dtype=torch.int64, device="cuda")
+    out = {"words": n_words, "atomics_per_thread": iters}
+    for name, ret in (("reductions_per_s", 0), ("dependent_atomics_per_s", 1)):
+        ts = []
+        for r in range(4):
+            a, b = _ev()
+            a.record()
+            L.check(lib.dsr_bench_atomics(C.c_void_p(words.data_ptr()), n_words, iters, ret, _stream_ptr()),
+                    "dsr_bench_atomics")
+            b.record()
+            b.synchronize()
+            if r:
+                ts.append(a.elapsed_time(b) * 1e-3)
+        out[name] = n_words * iters / statistics.median(ts)
+    del words
+    return out
+
+
 def bench_alloc_sweep():
     """M1: 2^24 objects with 1..4 types, 2^26 and 2^28 with 2 types, and the
-    50% churn mix at 2^26."""
+    50% churn mix at 2^26; beside them the L2 atomic ceiling."""
     rows = [bench_alloc_free(1 << 24, t) for t in (1, 2, 3, 4)]
     rows.append(bench_alloc_free(1 << 26, 2, churn=True))
     rows.append(bench_alloc_free(1 << 28, 2, reps=1))
     return {"rows": rows, "l2": "flushed before each kernel",
-            "types": "first n of 4 types with capacities 64, 42, 32, 16"}
+            "types": "first n of 4 types with capacities 64, 42, 32, 16", "l2_atomic_ceiling": bench_atomics()}
 
 
 def bench_streaming_doall(n=1 << 28, fields=4, reps=5):
@@ -697,6 +724,26 @@ def roofline(phases, peak, peak_kind):
             "peak_source": ("measured hbm_gbs" if peak_kind == "measured" else "fallback 6.8 TB/s")}
 
 
+def combine_ranks(times, counts, world, device):
+    """Whole-job figures over the ranks of a replica run: the slowest rank's
+    times (max) and the summed counts. One process per GPU, no exchange
+    inside the timed region: this runs after it."""
+    if world <= 1:
+        return list(times), list(counts)
+    import torch
+
+    t = torch.tensor(times, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    n = torch.tensor(counts, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(n, op=torch.distributed.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()], [int(x) for x in n.tolist()]
+
+
+def replica_seed(rank):
+    """Each rank runs its own wa-tor replica from seed SEED + rank."""
+    return SEED + rank
+
+
 def main():
     args = _args()
     rank = int(os.environ.get("RANK", 0))
@@ -722,16 +769,8 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl")
     r = run_gpu(args, rank, world)
-    dev_s, visits, allocfree, e2e_s = r["dev_s"], r["visits"], r["allocfree"], r["e2e_s"]
-    if world > 1:
-        t = torch.tensor([dev_s, e2e_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        n = torch.tensor([visits, allocfree, r["e2e_visits"]], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(n, op=torch.distributed.ReduceOp.SUM)
-        dev_s, e2e_s = float(t[0]), float(t[1])
-        visits, allocfree, e2e_visits = int(n[0]), int(n[1]), int(n[2])
-    else:
-        e2e_visits = r["e2e_visits"]
+    (dev_s, e2e_s), (visits, allocfree, e2e_visits) = combine_ranks(
+        [r["dev_s"], r["e2e_s"]], [r["visits"], r["allocfree"], r["e2e_visits"]], world, "cuda")
     if rank != 0:
         torch.distributed.destroy_process_group()
         return 0

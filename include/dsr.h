@@ -308,6 +308,13 @@ int dsr_bench_churn(dsr_heap* heap, uint64_t n_threads, int n_types_used, uint64
  * and writes one float to out_dev[thread]; the grid is `ctas` x 256 threads.
  * FLOPs = ctas * 256 * 8 * iters * 2. */
 int dsr_bench_fma(float* out_dev, int ctas, int iters, void* stream);
+/* dsr_bench_atomics: an L2 atomic throughput probe, the ceiling of the
+ * allocator's bitmap traffic. One thread per 64-bit word of words_dev
+ * (n_words, device), each doing `iters` atomics on its own word: alternating
+ * atomicOr and atomicAnd of one bit; with_return = 0 discards the results
+ * (reductions), 1 uses them (each waits for the previous). Atomics =
+ * n_words * iters. */
+int dsr_bench_atomics(void* words_dev, uint64_t n_words, int iters, int with_return, void* stream);
 
 #ifdef __cplusplus
 }

@@ -561,8 +561,14 @@ __device__ inline void dsr_delete(const dsr_dev_heap& H, dsr_ref r) {
         atomicOr(H.err, DSR_ERR_BAD_HANDLE);
         return;
     }
-    dsr_count(H.ctr, DSR_CTR_FREES, (dsr_u64)(__popc(lo) + __popc(hi)));
-    dsr_release(H, T, bid, ((dsr_u64)hi << 32) | lo);
+    dsr_u64 bits = ((dsr_u64)hi << 32) | lo;
+    if (bits & ~H.valid[T]) {  // a slot at or beyond the block's capacity
+        atomicOr(H.err, DSR_ERR_BAD_HANDLE);
+        bits &= H.valid[T];
+        if (!bits) return;
+    }
+    dsr_count(H.ctr, DSR_CTR_FREES, (dsr_u64)__popcll(bits));
+    dsr_release(H, T, bid, bits);
 }
 
 /* Address of field f of the object r (type T): block base + the field's SOA
@@ -625,8 +631,8 @@ __device__ __forceinline__ void dsr_call_finish(const dsr_dev_heap&, int, const 
  * over the same live set (one whose predecessor created and deleted no
  * object of T) that then skips its scan. */
 template <class Method>
-__global__ void dsr_doall_kernel(const __grid_constant__ dsr_dev_heap H, int T,
-                                 const __grid_constant__ typename Method::Args args, int keep_list = 0) {
+__device__ __forceinline__ void dsr_doall_body(const dsr_dev_heap& H, int T, const typename Method::Args& args,
+                                               int keep_list) {
     const unsigned sh = dsr_span_shift(H, T);
     const dsr_u64 total = (dsr_u64)(*(volatile uint32_t*)H.R_count) << sh;
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
@@ -643,6 +649,21 @@ __global__ void dsr_doall_kernel(const __grid_constant__ dsr_dev_heap H, int T,
             Method::run(H, T, args, ((dsr_u64)H.R_bid[i] << 6) | s);
     }
     if (dsr_doall_finish(H, keep_list != 0)) dsr_call_finish<Method>(H, T, args, 0);
+}
+template <class Method>
+__global__ void dsr_doall_kernel(const __grid_constant__ dsr_dev_heap H, int T,
+                                 const __grid_constant__ typename Method::Args args, int keep_list = 0) {
+    dsr_doall_body<Method>(H, T, args, keep_list);
+}
+/* The same kernel for CTAs of at most 256 threads, compiled for at least six
+ * such CTAs per SM (at most 40 registers a thread). The methods are chains
+ * of dependent loads and atomics: more resident warps hide more of their
+ * latency. */
+template <class Method>
+__global__ void __launch_bounds__(256, 6) dsr_doall_kernel_256(const __grid_constant__ dsr_dev_heap H, int T,
+                                                              const __grid_constant__ typename Method::Args args,
+                                                              int keep_list = 0) {
+    dsr_doall_body<Method>(H, T, args, keep_list);
 }
 
 /* Vector method kernel: a method may also provide
@@ -720,8 +741,8 @@ template <class M>
 __device__ __forceinline__ void dsr_call_finish_group(const dsr_group_dev&, int, const typename M::Args&, long) {}
 
 template <class Method>
-__global__ void dsr_group_doall_kernel(const __grid_constant__ dsr_group_dev G, int T, unsigned sh,
-                                       const __grid_constant__ typename Method::Args args, int keep_list = 0) {
+__device__ __forceinline__ void dsr_group_doall_body(const dsr_group_dev& G, int T, unsigned sh,
+                                                     const typename Method::Args& args, int keep_list) {
     __shared__ bool last;
     const dsr_u64 total = (dsr_u64)(*(volatile uint32_t*)G.R_count) << sh;
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
@@ -748,6 +769,18 @@ __global__ void dsr_group_doall_kernel(const __grid_constant__ dsr_group_dev G, 
     }
     __syncthreads();
     if (last) dsr_call_finish_group<Method>(G, T, args, 0);
+}
+template <class Method>
+__global__ void dsr_group_doall_kernel(const __grid_constant__ dsr_group_dev G, int T, unsigned sh,
+                                       const __grid_constant__ typename Method::Args args, int keep_list = 0) {
+    dsr_group_doall_body<Method>(G, T, sh, args, keep_list);
+}
+/* At most 256 threads a CTA, at least six CTAs per SM, as dsr_doall_kernel_256. */
+template <class Method>
+__global__ void __launch_bounds__(256, 6)
+    dsr_group_doall_kernel_256(const __grid_constant__ dsr_group_dev G, int T, unsigned sh,
+                               const __grid_constant__ typename Method::Args args, int keep_list = 0) {
+    dsr_group_doall_body<Method>(G, T, sh, args, keep_list);
 }
 
 #endif /* __CUDACC__ */

@@ -103,6 +103,7 @@ SIGNATURES = {
     "dsr_bench_free": (_i, [_vp, _u64, _vp, _vp]),
     "dsr_bench_churn": (_i, [_vp, _u64, _i, _u64, _vp, _vp, _vp]),
     "dsr_bench_fma": (_i, [_vp, _i, _i, _vp]),
+    "dsr_bench_atomics": (_i, [_vp, _u64, _i, _i, _vp]),
     "dsr_gol_types": (_i, [C.POINTER(TypeDesc)]),
     "dsr_gol_workspace_bytes": (_i, [_i, _i, C.POINTER(_sz)]),
     "dsr_gol_create": (_i, [_vp, _i, _i, _vp, _vp, _vp, C.POINTER(_vp)]),

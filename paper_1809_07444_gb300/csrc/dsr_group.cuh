@@ -52,8 +52,14 @@ int dsr__group_doall(dsr_group* g, int type, const typename M::Args& args, cudaS
     if (type < 0 || type >= g->n_types) return DSR_E_INVALID;
     if (with_scan) dsr__group_launch_scan(g, type, s, 1u + (unsigned)reuse);
     const int threads = g->tune.threads > 0 ? g->tune.threads : 256;
-    const int grid = dsr__group_grid(g, (const void*)dsr_group_doall_kernel<M>, threads);
-    dsr_group_doall_kernel<M><<<grid, threads, 0, s>>>(g->dev, type, dsr__group_span(g, type), args,
-                                                       reuse > 0 ? 1 : 0);
+    if (threads <= 256) {
+        const int grid = dsr__group_grid(g, (const void*)dsr_group_doall_kernel_256<M>, threads);
+        dsr_group_doall_kernel_256<M><<<grid, threads, 0, s>>>(g->dev, type, dsr__group_span(g, type), args,
+                                                               reuse > 0 ? 1 : 0);
+    } else {
+        const int grid = dsr__group_grid(g, (const void*)dsr_group_doall_kernel<M>, threads);
+        dsr_group_doall_kernel<M><<<grid, threads, 0, s>>>(g->dev, type, dsr__group_span(g, type), args,
+                                                           reuse > 0 ? 1 : 0);
+    }
     return dsr__check_launch("dsr_group_doall_kernel");
 }

@@ -829,6 +829,35 @@ extern "C" int dsr_bench_churn(dsr_heap* h, uint64_t n, int n_types_used, uint64
     return dsr__check_launch("k_bench_churn");
 }
 
+// One word per thread: reductions (results unused) or dependent atomics.
+__global__ void k_bench_atomics(dsr_u64* words, dsr_u64 n, int iters, int with_return) {
+    const dsr_u64 i = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    dsr_u64* w = words + i;
+    const dsr_u64 bit = 1ull << (i & 63);
+    if (with_return) {
+        dsr_u64 acc = 0;
+        for (int k = 0; k < iters; ++k) acc += (k & 1) ? atomicAnd(w, ~(bit ^ (acc & 1))) : atomicOr(w, bit | (acc & 2));
+        if (acc == 0x5DEECE66Dull) *w = acc;  // keeps the results live
+    } else {
+        for (int k = 0; k < iters; ++k) {
+            if (k & 1)
+                atomicAnd(w, ~bit);
+            else
+                atomicOr(w, bit);
+        }
+    }
+}
+
+extern "C" int dsr_bench_atomics(void* words_dev, uint64_t n_words, int iters, int with_return, void* stream) {
+    if (!words_dev || n_words == 0 || iters < 1) return DSR_E_INVALID;
+    const dsr_u64 ctas = (n_words + 255) / 256;
+    if (ctas > 0x7FFFFFFFull) return DSR_E_INVALID;
+    k_bench_atomics<<<(unsigned)ctas, 256, 0, dsr__stream(stream)>>>(static_cast<dsr_u64*>(words_dev), n_words, iters,
+                                                                     with_return);
+    return dsr__check_launch("k_bench_atomics");
+}
+
 extern "C" int dsr_bench_fma(float* out_dev, int ctas, int iters, void* stream) {
     if (!out_dev || ctas < 1 || iters < 1) return DSR_E_INVALID;
     k_bench_fma<<<ctas, 256, 0, dsr__stream(stream)>>>(out_dev, iters);

@@ -59,8 +59,10 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
     if (ev_scan) cudaEventRecord(ev_scan, s);
     static int grid_cache[17] = {0};
     const int threads = h->tune.threads;
+    const bool small = threads <= 256;  // the occupancy-bounded kernel
+    const void* kfn = small ? (const void*)dsr_doall_kernel_256<M> : (const void*)dsr_doall_kernel<M>;
     int& grid = grid_cache[threads / 64];
-    if (grid == 0 || h->tune.ctas_per_sm > 0) grid = dsr__persistent_grid(h, (const void*)dsr_doall_kernel<M>, threads);
+    if (grid == 0 || h->tune.ctas_per_sm > 0) grid = dsr__persistent_grid(h, kfn, threads);
     // Persistent grid: the CTAs that fit on the GPU at once, capped by the
     // work a do-all over this heap can list. (Every CTA ends with one atomic
     // on the completion counter, so a much larger grid costs more in those
@@ -84,7 +86,10 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
             return rc;
         }
     }
-    dsr_doall_kernel<M><<<g, threads, 0, s>>>(h->dev, type, args, reuse > 0 ? 1 : 0);
+    if (small)
+        dsr_doall_kernel_256<M><<<g, threads, 0, s>>>(h->dev, type, args, reuse > 0 ? 1 : 0);
+    else
+        dsr_doall_kernel<M><<<g, threads, 0, s>>>(h->dev, type, args, reuse > 0 ? 1 : 0);
     rc = dsr__check_launch("dsr_doall_kernel");
     if (ev_run) cudaEventRecord(ev_run, s);
     return rc;

@@ -252,3 +252,31 @@ def test_fma_probe_runs():
     L.check(L.load().dsr_bench_fma(C.c_void_p(out.data_ptr()), 4, 1000, None), "dsr_bench_fma")
     torch.cuda.synchronize()
     assert torch.isfinite(out).all()
+
+
+def test_atomic_probe_leaves_each_word_as_its_last_atomic_set_it():
+    words = torch.zeros(1000, dtype=torch.int64, device="cuda")
+    lib = L.load()
+    L.check(lib.dsr_bench_atomics(C.c_void_p(words.data_ptr()), 1000, 5, 0, None), "dsr_bench_atomics")
+    torch.cuda.synchronize()
+    # 5 atomics: or, and, or, and, or -> each thread's own bit set
+    want = np.array([1 << (i % 64) for i in range(1000)], dtype=np.uint64)
+    assert np.array_equal(words.cpu().numpy().view(np.uint64), want)
+    L.check(lib.dsr_bench_atomics(C.c_void_p(words.data_ptr()), 1000, 8, 1, None), "dsr_bench_atomics")
+    torch.cuda.synchronize()
+
+
+def test_delete_of_a_slot_beyond_capacity_is_rejected():
+    # type 1 has capacity 42: a handle with slot 50 is not a slot of it
+    h = _heap(100, types=[[4, 4], [4, 4, 4]])
+    refs = torch.empty(64, dtype=torch.int64, device="cuda")
+    h.bench_alloc(refs, 2, 1)
+    assert h.stats()["capacity"][1] == 42
+    f1, hd1 = h.dump(1)
+    bid = int(hd1[0]) >> 6
+    bad = torch.tensor([np.int64((bid << 6) | 50), np.int64(-1)], dtype=torch.int64, device="cuda")
+    h.bench_free(bad)
+    st = h.stats()
+    assert st["error_flags"] & L.ERR_BAD_HANDLE
+    check_invariants(h)  # nothing else changed
+    assert h.count(1) == len(f1)
