@@ -101,6 +101,16 @@ int dsr_wator_workspace_bytes(int W, int H, size_t* out);
 int dsr_wator_create(dsr_heap* heap, const dsr_wator_params* p, const void* kind0_dev, void* workspace_dev,
                      void* stream, dsr_wator** out);
 int dsr_wator_step(dsr_wator* w, int n_steps, void* stream);
+/* A handle over a heap and workspace that already hold a wa-tor state, with
+ * no initialisation: resuming from a checkpoint. A checkpoint of a wa-tor
+ * run is the bytes of its heap arena and of its workspace (no pointer is
+ * stored inside either; handles are block and slot numbers, the random draws
+ * are keyed on the step counter in the workspace). Restore by creating a
+ * heap of the same types, size and tuning over a new arena (the same layout
+ * follows), copying the saved arena bytes over it after the creation's reset
+ * has run, copying the workspace bytes, and attaching. No counterpart in the
+ * paper. */
+int dsr_wator_attach(dsr_heap* heap, const dsr_wator_params* p, void* workspace_dev, dsr_wator** out);
 /* Device uint8[W*H] occupancy snapshot (0/1/2) of the current state. */
 int dsr_wator_kinds(dsr_wator* w, void* kind_out_dev, void* stream);
 int dsr_wator_destroy(dsr_wator* w);

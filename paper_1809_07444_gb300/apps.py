@@ -96,6 +96,30 @@ class Wator:
             self.lib.dsr_wator_destroy(self.handle)
             self.handle = None
 
+    def checkpoint(self):
+        """Host copies of the heap arena and the workspace, with what a
+        restore needs (see dsr_wator_attach)."""
+        torch.cuda.synchronize()
+        return {"W": self.W, "H": self.H, "params": bytes(self.params), "tuning": self.heap.tuning,
+                "arena": self.heap.arena.cpu(), "workspace": self.workspace.cpu()}
+
+    @classmethod
+    def restore(cls, ck, stream=None):
+        """A Wator that continues from a checkpoint, bit for bit."""
+        w = cls.__new__(cls)
+        w.lib = L.load()
+        w.W, w.H = ck["W"], ck["H"]
+        w.heap = Heap(WATOR_TYPES, ck["arena"].numel(), names=["Fish", "Shark"], tuning=ck["tuning"], stream=stream)
+        torch.cuda.synchronize()  # the creation's reset has run
+        w.heap.arena.copy_(ck["arena"])
+        w.workspace = ck["workspace"].cuda()
+        w.params = L.WatorParams.from_buffer_copy(ck["params"])
+        h = C.c_void_p()
+        L.check(w.lib.dsr_wator_attach(w.heap.handle, C.byref(w.params), C.c_void_p(w.workspace.data_ptr()),
+                                       C.byref(h)), "dsr_wator_attach")
+        w.handle = h
+        return w
+
     def step(self, n=1, stream=None):
         L.check(self.lib.dsr_wator_step(self.handle, n, _stream_ptr(stream)), "dsr_wator_step")
 

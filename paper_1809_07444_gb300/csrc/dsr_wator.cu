@@ -396,6 +396,16 @@ extern "C" int dsr_wator_create(dsr_heap* heap, const dsr_wator_params* p, const
     return DSR_OK;
 }
 
+extern "C" int dsr_wator_attach(dsr_heap* heap, const dsr_wator_params* p, void* workspace_dev, dsr_wator** out) {
+    if (!heap || !params_ok(p) || !workspace_dev || !out) return DSR_E_INVALID;
+    if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255) || !heap_matches(heap)) return DSR_E_INVALID;
+    dsr_wator* w = new dsr_wator;
+    w->heap = heap;
+    w->inst = carve(workspace_dev, *p);
+    *out = w;
+    return DSR_OK;
+}
+
 extern "C" int dsr_wator_step(dsr_wator* w, int n_steps, void* stream) {
     if (!w || n_steps < 0) return DSR_E_INVALID;
     cudaStream_t s = dsr__stream(stream);

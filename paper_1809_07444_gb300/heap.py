@@ -54,6 +54,7 @@ class Heap:
         self.lib = L.load()
         self.types = [list(t) for t in types]
         self.names = names
+        self.tuning = tuning
         self.arena = torch.empty(int(heap_bytes), dtype=torch.uint8, device=device)
         descs, keep = _descs(self.types, names)
         self._keep = (descs, keep)

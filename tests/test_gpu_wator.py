@@ -78,3 +78,21 @@ def test_wator_2048_full_size_hash_parity():
     # for the first 40 steps, full multisets at the end
     W = H = 2048
     _run_pair(W, H, WL.wator_initial(W, H, 1), 1, 40, full_every=20)
+
+
+def test_wator_checkpoint_and_resume_bit_exact():
+    W, H = 200, 150
+    k0 = WL.wator_initial(W, H, 8)
+    a, ref = Wator(W, H, k0, 8, tuning={"fanout": 32}), O.Wator(W, H, k0, seed=8)
+    a.step(25)
+    ref.step(25)
+    ck = a.checkpoint()
+    a.step(25)
+    b = Wator.restore(ck)
+    b.step(25)
+    ref.step(25)
+    assert a.hash() == b.hash() == ref.hash()
+    fa, sa = a.dump()
+    fb, sb = b.dump()
+    assert np.array_equal(fa, fb) and np.array_equal(sa, sb)
+    check_invariants(b.heap, list(ref.counts()))
