@@ -101,6 +101,60 @@ def oracle_wator_rate(seconds, steps=None, warmup=0):
     return updates / el, n, el
 
 
+def _oracle_instance_rate(args):
+    """One batched-workload instance on the oracle (runs in a spawned
+    worker): (object-updates, seconds) of `steps` steps after `warmup`."""
+    side, seed, warmup, steps = args
+    import oracle as Ow
+    from paper_1809_07444_gb300 import workloads as WLw
+    w = Ow.Wator(side, side, WLw.wator_initial(side, side, seed), seed=seed)
+    w.step(warmup)
+    upd, t0 = 0, time.perf_counter()
+    for _ in range(steps):
+        nf, ns = w.counts()
+        ev = w.step(1)[0]
+        upd += 2 * nf + ns + 2 * (ns - int(ev[3]))
+    return upd, time.perf_counter() - t0
+
+
+def oracle_config_rates():
+    """The oracle on the other configurations, each a bounded sample: game
+    of life 64x64 (100 generations, one core), n-body 65,536 bodies in FP64
+    (one step, rows split over all cores), and the batched workload (every
+    fourth of the 256 instances, 3 steps each after 3 warm-up steps, one
+    spawned process per core)."""
+    import multiprocessing
+    import oracle as O
+    from paper_1809_07444_gb300 import workloads as WL
+
+    cores = os.cpu_count() or 1
+    out = {}
+    g = O.Gol(64, 64, WL.gol_initial(64, 64, 1))
+    t0 = time.perf_counter()
+    g.step(100)
+    out["gol_64"] = {"gens_per_s": 100 / (time.perf_counter() - t0), "cores": 1, "sample": "100 generations"}
+    rows, _ = WL.nbody_initial(65536, 1)
+    O.set_threads(cores)
+    nb = O.NBody(rows)
+    t0 = time.perf_counter()
+    nb.step(1)
+    dt = time.perf_counter() - t0
+    O.set_threads(1)
+    out["nbody_65536"] = {"s_per_step": dt, "flops": 28.0 * 65536 * 65536 / dt, "cores": cores,
+                          "sample": "the first step, FP64", "flop_per_pair": 28}
+    sides = [int(s) for s in WL.batched_sides(256, 1)]
+    jobs = [(sides[i], 1000 + i, 3, 3) for i in range(0, 256, 4)]
+    t0 = time.perf_counter()
+    with multiprocessing.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_instance_rate, jobs)
+    wall = time.perf_counter() - t0
+    upd = sum(u for u, _ in res)
+    out["batched"] = {"object_updates_per_s_all_cores": upd / wall,
+                      "object_updates_per_s_per_core": upd / sum(t for _, t in res), "cores": cores,
+                      "sample": "every fourth of the 256 instances, steps 4-6, one process per core"}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -791,6 +845,8 @@ def main():
         rate, n, el = oracle_wator_rate(args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "first %d steps of the same wa-tor 2048x2048 run (%.1f s)" % (n, el)}
+        if world == 1 and not args.no_extra:
+            line["cpu_baseline"]["configs"] = oracle_config_rates()
     if world == 1 and not args.no_extra:
         # the other halves of the metric: batched vs plain, alloc+free/s, the
         # streaming do-all against the HBM roofline, and the served form

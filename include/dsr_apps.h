@@ -75,9 +75,12 @@ int dsr_gol_batch_destroy(dsr_gol_batch* b);
  *   S2 (Shark): winners move; a fish in the target is deleted and energy +=
  *               shark_gain; timer >= shark_breed: leave a new Shark (timer 0,
  *               energy shark_energy0) behind and reset timer.
- * Workspace: uint64 grid (0 empty, else (handle << 2) | kind), uint64 claim
- * and uint32 intent per cell, plus the step counter. Each successful move (F2
- * and S2 winners) adds one to the heap's DSR_CTR_APP0 event counter. */
+ * Workspace (dsr_wator_workspace_bytes, which depends on the heap): uint64
+ * grid (0 empty, else (handle << 2) | kind) and uint64 claim per cell, the
+ * step counter, and a uint32 intent per object slot of the heap (the target
+ * an agent chose in F1 / S1, read back in F2 / S2 with the agent's fields).
+ * Each successful move (F2 and S2 winners) adds one to the heap's
+ * DSR_CTR_APP0 event counter. */
 enum {
     DSR_METHOD_WATOR_F1 = 200,
     DSR_METHOD_WATOR_F2 = 201,
@@ -95,7 +98,8 @@ typedef struct {
 } dsr_wator_params;
 typedef struct dsr_wator dsr_wator;
 int dsr_wator_types(dsr_type_desc* out /* 2 entries */);
-int dsr_wator_workspace_bytes(int W, int H, size_t* out);
+/* Workspace bytes for a W x H torus whose agents live in `heap`. */
+int dsr_wator_workspace_bytes(const dsr_heap* heap, int W, int H, size_t* out);
 /* kind0_dev: device uint8[W*H]: 0 empty, 1 fish, 2 shark. Initial fish have
  * timer 0; sharks timer 0 and energy shark_energy0. */
 int dsr_wator_create(dsr_heap* heap, const dsr_wator_params* p, const void* kind0_dev, void* workspace_dev,
@@ -131,6 +135,7 @@ int dsr_wator_phase_times(dsr_wator* w, double* out_ms /* 10 */, int* steps);
  * rules and workspace as dsr_wator_*, with Fish and Shark objects in the
  * comparator's per-type arrays (types 0 and 1 as dsr_wator_types gives). */
 typedef struct dsr_wator_bm dsr_wator_bm;
+int dsr_wator_bm_workspace_bytes(const dsr_bm_heap* heap, int W, int H, size_t* out);
 int dsr_wator_bm_create(dsr_bm_heap* heap, const dsr_wator_params* p, const void* kind0_dev, void* workspace_dev,
                         void* stream, dsr_wator_bm** out);
 int dsr_wator_bm_step(dsr_wator_bm* w, int n_steps, void* stream);

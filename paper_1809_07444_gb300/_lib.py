@@ -110,7 +110,7 @@ SIGNATURES = {
     "dsr_gol_step": (_i, [_vp, _i, _vp]),
     "dsr_gol_destroy": (_i, [_vp]),
     "dsr_wator_types": (_i, [C.POINTER(TypeDesc)]),
-    "dsr_wator_workspace_bytes": (_i, [_i, _i, C.POINTER(_sz)]),
+    "dsr_wator_workspace_bytes": (_i, [_vp, _i, _i, C.POINTER(_sz)]),
     "dsr_wator_create": (_i, [_vp, C.POINTER(WatorParams), _vp, _vp, _vp, C.POINTER(_vp)]),
     "dsr_wator_step": (_i, [_vp, _i, _vp]),
     "dsr_wator_kinds": (_i, [_vp, _vp, _vp]),
@@ -123,6 +123,7 @@ SIGNATURES = {
     "dsr_bm_heap_stats": (_i, [_vp, _vp, C.POINTER(_u64), C.POINTER(_u32)]),
     "dsr_bm_heap_hash": (_i, [_vp, _i, _vp, _vp]),
     "dsr_bm_heap_counters": (_i, [_vp, _vp, C.POINTER(_u64)]),
+    "dsr_wator_bm_workspace_bytes": (_i, [_vp, _i, _i, C.POINTER(_sz)]),
     "dsr_wator_bm_create": (_i, [_vp, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
     "dsr_wator_bm_step": (_i, [_vp, _i, _vp]),
     "dsr_wator_bm_destroy": (_i, [_vp]),

@@ -80,7 +80,7 @@ class Wator:
             heap_bytes = heap_bytes_for_blocks(WATOR_TYPES, _blocks_for(W * H, [48], tuning=tuning), tuning)
         self.heap = Heap(WATOR_TYPES, heap_bytes, names=["Fish", "Shark"], tuning=tuning, stream=stream)
         ws = C.c_size_t(0)
-        L.check(self.lib.dsr_wator_workspace_bytes(W, H, C.byref(ws)), "dsr_wator_workspace_bytes")
+        L.check(self.lib.dsr_wator_workspace_bytes(self.heap.handle, W, H, C.byref(ws)), "dsr_wator_workspace_bytes")
         self.workspace = torch.empty(ws.value, dtype=torch.uint8, device="cuda")
         k0 = torch.as_tensor(np.ascontiguousarray(kind0, dtype=np.uint8).reshape(-1)).cuda()
         self.params = L.WatorParams(W, H, seed, fish_breed, shark_breed, shark_energy0, shark_gain)
@@ -170,7 +170,8 @@ class WatorBitmap:
         n = -(-(W * H) // 64) * 64
         self.heap = BitmapHeap(WATOR_TYPES, capacity or [n, n], stream=stream)
         ws = C.c_size_t(0)
-        L.check(self.lib.dsr_wator_workspace_bytes(W, H, C.byref(ws)), "dsr_wator_workspace_bytes")
+        L.check(self.lib.dsr_wator_bm_workspace_bytes(self.heap.handle, W, H, C.byref(ws)),
+                "dsr_wator_bm_workspace_bytes")
         self.workspace = torch.empty(ws.value, dtype=torch.uint8, device="cuda")
         k0 = torch.as_tensor(np.ascontiguousarray(kind0, dtype=np.uint8).reshape(-1)).cuda()
         self.params = L.WatorParams(W, H, seed, fish_breed, shark_breed, shark_energy0, shark_gain)

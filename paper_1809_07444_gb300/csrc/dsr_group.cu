@@ -229,8 +229,10 @@ extern "C" int dsr_group_add_heap(dsr_group* g, uint64_t n_blocks, size_t extra_
     size_t hb = 0;
     int rc = dsr_heap_bytes_for_blocks(g->types.data(), g->n_types, n_blocks, &g->tune, &hb);
     if (rc) return rc;
-    hb = round_up(hb, 1024);
-    const size_t need = hb + round_up(extra_bytes, 1024);
+    // The heap gets exactly the bytes of n_blocks blocks (so exactly n_blocks
+    // blocks); its range is rounded up so that the extra bytes after it stay
+    // aligned.
+    const size_t need = round_up(hb, 1024) + round_up(extra_bytes, 1024);
     // first fit
     auto it = g->free_ranges.begin();
     for (; it != g->free_ranges.end(); ++it)
@@ -260,7 +262,7 @@ extern "C" int dsr_group_add_heap(dsr_group* g, uint64_t n_blocks, size_t extra_
     if (rc) return rc;
     *index_out = slot;
     if (heap_out) *heap_out = h;
-    if (extra_dev_out) *extra_dev_out = g->arena + off + hb;
+    if (extra_dev_out) *extra_dev_out = g->arena + off + round_up(hb, 1024);
     return DSR_OK;
 }
 

@@ -17,10 +17,20 @@ constexpr uint32_t NO_MOVE = 0xFFFFFFFFu;
 struct WatorInst {
     dsr_u64* grid;     // 0 = empty, else (handle << 2) | kind
     dsr_u64* claim;    // lowest claim key of the current phase
-    uint32_t* intent;  // target chosen by the agent in this cell, or NO_MOVE
+    uint32_t* intent;  // per object slot (intent_index): its chosen target, or NO_MOVE
+    dsr_u64 n_slots;   // entries of intent
     dsr_u64* step;     // device step counter (nullptr: unused batch slot)
     dsr_wator_params p;
 };
+
+// Intents are indexed by the object's slot, not by its cell: the move phase
+// then reads its own intent together with its fields (one round trip), and
+// the choose phase writes them coalesced. dsr heap: handle = block * 64 +
+// slot; BitmapAlloc: the slot of the type's array.
+__device__ __forceinline__ dsr_u64 intent_index(const dsr_dev_heap&, dsr_ref r) { return r; }
+__device__ __forceinline__ dsr_u64 intent_index(const dsr_bm_dev&, dsr_ref r) {
+    return r & ((1ull << DSR_BM_SLOT_BITS) - 1);
+}
 
 // Claim key of phase `ph` (0 fish, 1 shark) of step t for a mover in cell c.
 // Keys of later phases compare lower than every key of earlier phases, so the
@@ -71,7 +81,8 @@ __device__ __forceinline__ void fish_choose(const HP& H, const WatorInst& I, dsr
         tgt = nb[pick(m, (unsigned)(dsr_rand(I.p.seed, 0, t, c) % (dsr_u64)__popc(m)))];
         atomicMin(I.claim + tgt, claim_key(t, 0, c));
     }
-    I.intent[c] = tgt;
+    const dsr_u64 ix = intent_index(H, self);
+    if (dsr_check(ix < I.n_slots, H.err, H.dbg, 8, ix)) I.intent[ix] = tgt;
 }
 
 // F2: winners move and breed.
@@ -81,10 +92,13 @@ __device__ __forceinline__ void fish_move(const HP& H, const WatorInst& I, dsr_r
     int32_t* px = dsr_field<int32_t>(H, FISH, self, X);
     int32_t* py = dsr_field<int32_t>(H, FISH, self, Y);
     int32_t* timer = dsr_field<int32_t>(H, FISH, self, TIMER);
-    const int32_t age = *timer;  // loaded with x and y: one round trip fewer for movers
+    const dsr_u64 ix = intent_index(H, self);
+    if (!dsr_check(ix < I.n_slots, H.err, H.dbg, 8, ix)) return;
+    // timer and intent are loaded with x and y: one round trip for all four
+    const int32_t age = *timer;
+    const uint32_t tgt = I.intent[ix];
     const uint32_t c = (uint32_t)(*py * I.p.W + *px);
     if (!cell_ok(H, I, c, 6)) return;
-    const uint32_t tgt = I.intent[c];
     if (tgt != NO_MOVE && !cell_ok(H, I, tgt, 7)) return;
     if (tgt == NO_MOVE || I.claim[tgt] != claim_key(t, 0, c)) return;
     dsr_count_lanes(H.ctr, DSR_CTR_APP0);
@@ -138,7 +152,8 @@ __device__ __forceinline__ void shark_choose(const HP& H, const WatorInst& I, ds
         tgt = nb[pick(m, (unsigned)(dsr_rand(I.p.seed, 1, t, c) % (dsr_u64)__popc(m)))];
         atomicMin(I.claim + tgt, claim_key(t, 1, c));
     }
-    I.intent[c] = tgt;
+    const dsr_u64 ix = intent_index(H, self);
+    if (dsr_check(ix < I.n_slots, H.err, H.dbg, 8, ix)) I.intent[ix] = tgt;
 }
 
 // S2: winners move, eat and breed.
@@ -149,10 +164,12 @@ __device__ __forceinline__ void shark_move(const HP& H, const WatorInst& I, dsr_
     int32_t* py = dsr_field<int32_t>(H, SHARK, self, Y);
     int32_t* timer = dsr_field<int32_t>(H, SHARK, self, TIMER);
     int32_t* energy = dsr_field<int32_t>(H, SHARK, self, ENERGY);
+    const dsr_u64 ix = intent_index(H, self);
+    if (!dsr_check(ix < I.n_slots, H.err, H.dbg, 8, ix)) return;
     const int32_t age = *timer, e0 = *energy;  // loaded with x and y
+    const uint32_t tgt = I.intent[ix];
     const uint32_t c = (uint32_t)(*py * I.p.W + *px);
     if (!cell_ok(H, I, c, 6)) return;
-    const uint32_t tgt = I.intent[c];
     if (tgt != NO_MOVE && !cell_ok(H, I, tgt, 7)) return;
     if (tgt == NO_MOVE || I.claim[tgt] != claim_key(t, 1, c)) return;
     dsr_count_lanes(H.ctr, DSR_CTR_APP0);
@@ -286,7 +303,6 @@ __global__ void k_wator_init(const __grid_constant__ HP H, const uint8_t* kind0,
         }
         I.grid[c] = g;
         I.claim[c] = ~0ull;
-        I.intent[c] = NO_MOVE;
         if (c == 0) *I.step = 0;
     }
 }
@@ -314,22 +330,30 @@ bool params_ok(const dsr_wator_params* p) {
            p->shark_breed >= 1 && p->shark_energy0 >= 1 && p->shark_gain >= 0;
 }
 
-size_t ws_bytes(int W, int H) {
+// Workspace: grid u64[n] | claim u64[n] | step counter (256 B) | intent
+// u32[slots], each part 256-byte aligned; slots = object slots of the heap.
+size_t ws_bytes(int W, int H, dsr_u64 slots) {
     const size_t n = (size_t)W * H;
-    return ((n * 8 + 255) / 256 * 256) * 2 + (n * 4 + 255) / 256 * 256 + 256;
+    return ((n * 8 + 255) / 256 * 256) * 2 + 256 + (slots * 4 + 255) / 256 * 256;
 }
 
-WatorInst carve(void* base, const dsr_wator_params& p) {
+WatorInst carve(void* base, const dsr_wator_params& p, dsr_u64 slots) {
     const size_t n = (size_t)p.W * p.H;
     uint8_t* b = static_cast<uint8_t*>(base);
-    const size_t g = (n * 8 + 255) / 256 * 256, in = (n * 4 + 255) / 256 * 256;
+    const size_t g = (n * 8 + 255) / 256 * 256;
     WatorInst w;
     w.grid = reinterpret_cast<dsr_u64*>(b);
     w.claim = reinterpret_cast<dsr_u64*>(b + g);
-    w.intent = reinterpret_cast<uint32_t*>(b + 2 * g);
-    w.step = reinterpret_cast<dsr_u64*>(b + 2 * g + in);
+    w.step = reinterpret_cast<dsr_u64*>(b + 2 * g);
+    w.intent = reinterpret_cast<uint32_t*>(b + 2 * g + 256);
+    w.n_slots = slots;
     w.p = p;
     return w;
+}
+
+dsr_u64 heap_slots(const dsr_heap* h) { return h->layout.n_blocks * 64; }
+dsr_u64 bm_slots(const dsr_bm_heap* h) {
+    return h->dev.cap[FISH] > h->dev.cap[SHARK] ? h->dev.cap[FISH] : h->dev.cap[SHARK];
 }
 
 int launch_init(const dsr_heap* heap, const WatorInst& I, const void* kind0_dev, cudaStream_t s) {
@@ -374,9 +398,15 @@ extern "C" int dsr_wator_types(dsr_type_desc* out) {
     return DSR_OK;
 }
 
-extern "C" int dsr_wator_workspace_bytes(int W, int H, size_t* out) {
-    if (!out || W < 3 || H < 3 || (int64_t)W * H >= (1ll << 31)) return DSR_E_INVALID;
-    *out = ws_bytes(W, H);
+extern "C" int dsr_wator_workspace_bytes(const dsr_heap* heap, int W, int H, size_t* out) {
+    if (!heap || !out || W < 3 || H < 3 || (int64_t)W * H >= (1ll << 31)) return DSR_E_INVALID;
+    *out = ws_bytes(W, H, heap_slots(heap));
+    return DSR_OK;
+}
+
+extern "C" int dsr_wator_bm_workspace_bytes(const dsr_bm_heap* heap, int W, int H, size_t* out) {
+    if (!heap || !out || W < 3 || H < 3 || (int64_t)W * H >= (1ll << 31)) return DSR_E_INVALID;
+    *out = ws_bytes(W, H, bm_slots(heap));
     return DSR_OK;
 }
 
@@ -386,7 +416,7 @@ extern "C" int dsr_wator_create(dsr_heap* heap, const dsr_wator_params* p, const
     if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255) || !heap_matches(heap)) return DSR_E_INVALID;
     dsr_wator* w = new dsr_wator;
     w->heap = heap;
-    w->inst = carve(workspace_dev, *p);
+    w->inst = carve(workspace_dev, *p, heap_slots(heap));
     int rc = launch_init(heap, w->inst, kind0_dev, dsr__stream(stream));
     if (rc) {
         delete w;
@@ -401,7 +431,7 @@ extern "C" int dsr_wator_attach(dsr_heap* heap, const dsr_wator_params* p, void*
     if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255) || !heap_matches(heap)) return DSR_E_INVALID;
     dsr_wator* w = new dsr_wator;
     w->heap = heap;
-    w->inst = carve(workspace_dev, *p);
+    w->inst = carve(workspace_dev, *p, heap_slots(heap));
     *out = w;
     return DSR_OK;
 }
@@ -529,7 +559,7 @@ extern "C" int dsr_wator_bm_create(dsr_bm_heap* heap, const dsr_wator_params* p,
     if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255) || !bm_heap_matches(heap)) return DSR_E_INVALID;
     dsr_wator_bm* w = new dsr_wator_bm;
     w->heap = heap;
-    w->inst = carve(workspace_dev, *p);
+    w->inst = carve(workspace_dev, *p, bm_slots(heap));
     const uint32_t n = (uint32_t)p->W * (uint32_t)p->H;
     unsigned ctas = (n + 255) / 256;
     if (ctas > (unsigned)heap->sm_count * 8) ctas = (unsigned)heap->sm_count * 8;
@@ -609,7 +639,7 @@ extern "C" int dsr_wator_batch_create(void* arena_dev, size_t arena_bytes, int m
 
 extern "C" int dsr_wator_batch_instance_bytes(const dsr_wator_batch* b, int W, int H, uint64_t n_blocks, size_t* out) {
     if (!b || !out || W < 3 || H < 3) return DSR_E_INVALID;
-    return dsr_group_heap_bytes(b->group, n_blocks, ws_bytes(W, H), out);
+    return dsr_group_heap_bytes(b->group, n_blocks, ws_bytes(W, H, n_blocks * 64), out);
 }
 
 extern "C" int dsr_wator_batch_add(dsr_wator_batch* b, const dsr_wator_params* p, uint64_t n_blocks,
@@ -618,10 +648,14 @@ extern "C" int dsr_wator_batch_add(dsr_wator_batch* b, const dsr_wator_params* p
     int slot = -1;
     dsr_heap* heap = nullptr;
     void* extra = nullptr;
-    int rc = dsr_group_add_heap(b->group, n_blocks, ws_bytes(p->W, p->H), stream, &slot, &heap, &extra);
+    int rc = dsr_group_add_heap(b->group, n_blocks, ws_bytes(p->W, p->H, n_blocks * 64), stream, &slot, &heap, &extra);
     if (rc) return rc;
     cudaStream_t s = dsr__stream(stream);
-    WatorInst I = carve(extra, *p);
+    if (heap->layout.n_blocks > n_blocks) {  // the intent array must cover every slot of the heap
+        dsr_group_remove_heap(b->group, slot);
+        return DSR_E_INVALID;
+    }
+    WatorInst I = carve(extra, *p, n_blocks * 64);
     rc = launch_init(heap, I, kind0_dev, s);
     if (rc) return rc;
     b->table_h[slot] = I;
