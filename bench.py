@@ -3,8 +3,9 @@
 
 Workload: wa-tor on a 2048 x 2048 torus (30% fish, 3% sharks, seed 1), the
 plain one-simulation form. A step is one wa-tor step: five parallel do-alls
-(scan + compaction + method kernel each) with device new/delete for births
-and deaths, i.e. every row of the hot path.
+with device new/delete for births and deaths, i.e. every row of the hot
+path. Three of them scan and compact the block list; F2 and S2 run over the
+lists of F1 and S1, which create and delete nothing.
 
   value      do-all object-updates/s (objects visited by method kernels per
              second of device time), inputs resident in HBM;
@@ -20,7 +21,8 @@ and deaths, i.e. every row of the hot path.
              method kernel inside the timed region; the event counts
              (objects, blocks, moves, births, deaths) from a replay of the
              same steps, checked against the timed window's visit count;
-  cpu_baseline  the oracle (single-threaded C++) on the same workload.
+  cpu_baseline  the oracle (single-threaded C++) on the same workload, and
+             bounded samples of the other configurations (configs).
 
 L2 (129 MB) is flushed by writing a 512 MB buffer before every timed step,
 outside the step's events. Multi-GPU: one independent replica per rank (no
@@ -763,7 +765,7 @@ def bench_served(seconds=20.0, n_jobs=10000, arena_gb=64, lo=128, hi=4096, steps
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel on this workload, mean over the 50 timed steps of a default run
 # (None for a kernel not captured as it is now).
-TRAFFIC = {}
+TRAFFIC = {"F2": 74.7e6}
 
 
 def roofline(phases, peak, peak_kind):
@@ -859,8 +861,8 @@ def main():
         line["nbody_65536"] = bench_nbody()
         if args.served_seconds > 0:
             line["served"] = bench_served(args.served_seconds)
-            # the same arrival process with jobs small enough to finish inside
-            # the bench's budget, so that job latencies exist
+            # the same arrival process with jobs small enough to finish within
+            # the served time window, so that job latencies exist
             line["served_small"] = bench_served(args.served_seconds, n_jobs=2000, arena_gb=16, lo=64, hi=512,
                                                 steps_lo=50, steps_hi=200,
                                                 label="a 2,000-job stream with sides in [64, 512] and 50-200 steps")
