@@ -62,6 +62,7 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-extra", action="store_true", help="headline only (no batched/served/microbenchmarks)")
     p.add_argument("--served-seconds", type=float, default=20.0)
+    p.add_argument("--leg", choices=sorted(LEGS), help="run one secondary benchmark alone and print its result")
     return p.parse_args()
 
 
@@ -800,10 +801,26 @@ def replica_seed(rank):
     return SEED + rank
 
 
+LEGS = {
+    "batched": lambda a: bench_batched(),
+    "alloc": lambda a: bench_alloc_sweep(),
+    "streaming": lambda a: bench_streaming_sweep(),
+    "gol": lambda a: bench_gol(),
+    "space": lambda a: bench_space(),
+    "comparators": lambda a: bench_comparators(),
+    "nbody": lambda a: bench_nbody(),
+    "served": lambda a: bench_served(a.served_seconds),
+}
+
+
 def main():
     args = _args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+
+    if args.leg:
+        print(json.dumps({"leg": args.leg, "result": LEGS[args.leg](args)}))
+        return 0
 
     if args.impl == "reference":
         if rank != 0:

@@ -202,8 +202,10 @@ int dsr_wator_batch_destroy(dsr_wator_batch* b);
  * id j != i closer than r_merge; mutual partners merge (the lower id keeps
  * the summed mass and the mass-weighted mean position and velocity, the
  * higher id is deleted). Workspace (dsr_nbody_workspace_bytes): dense
- * per-slot arrays for all M * 64 slots of the heap plus a merge log of
- * log_cap entries. */
+ * per-slot arrays for all M * 64 slots of the heap, the slice buffers of the
+ * split all-pairs kernels (sized from the device's SM count and the
+ * kernels' occupancy, so query it on the device that will run the step),
+ * and a merge log of log_cap entries. */
 typedef struct {
     float G, eps, dt, r_merge;
 } dsr_nbody_params;
