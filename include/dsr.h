@@ -160,6 +160,25 @@ int dsr_heap_plan(const dsr_type_desc* types, int n_types, uint64_t n_blocks, co
 int dsr_heap_create(const dsr_type_desc* types, int n_types, void* arena_dev, size_t heap_bytes,
                     const dsr_tuning* tune, void* stream, dsr_heap** out);
 
+/* Subtypes (Section 1: class inheritance without wasted memory).
+ * base[t] is the direct base type of type t, or -1. A base must be declared
+ * before its subtypes (base[t] < t), and a subtype's first fields are its
+ * base's fields, with the same sizes, in the same order (so field index f
+ * names the same field in a base and in all its subtypes). A subtype has its
+ * own blocks, laid out for its own size (its capacity follows from its own
+ * fields, not the largest type of the hierarchy). After dsr_heap_set_bases,
+ * a do-all over type t (dsr_parallel_do, dsr_doall_scan / dsr_doall_run)
+ * visits the live objects of t and of all its transitive subtypes, and the
+ * method sees each object's concrete type; dsr_heap_dump and dsr_heap_hash
+ * still cover exactly one type. Host-only, no CUDA call; call it before the
+ * heap's first do-all (it takes effect in kernels queued after it).
+ * dsr_type_tree checks base[] against the descriptors alone and writes
+ * sub_out[t], the bit mask of the types a do-all over t visits.
+ * DSR_E_INVALID for a base index out of range or after its subtype, or a
+ * subtype whose leading fields do not match its base's. */
+int dsr_type_tree(const dsr_type_desc* types, int n_types, const int* base, uint32_t* sub_out);
+int dsr_heap_set_bases(dsr_heap* heap, const int* base);
+
 /* Free the host handle. Does not touch the arena. */
 int dsr_heap_destroy(dsr_heap* heap);
 

@@ -84,6 +84,8 @@ struct dsr_dev_heap {
     uint32_t n_fields[DSR_MAX_TYPES];
     uint32_t foff[DSR_MAX_TYPES][DSR_MAX_FIELDS];  /* byte offset of a field's SOA array */
     uint8_t fsize[DSR_MAX_TYPES][DSR_MAX_FIELDS];
+    uint32_t sub[DSR_MAX_TYPES];                   /* types a do-all over T visits: T and its subtypes (bit mask) */
+    uint8_t span_sh[DSR_MAX_TYPES];                /* log2 threads per listed block in a do-all over T */
 };
 
 #ifdef __CUDACC__
@@ -587,10 +589,18 @@ __device__ __forceinline__ F* dsr_field(const dsr_dev_heap& H, int T, dsr_ref r,
 /* parallel do-all (Section 2.3)                                           */
 /* ------------------------------------------------------------------------ */
 
-/* Threads per listed block in the method kernel: 32 when the type's capacity
- * fits one warp, else 64. Each warp then covers one block, reads its R entry
- * once and touches one contiguous segment of every SOA array. */
-__device__ __forceinline__ unsigned dsr_span_shift(const dsr_dev_heap& H, int T) { return H.cap[T] <= 32 ? 5u : 6u; }
+/* Threads per listed block in the method kernel: 32 when the capacity of
+ * every type the do-all visits fits one warp, else 64. Each warp then covers
+ * one block, reads its R entry once and touches one contiguous segment of
+ * every SOA array. */
+__device__ __forceinline__ unsigned dsr_span_shift(const dsr_dev_heap& H, int T) { return H.span_sh[T]; }
+
+/* Concrete type of a listed block in a do-all over T: T itself, unless T has
+ * subtypes (dsr_heap_set_bases), whose blocks the list may also hold; then
+ * the block's type byte. */
+__device__ __forceinline__ int dsr_listed_type(const dsr_dev_heap& H, int T, uint32_t bid) {
+    return H.sub[T] == (1u << T) ? T : (int)H.btype[bid];
+}
 
 /* End of every kernel that consumes R: the last CTA to finish resets the
  * block-list counter for the next do-all. Returns true in thread 0 of that
@@ -625,7 +635,8 @@ __device__ __forceinline__ void dsr_call_finish(const dsr_dev_heap&, int, const 
  *   struct Args;  (trivially copyable)
  *   static __device__ void run(const dsr_dev_heap&, int T, const Args&, dsr_ref self);
  *   optionally static __device__ void finish(const dsr_dev_heap&, int T, const Args&);
- * Persistent grid-stride loop over (listed block, slot); a slot runs the
+ * run gets the concrete type of `self`: T, or one of T's subtypes when the
+ * heap declares them (dsr_heap_set_bases). Persistent grid-stride loop over (listed block, slot); a slot runs the
  * method iff it was occupied in the snapshot taken by the scan. With
  * keep_list the block list R survives the kernel, for a following do-all
  * over the same live set (one whose predecessor created and deleted no
@@ -645,8 +656,10 @@ __device__ __forceinline__ void dsr_doall_body(const dsr_dev_heap& H, int T, con
         __syncwarp();
         const dsr_u64 i = g >> sh;
         const unsigned s = (unsigned)(g & ((1u << sh) - 1));
-        if (((H.R_mask[i] >> s) & 1ull) && dsr_check(H.R_bid[i] < H.M, H.err, H.dbg, 10, i))
-            Method::run(H, T, args, ((dsr_u64)H.R_bid[i] << 6) | s);
+        if (((H.R_mask[i] >> s) & 1ull) && dsr_check(H.R_bid[i] < H.M, H.err, H.dbg, 10, i)) {
+            const uint32_t bid = H.R_bid[i];
+            Method::run(H, dsr_listed_type(H, T, bid), args, ((dsr_u64)bid << 6) | s);
+        }
     }
     if (dsr_doall_finish(H, keep_list != 0)) dsr_call_finish<Method>(H, T, args, 0);
 }

@@ -86,6 +86,8 @@ SIGNATURES = {
     "dsr_heap_destroy": (_i, [_vp]),
     "dsr_heap_reset": (_i, [_vp, _vp]),
     "dsr_heap_layout": (_i, [_vp, C.POINTER(Layout)]),
+    "dsr_type_tree": (_i, [C.POINTER(TypeDesc), _i, C.POINTER(_i), C.POINTER(_u32)]),
+    "dsr_heap_set_bases": (_i, [_vp, C.POINTER(_i)]),
     "dsr_dev_heap_size": (_sz, []),
     "dsr_heap_device_view": (_i, [_vp, _vp, _sz]),
     "dsr_heap_stats": (_i, [_vp, _vp, C.POINTER(Stats)]),

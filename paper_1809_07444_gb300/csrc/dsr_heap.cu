@@ -208,39 +208,45 @@ __global__ void k_heap_mark_free(const __grid_constant__ dsr_dev_heap H, dsr_u64
 // and reserves its run of R with one atomicAdd; every listed block gets its
 // id and the snapshot of its occupied slots. Runs of R follow block order
 // within a round, so consecutive entries are usually neighbouring blocks.
-__global__ void __launch_bounds__(256) k_scan(const __grid_constant__ dsr_dev_heap H, int T, unsigned visits_mult) {
+// `types` is a bit mask: a do-all over a type with subtypes lists the blocks
+// of every type in its subtree, one type after the other.
+__global__ void __launch_bounds__(256) k_scan(const __grid_constant__ dsr_dev_heap H, uint32_t types,
+                                              unsigned visits_mult) {
     __shared__ unsigned warp_n[8];
     __shared__ unsigned run_base;
-    const dsr_u64* leaf = H.alloc_bm[T].lvl[0];
-    const unsigned fsh = H.alloc_bm[T].shift, flo = (1u << fsh) - 1;
-    const dsr_u64 v = H.valid[T];
     const dsr_u64 M = H.M;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned objs = 0;
-    for (dsr_u64 base = (dsr_u64)blockIdx.x * 256; base < M; base += (dsr_u64)gridDim.x * 256) {
-        const dsr_u64 b = base + threadIdx.x;
-        const bool set = b < M && ((leaf[b >> fsh] >> (b & flo)) & 1ull);
-        const unsigned ballot = __ballot_sync(0xFFFFFFFFu, set);
-        if (lane == 0) warp_n[warp] = __popc(ballot);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned total = 0;
-            for (int w = 0; w < 8; ++w) {
-                const unsigned n = warp_n[w];
-                warp_n[w] = total;
-                total += n;
+    for (uint32_t tm = types; tm; tm &= tm - 1) {
+        const int T = __ffs(tm) - 1;
+        const dsr_u64* leaf = H.alloc_bm[T].lvl[0];
+        const unsigned fsh = H.alloc_bm[T].shift, flo = (1u << fsh) - 1;
+        const dsr_u64 v = H.valid[T];
+        for (dsr_u64 base = (dsr_u64)blockIdx.x * 256; base < M; base += (dsr_u64)gridDim.x * 256) {
+            const dsr_u64 b = base + threadIdx.x;
+            const bool set = b < M && ((leaf[b >> fsh] >> (b & flo)) & 1ull);
+            const unsigned ballot = __ballot_sync(0xFFFFFFFFu, set);
+            if (lane == 0) warp_n[warp] = __popc(ballot);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned total = 0;
+                for (int w = 0; w < 8; ++w) {
+                    const unsigned n = warp_n[w];
+                    warp_n[w] = total;
+                    total += n;
+                }
+                run_base = total ? atomicAdd(H.R_count, total) : 0;
             }
-            run_base = total ? atomicAdd(H.R_count, total) : 0;
+            __syncthreads();
+            if (set) {
+                const dsr_u64 live = v & ~H.obj[b];
+                const unsigned k = run_base + warp_n[warp] + __popc(ballot & ((1u << lane) - 1));
+                H.R_bid[k] = (uint32_t)b;
+                H.R_mask[k] = live;
+                objs += __popcll(live);
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (set) {
-            const dsr_u64 live = v & ~H.obj[b];
-            const unsigned k = run_base + warp_n[warp] + __popc(ballot & ((1u << lane) - 1));
-            H.R_bid[k] = (uint32_t)b;
-            H.R_mask[k] = live;
-            objs += __popcll(live);
-        }
-        __syncthreads();
     }
     objs = __reduce_add_sync(0xFFFFFFFFu, objs);
     if (lane == 0 && objs) dsr_count(H.ctr, DSR_CTR_VISITS, (dsr_u64)objs * visits_mult);
@@ -276,6 +282,7 @@ __global__ void k_stats(const __grid_constant__ dsr_dev_heap H, dsr_u64* out) {
 
 bool dsr__vec4_ok(const dsr_heap* h, int type) {
     const dsr_layout& L = h->layout;
+    if (h->dev.sub[type] != (1u << type)) return false;  // run4 takes one type
     if (L.capacity[type] % 4 || L.block_bytes % 16) return false;
     for (uint32_t f = 0; f < L.n_fields[type]; ++f)
         if (L.field_offset[type][f] % 16 || L.field_bytes[type][f] != 4) return false;
@@ -290,8 +297,9 @@ int dsr__scan_grid(const dsr_heap* h, int type) {
     return ctas < 1 ? 1 : (int)ctas;
 }
 
-void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s, unsigned visits_per_object) {
-    k_scan<<<dsr__scan_grid(h, type), 256, 0, s>>>(h->dev, type, visits_per_object);
+void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s, unsigned visits_per_object, bool exact) {
+    const uint32_t types = exact ? (1u << type) : h->dev.sub[type];
+    k_scan<<<dsr__scan_grid(h, type), 256, 0, s>>>(h->dev, types, visits_per_object);
 }
 
 int dsr__persistent_grid(const dsr_heap* h, const void* kernel, int threads) {
@@ -352,6 +360,8 @@ static void build_dev_view(dsr_heap* h) {
             D.foff[t][f] = L.field_offset[t][f];
             D.fsize[t][f] = (uint8_t)L.field_bytes[t][f];
         }
+        D.sub[t] = 1u << t;  // no subtypes until dsr_heap_set_bases
+        D.span_sh[t] = L.capacity[t] <= 32 ? 5 : 6;
     }
     h->stats_dev = reinterpret_cast<dsr_u64*>(a + DSR_HDR_STATS);
 }
@@ -412,6 +422,59 @@ extern "C" int dsr_heap_create(const dsr_type_desc* types, int n_types, void* ar
         return rc;
     }
     *out = h;
+    return DSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// subtypes (Section 1: class inheritance without wasted memory)
+// ---------------------------------------------------------------------------
+// Validates base[] against the types' fields and writes each type's subtree
+// mask: bit u of sub[t] is set iff u is t or a (transitive) subtype of t.
+static int type_tree(int n_types, const uint32_t* n_fields, const uint32_t (*field_bytes)[DSR_MAX_FIELDS],
+                     const int* base, uint32_t* sub) {
+    if (n_types < 1 || n_types > DSR_MAX_TYPES || !base || !sub) return DSR_E_INVALID;
+    for (int t = 0; t < n_types; ++t) {
+        const int b = base[t];
+        if (b < -1 || b >= t) return DSR_E_INVALID;  // a base is declared before its subtypes
+        if (b < 0) continue;
+        // the inherited fields come first, with the base's sizes, so a field
+        // index means the same field in the base and in every subtype
+        if (n_fields[t] < n_fields[b]) return DSR_E_INVALID;
+        for (uint32_t f = 0; f < n_fields[b]; ++f)
+            if (field_bytes[t][f] != field_bytes[b][f]) return DSR_E_INVALID;
+    }
+    for (int t = 0; t < n_types; ++t) sub[t] = 1u << t;
+    for (int t = n_types - 1; t >= 0; --t)  // subtypes have higher indices: children before parents
+        if (base[t] >= 0) sub[base[t]] |= sub[t];
+    return DSR_OK;
+}
+
+extern "C" int dsr_type_tree(const dsr_type_desc* types, int n_types, const int* base, uint32_t* sub_out) {
+    if (!types || n_types < 1 || n_types > DSR_MAX_TYPES) return DSR_E_INVALID;
+    uint32_t nf[DSR_MAX_TYPES];
+    uint32_t fb[DSR_MAX_TYPES][DSR_MAX_FIELDS];
+    for (int t = 0; t < n_types; ++t) {
+        if (types[t].n_fields < 1 || types[t].n_fields > DSR_MAX_FIELDS || !types[t].field_bytes)
+            return DSR_E_INVALID;
+        nf[t] = (uint32_t)types[t].n_fields;
+        for (int f = 0; f < types[t].n_fields; ++f) fb[t][f] = (uint32_t)types[t].field_bytes[f];
+    }
+    return type_tree(n_types, nf, fb, base, sub_out);
+}
+
+extern "C" int dsr_heap_set_bases(dsr_heap* h, const int* base) {
+    if (!h) return DSR_E_INVALID;
+    const dsr_layout& L = h->layout;
+    uint32_t sub[DSR_MAX_TYPES];
+    const int rc = type_tree((int)L.n_types, L.n_fields, L.field_bytes, base, sub);
+    if (rc) return rc;
+    for (uint32_t t = 0; t < L.n_types; ++t) {
+        h->dev.sub[t] = sub[t];
+        uint8_t sh = 5;  // 64 threads per listed block if any visited type has more than 32 slots
+        for (uint32_t u = 0; u < L.n_types; ++u)
+            if (((sub[t] >> u) & 1u) && L.capacity[u] > 32) sh = 6;
+        h->dev.span_sh[t] = sh;
+    }
     return DSR_OK;
 }
 
@@ -680,13 +743,13 @@ extern "C" int dsr_heap_dump(dsr_heap* h, int type, void* out_dev, uint64_t cap,
         return DSR_E_CUDA;
     }
     DumpArgs a{static_cast<uint32_t*>(out_dev), static_cast<dsr_u64*>(count_dev), cap, dsr_row_words(h, type)};
-    return dsr__doall<MDump>(h, type, a, s);
+    return dsr__doall<MDump>(h, type, a, s, true, nullptr, nullptr, 0, true);
 }
 
 extern "C" int dsr_heap_hash(dsr_heap* h, int type, void* hash_dev, void* stream) {
     if (!h || !hash_dev || type < 0 || type >= (int)h->layout.n_types) return DSR_E_INVALID;
     HashArgs a{static_cast<dsr_u64*>(hash_dev)};
-    return dsr__doall<MHash>(h, type, a, dsr__stream(stream));
+    return dsr__doall<MHash>(h, type, a, dsr__stream(stream), true, nullptr, nullptr, 0, true);
 }
 
 template <class M>
@@ -696,9 +759,19 @@ static int typed_args(const void* args, size_t bytes, typename M::Args* out) {
     return DSR_OK;
 }
 
+// True if every field of every type in the mask is 4 bytes wide.
+static bool all_fields_4(const dsr_layout& L, uint32_t types) {
+    for (uint32_t t = 0; t < L.n_types; ++t)
+        if ((types >> t) & 1u)
+            for (uint32_t f = 0; f < L.n_fields[t]; ++f)
+                if (L.field_bytes[t][f] != 4) return false;
+    return true;
+}
+
 static int dispatch(dsr_heap* h, int type, int method, const void* args, size_t args_bytes, cudaStream_t s,
                     bool with_scan) {
     if (!h || type < 0 || type >= (int)h->layout.n_types) return DSR_E_INVALID;
+    const uint32_t visited = h->dev.sub[type];  // type and its subtypes
     switch (method) {
         case DSR_METHOD_COUNT: {
             MCount::Args a;
@@ -706,8 +779,7 @@ static int dispatch(dsr_heap* h, int type, int method, const void* args, size_t 
             return dsr__doall<MCount>(h, type, a, s, with_scan);
         }
         case DSR_METHOD_STREAM_ADD: {
-            for (uint32_t f = 0; f < h->layout.n_fields[type]; ++f)
-                if (h->layout.field_bytes[type][f] != 4) return DSR_E_INVALID;
+            if (!all_fields_4(h->layout, visited)) return DSR_E_INVALID;
             return dsr__doall<MStreamAdd>(h, type, MStreamAdd::Args{0}, s, with_scan);
         }
         case DSR_METHOD_DELETE_IF: {
@@ -719,11 +791,10 @@ static int dispatch(dsr_heap* h, int type, int method, const void* args, size_t 
         case DSR_METHOD_CLONE: {
             MClone::Args a;
             if (typed_args<MClone>(args, args_bytes, &a)) return DSR_E_INVALID;
-            if (a.dst_type < 0 || a.dst_type >= (int)h->layout.n_types || a.dst_type == type) return DSR_E_INVALID;
-            for (uint32_t f = 0; f < h->layout.n_fields[type]; ++f)
-                if (h->layout.field_bytes[type][f] != 4) return DSR_E_INVALID;
-            for (uint32_t f = 0; f < h->layout.n_fields[a.dst_type]; ++f)
-                if (h->layout.field_bytes[a.dst_type][f] != 4) return DSR_E_INVALID;
+            // the clones are not visited: dst_type must lie outside the visited subtree
+            if (a.dst_type < 0 || a.dst_type >= (int)h->layout.n_types || ((visited >> a.dst_type) & 1u))
+                return DSR_E_INVALID;
+            if (!all_fields_4(h->layout, visited | (1u << a.dst_type))) return DSR_E_INVALID;
             return dsr__doall<MClone>(h, type, a, s, with_scan);
         }
         default:

@@ -43,7 +43,8 @@ int dsr__scan_grid(const dsr_heap* h, int type);
 // True if every field array of `type` starts on a 16-byte boundary within a
 // block and the capacity is a multiple of 4 (vector methods may run).
 bool dsr__vec4_ok(const dsr_heap* h, int type);
-void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s, unsigned visits_per_object = 1);
+// exact: list the blocks of `type` only, not those of its subtypes.
+void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s, unsigned visits_per_object = 1, bool exact = false);
 
 // Run a do-all: scan + compaction of allocated[type] into R, then the method
 // kernel over the listed blocks.
@@ -51,11 +52,12 @@ void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s, unsigned visi
 // method kernel, for per-phase timing. reuse > 0: the block list is kept for
 // `reuse` more do-alls over the same live set, and the scan counts each
 // listed object 1 + reuse times as visited (the visits those do-alls make).
+// exact: visit the objects of `type` only, not those of its subtypes.
 template <class M>
 int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t s, bool with_scan = true,
-               cudaEvent_t ev_scan = nullptr, cudaEvent_t ev_run = nullptr, int reuse = 0) {
+               cudaEvent_t ev_scan = nullptr, cudaEvent_t ev_run = nullptr, int reuse = 0, bool exact = false) {
     if (type < 0 || type >= h->dev.n_types) return DSR_E_INVALID;
-    if (with_scan) dsr__launch_scan(h, type, s, 1u + (unsigned)reuse);
+    if (with_scan) dsr__launch_scan(h, type, s, 1u + (unsigned)reuse, exact);
     if (ev_scan) cudaEventRecord(ev_scan, s);
     static int grid_cache[17] = {0};
     const int threads = h->tune.threads;

@@ -44,13 +44,27 @@ def heap_bytes_for_blocks(types, n_blocks, tuning=None):
     return int(out.value)
 
 
+def type_tree(types, bases):
+    """Bit masks of the types a do-all over each type visits, given each
+    type's direct base (-1 for none); raises DsrError for an invalid
+    hierarchy (a base after its subtype, or leading fields that differ)."""
+    lib = L.load()
+    descs, _keep = _descs(types)
+    b = (C.c_int * len(types))(*bases)
+    out = (C.c_uint32 * len(types))()
+    L.check(lib.dsr_type_tree(descs, len(types), b, out), "dsr_type_tree")
+    return [int(x) for x in out]
+
+
 class Heap:
     """A dsr heap in a torch-allocated device arena.
 
     types: list of per-type field byte sizes, e.g. [[4, 4, 4], [4, 4, 4, 4]].
+    bases: optional direct base type of each type (-1 for none); a do-all
+    over a type then also visits its subtypes' objects.
     """
 
-    def __init__(self, types, heap_bytes, names=None, tuning=None, stream=None, device="cuda"):
+    def __init__(self, types, heap_bytes, names=None, tuning=None, stream=None, device="cuda", bases=None):
         self.lib = L.load()
         self.types = [list(t) for t in types]
         self.names = names
@@ -65,6 +79,13 @@ class Heap:
                 "dsr_heap_create")
         self.handle = h
         self._scratch = torch.zeros(2, dtype=torch.int64, device=device)
+        if bases is not None:
+            self.set_bases(bases)
+
+    def set_bases(self, bases):
+        """Declare each type's direct base (-1 for none); see type_tree."""
+        b = (C.c_int * len(self.types))(*bases)
+        L.check(self.lib.dsr_heap_set_bases(self.handle, b), "dsr_heap_set_bases")
 
     @classmethod
     def view(cls, handle, types, arena, names=None):
