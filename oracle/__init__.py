@@ -86,6 +86,16 @@ def lib():
         L.orc_nbody_count.argtypes = [vp]
         L.orc_nbody_dump.restype = i64
         L.orc_nbody_dump.argtypes = [vp, vp, i64]
+
+        L.orc_traffic_create.restype = vp
+        L.orc_traffic_create.argtypes = [vp, vp]
+        L.orc_traffic_destroy.argtypes = [vp]
+        L.orc_traffic_step.argtypes = [vp, i32, vp]
+        L.orc_traffic_count.restype = i64
+        L.orc_traffic_count.argtypes = [vp]
+        L.orc_traffic_hash.argtypes = [vp, vp, vp]
+        L.orc_traffic_dump.restype = i64
+        L.orc_traffic_dump.argtypes = [vp, vp, i64, vp]
         _lib = L
     return _lib
 
@@ -321,3 +331,58 @@ class NBody:
         out = np.zeros((max(self.n0, 1), 8), dtype=np.float64)
         k = lib().orc_nbody_dump(self._h, _ptr(out), self.n0)
         return out[:k]
+
+
+class _TrafficParams(C.Structure):
+    _fields_ = [("R", C.c_int32), ("L", C.c_int32), ("vmax", C.c_int32), ("v_entry", C.c_int32),
+                ("periodic", C.c_int32), ("pad_", C.c_int32), ("seed", C.c_uint64), ("p_thr", C.c_uint64),
+                ("a_thr", C.c_uint64)]
+
+
+def prob_threshold(p):
+    """floor(p * 2^32): a 32-bit draw u is below probability p iff u < this."""
+    assert 0.0 <= p <= 1.0
+    return int(np.floor(p * 4294967296.0))
+
+
+class Traffic:
+    """Nagel-Schreckenberg traffic on R single-lane roads of L cells as two
+    do-alls per step (Car, then Source on open roads); rules in
+    orc_traffic.cpp."""
+
+    def __init__(self, R, L, v0, seed, vmax=5, p=0.25, alpha=0.5, v_entry=None, periodic=False):
+        v = np.ascontiguousarray(v0, dtype=np.int8).reshape(-1)
+        assert v.size == R * L
+        self.R, self.L, self.periodic = R, L, bool(periodic)
+        self._p = _TrafficParams(R, L, vmax, vmax if v_entry is None else v_entry, int(bool(periodic)), 0, seed,
+                                 prob_threshold(p), prob_threshold(alpha))
+        self._h = lib().orc_traffic_create(C.byref(self._p), _ptr(v))
+        assert self._h, "invalid traffic parameters"
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_traffic_destroy(self._h)
+            self._h = None
+
+    def step(self, n=1):
+        """Advance n steps; returns int64[n, 4] events (entered, left, moved,
+        velocity sum)."""
+        ev = np.zeros((max(n, 1), 4), dtype=np.int64)
+        lib().orc_traffic_step(self._h, n, _ptr(ev))
+        return ev[:n]
+
+    def count(self):
+        return int(lib().orc_traffic_count(self._h))
+
+    def hash(self):
+        a, b = C.c_uint64(0), C.c_uint64(0)
+        lib().orc_traffic_hash(self._h, C.byref(a), C.byref(b))
+        return a.value, b.value
+
+    def dump(self):
+        """(cars int32[n, 3] (road, x, v) sorted, sources int32[R or 0, 3])."""
+        n = self.count()
+        cars = np.zeros((max(n, 1), 3), dtype=np.int32)
+        src = np.zeros((self.R, 3), dtype=np.int32)
+        assert lib().orc_traffic_dump(self._h, _ptr(cars), n, _ptr(src)) == n
+        return cars[:n], (src[:0] if self.periodic else src)

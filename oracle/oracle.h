@@ -20,7 +20,8 @@
  *   - Heap invariant checker (Section 2, block states and Fig. 2; Section 3
  *     container consistency).
  *   - SMMO applications over a trivial allocator (Section 1.1, Fig. 6):
- *     game-of-life, wa-tor, n-body with merging collisions (FP64).
+ *     game-of-life, wa-tor, n-body with merging collisions (FP64), traffic
+ *     (Nagel-Schreckenberg).
  *
  * Parity status: every function here is pinned by tests under tests/ against
  * closed forms, published values, invariants or brute force, except where a
@@ -130,6 +131,32 @@ int64_t    orc_nbody_step(orc_nbody* b, int n_steps, int64_t* merges_out, int64_
 int64_t    orc_nbody_count(const orc_nbody* b);
 /* rows (id, x, y, z, vx, vy, vz, m) sorted by id; returns the count. */
 int64_t    orc_nbody_dump(const orc_nbody* b, double* out, int64_t cap);
+
+/* ---- traffic (Nagel-Schreckenberg; rules in orc_traffic.cpp) ----------- */
+typedef struct {
+    int32_t R, L;         /* roads, cells per road */
+    int32_t vmax;         /* maximum velocity (cells per step) */
+    int32_t v_entry;      /* velocity of a car entering an open road */
+    int32_t periodic;     /* 1: ring roads (no sources); 0: open roads */
+    int32_t pad_;
+    uint64_t seed;
+    uint64_t p_thr;       /* dawdle iff (r >> 32) < p_thr; floor(p * 2^32) */
+    uint64_t a_thr;       /* entry iff (r >> 32) < a_thr; floor(alpha * 2^32) */
+} orc_traffic_params;
+typedef struct orc_traffic orc_traffic;
+/* v0[R*L]: -1 = empty cell, else the initial velocity of the car there. */
+orc_traffic* orc_traffic_create(const orc_traffic_params* p, const int8_t* v0);
+void         orc_traffic_destroy(orc_traffic* t);
+/* events_out (may be NULL) receives, per step, 4 counts: cars entered, cars
+ * that left, cars that moved (v > 0), and the sum of the new velocities (all
+ * cars of the step, leaving ones included). */
+void         orc_traffic_step(orc_traffic* t, int n_steps, int64_t* events_out);
+int64_t      orc_traffic_count(const orc_traffic* t);
+void         orc_traffic_hash(const orc_traffic* t, uint64_t* car_hash, uint64_t* source_hash);
+/* cars_out[cap*3]: (road, x, v) sorted lexicographically; sources_out (may be
+ * NULL) [R*3]: (road, entered, blocked) by road (open roads). Returns the
+ * number of cars, or -1 if cap is too small. */
+int64_t      orc_traffic_dump(const orc_traffic* t, int32_t* cars_out, int64_t cap, int32_t* sources_out);
 
 #ifdef __cplusplus
 }
