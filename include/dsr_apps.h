@@ -2,8 +2,8 @@
  * dsr_apps.h -- C ABI of the SMMO applications that drive the heap.
  *
  * The paper evaluates its allocator with SMMO applications (Fig. 6): among
- * them game-of-life (cellular automaton), wator (agent-based predator-prey)
- * and nbody / collisions (particle systems). It names them without rules;
+ * them game-of-life (cellular automaton), wator (agent-based predator-prey),
+ * nbody / collisions (particle systems) and traffic (Nagel-Schreckenberg). It names them without rules;
  * the rules implemented here are stated at each entry point and are the same
  * as the oracle's.
  *
@@ -248,6 +248,44 @@ int dsr_nbody_destroy(dsr_nbody* nb);
 #define DSR_NOALLOC_MAX_SLOTS 16384
 int dsr_nbody_step_noalloc(dsr_heap* heap, const dsr_nbody_params* p, int n_steps, uint64_t step0, void* log_dev,
                            uint64_t log_cap, void* log_count_dev, void* stream);
+
+/* ---- traffic (Fig. 6g: the Nagel-Schreckenberg model) --------------------
+ * R single-lane roads of L cells, parallel update, integer state. Types:
+ * 0 Car {road, x, v}, 1 Source {road, entered, blocked} (one per open road).
+ * Step t (from 0), with occupancy read as it was at the start of the step:
+ *   do-all Car:    v1 = min(v + 1, vmax); g = free cells ahead of the car
+ *                  up to v1 cells (open road: cells past the end are free;
+ *                  periodic road: the road wraps); v2 = min(v1, g);
+ *                  v3 = max(v2 - 1, 0) if the draw rand(seed, 5, t,
+ *                  road * L + x) is below p, else v2; x' = x + v3; on an
+ *                  open road a car with x' >= L leaves (is deleted), on a
+ *                  periodic road x' wraps.
+ *   do-all Source: (open roads) if cell 0 is free after the cars moved and
+ *                  the draw rand(seed, 6, t, road) is below alpha, a new
+ *                  Car(road, 0, v_entry) enters and `entered` grows by 1; if
+ *                  a car holds cell 0, `blocked` grows by 1.
+ * rand is the counter-based draw of the wa-tor rules (SplitMix64 outputs
+ * keyed by seed, stream, step and cell); "below p" means (r >> 32) < p_thr
+ * with p_thr = floor(p * 2^32) (2^32 for p = 1). Event counters
+ * (dsr_heap_counters): APP0 cars entered, APP1 cars that left, APP2 cars
+ * that moved, APP3 the sum of the new velocities (flow x R x L per step).
+ * Workspace: two byte grids of R * L cells (each rounded up to 256 bytes).
+ * Requires 1 <= vmax <= 127, L > vmax, 0 <= v_entry <= vmax. */
+typedef struct {
+    int32_t R, L, vmax, v_entry, periodic, pad_;
+    uint64_t seed, p_thr, a_thr;
+} dsr_traffic_params;
+typedef struct dsr_traffic dsr_traffic;
+int dsr_traffic_types(dsr_type_desc* out /* 2 entries */);
+int dsr_traffic_workspace_bytes(const dsr_traffic_params* p, size_t* out);
+/* v0_dev: device int8[R * L], -1 for an empty cell, else the initial
+ * velocity of the car there (capped at vmax). */
+int dsr_traffic_create(dsr_heap* heap, const dsr_traffic_params* p, const void* v0_dev, void* workspace_dev,
+                       void* stream, dsr_traffic** out);
+int dsr_traffic_step(dsr_traffic* t, int n_steps, void* stream);
+/* Device pointer to the current occupancy grid (uint8[R * L], 1 = car). */
+int dsr_traffic_occupancy(const dsr_traffic* t, const void** grid_dev);
+int dsr_traffic_destroy(dsr_traffic* t);
 
 #ifdef __cplusplus
 }

@@ -57,6 +57,12 @@ class WatorParams(C.Structure):
                 ("shark_breed", C.c_int32), ("shark_energy0", C.c_int32), ("shark_gain", C.c_int32)]
 
 
+class TrafficParams(C.Structure):
+    _fields_ = [("R", C.c_int32), ("L", C.c_int32), ("vmax", C.c_int32), ("v_entry", C.c_int32),
+                ("periodic", C.c_int32), ("pad_", C.c_int32), ("seed", C.c_uint64), ("p_thr", C.c_uint64),
+                ("a_thr", C.c_uint64)]
+
+
 class NBodyParams(C.Structure):
     _fields_ = [("G", C.c_float), ("eps", C.c_float), ("dt", C.c_float), ("r_merge", C.c_float)]
 
@@ -144,6 +150,12 @@ SIGNATURES = {
     "dsr_nbody_merge_log": (_i, [_vp, C.POINTER(_vp), C.POINTER(_vp)]),
     "dsr_nbody_destroy": (_i, [_vp]),
     "dsr_nbody_step_noalloc": (_i, [_vp, C.POINTER(NBodyParams), _i, _u64, _vp, _u64, _vp, _vp]),
+    "dsr_traffic_types": (_i, [C.POINTER(TypeDesc)]),
+    "dsr_traffic_workspace_bytes": (_i, [C.POINTER(TrafficParams), C.POINTER(_sz)]),
+    "dsr_traffic_create": (_i, [_vp, C.POINTER(TrafficParams), _vp, _vp, _vp, C.POINTER(_vp)]),
+    "dsr_traffic_step": (_i, [_vp, _i, _vp]),
+    "dsr_traffic_occupancy": (_i, [_vp, C.POINTER(_vp)]),
+    "dsr_traffic_destroy": (_i, [_vp]),
     "dsr_group_create": (_i, [C.POINTER(TypeDesc), _i, _vp, _sz, _i, C.POINTER(Tuning), _vp, C.POINTER(_vp)]),
     "dsr_group_destroy": (_i, [_vp]),
     "dsr_group_add_heap": (_i, [_vp, _u64, _sz, _vp, C.POINTER(_i), C.POINTER(_vp), C.POINTER(_vp)]),

@@ -10,6 +10,7 @@ from .heap import Heap, _stream_ptr, heap_bytes_for_blocks
 
 GOL_TYPES = [[4, 4, 4], [4, 4]]          # Cell {alive, count, idx}, Alive {x, y}
 WATOR_TYPES = [[4, 4, 4], [4, 4, 4, 4]]  # Fish {x, y, timer}, Shark {x, y, timer, energy}
+TRAFFIC_TYPES = [[4, 4, 4], [4, 4, 4]]   # Car {road, x, v}, Source {road, entered, blocked}
 
 
 def _sorted_rows(a):
@@ -489,3 +490,77 @@ class NBody:
         off = lp.value - base
         log = self.workspace[off: off + 12 * n].cpu().numpy().view(np.int32).reshape(n, 3).astype(np.int64)
         return log[np.lexsort(log.T[::-1])] if n else log
+
+
+_LIBMOD = L  # Traffic's road length is named L, after the model
+
+
+def prob_threshold(p):
+    """floor(p * 2^32): a 32-bit draw u counts as below probability p iff u < this."""
+    if not 0.0 <= p <= 1.0:
+        raise ValueError("probability out of range")
+    return int(math.floor(p * 4294967296.0))
+
+
+class Traffic:
+    """Nagel-Schreckenberg traffic on R single-lane roads of L cells, driven
+    through libdsr (rules in include/dsr_apps.h).
+
+    v0: int8[R, L], -1 for an empty cell, else the car's initial velocity.
+    periodic: ring roads; otherwise open roads with a Source per road that
+    admits cars with probability alpha at velocity v_entry (default vmax).
+    """
+
+    def __init__(self, R, L, v0, seed, vmax=5, p=0.25, alpha=0.5, v_entry=None, periodic=False,
+                 heap_bytes=None, tuning=None, stream=None):
+        self.lib = _LIBMOD.load()
+        self.R, self.L, self.periodic = R, L, bool(periodic)
+        self.params = _LIBMOD.TrafficParams(R, L, vmax, vmax if v_entry is None else v_entry, int(bool(periodic)), 0,
+                                      seed, prob_threshold(p), prob_threshold(alpha))
+        if heap_bytes is None:
+            blocks = _blocks_for(R * L, [64], tuning=tuning) + math.ceil(R / 64)
+            heap_bytes = heap_bytes_for_blocks(TRAFFIC_TYPES, blocks, tuning)
+        self.heap = Heap(TRAFFIC_TYPES, heap_bytes, names=["Car", "Source"], tuning=tuning, stream=stream)
+        ws = C.c_size_t(0)
+        _LIBMOD.check(self.lib.dsr_traffic_workspace_bytes(C.byref(self.params), C.byref(ws)),
+                      "dsr_traffic_workspace_bytes")
+        self.workspace = torch.empty(ws.value, dtype=torch.uint8, device="cuda")
+        v = torch.as_tensor(np.ascontiguousarray(v0, dtype=np.int8).reshape(-1)).cuda()
+        h = C.c_void_p()
+        _LIBMOD.check(self.lib.dsr_traffic_create(self.heap.handle, C.byref(self.params), C.c_void_p(v.data_ptr()),
+                                            C.c_void_p(self.workspace.data_ptr()), _stream_ptr(stream), C.byref(h)),
+                "dsr_traffic_create")
+        self.handle = h
+        self._v0 = v
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.dsr_traffic_destroy(self.handle)
+            self.handle = None
+
+    def step(self, n=1, stream=None):
+        L.check(self.lib.dsr_traffic_step(self.handle, n, _stream_ptr(stream)), "dsr_traffic_step")
+
+    def count(self):
+        return int(self.heap.stats()["live_objects"][0])
+
+    def events(self):
+        """Cumulative (cars entered, cars that left, cars that moved, velocity sum)."""
+        c = self.heap.counters()
+        return tuple(int(c["app%d" % k]) for k in range(4))
+
+    def dump(self):
+        """(cars int32[n, 3] (road, x, v) sorted, sources int32[R or 0, 3] sorted)."""
+        cars, _ = self.heap.dump(0)
+        src, _ = self.heap.dump(1)
+        return _sorted_rows(cars.view(np.int32)), _sorted_rows(src.view(np.int32))
+
+    def hash(self):
+        return self.heap.hash(0), self.heap.hash(1)
+
+    def occupancy(self):
+        g = C.c_void_p()
+        L.check(self.lib.dsr_traffic_occupancy(self.handle, C.byref(g)), "dsr_traffic_occupancy")
+        n = self.R * self.L
+        off = g.value - self.workspace.data_ptr()
+        return self.workspace[off:off + n].cpu().numpy().reshape(self.R, self.L)

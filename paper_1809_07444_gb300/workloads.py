@@ -15,6 +15,8 @@ Shapes and distributions follow the workloads the applications run on:
     state and the FP64 oracle start from the same numbers; a draw is rejected
     (and the seed advanced) while some pair lies within `margin` of the merge
     distance;
+  - traffic: R roads of L cells, each cell holds a car with probability
+    `density`, with a velocity uniform in {0, ..., vmax};
   - batched wa-tor: side lengths log-uniform in [64, 1024];
   - served jobs: Poisson arrivals, game-of-life or wa-tor with equal odds,
     sides log-uniform in [128, 4096], step counts uniform in [50, 1000].
@@ -38,6 +40,14 @@ def wator_initial(W, H, seed, fish=0.30, shark=0.03):
     k[u < fish] = FISH
     k[(u >= fish) & (u < fish + shark)] = SHARK
     return k
+
+
+def traffic_initial(R, L, seed, density=0.2, vmax=5):
+    """int8[R, L]: -1 for an empty cell, else the initial velocity of its car."""
+    rng = np.random.default_rng(seed)
+    occupied = rng.random((R, L)) < density
+    v = rng.integers(0, vmax + 1, size=(R, L))
+    return np.where(occupied, v, -1).astype(np.int8)
 
 
 def nbody_initial(n, seed, r_merge=2e-3, margin=1e-5, max_tries=64):
