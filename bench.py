@@ -123,9 +123,10 @@ def _oracle_instance_rate(args):
 def oracle_config_rates():
     """The oracle on the other configurations, each a bounded sample: game
     of life 64x64 (100 generations, one core), n-body 65,536 bodies in FP64
-    (one step, rows split over all cores), and the batched workload (every
+    (one step, rows split over all cores), the batched workload (every
     fourth of the 256 instances, 3 steps each after 3 warm-up steps, one
-    spawned process per core)."""
+    spawned process per core), and traffic 8192 x 4096 (3 steps after 1
+    warm-up step, one core)."""
     import multiprocessing
     import oracle as O
     from paper_1809_07444_gb300 import workloads as WL
@@ -145,6 +146,18 @@ def oracle_config_rates():
     O.set_threads(1)
     out["nbody_65536"] = {"s_per_step": dt, "flops": 28.0 * 65536 * 65536 / dt, "cores": cores,
                           "sample": "the first step, FP64", "flop_per_pair": 28}
+    c = TRAFFIC_APP
+    tr = O.Traffic(c["R"], c["L"], WL.traffic_initial(c["R"], c["L"], SEED, c["density"], c["vmax"]), SEED,
+                   vmax=c["vmax"], p=c["p"], alpha=c["alpha"])
+    tr.step(1)
+    cars = 0
+    t0 = time.perf_counter()
+    for _ in range(3):
+        cars += tr.count()
+        tr.step(1)
+    dt = time.perf_counter() - t0
+    out["traffic"] = {"car_updates_per_s": cars / dt, "cores": 1, "sample": "steps 2-4"}
+    del tr
     sides = [int(s) for s in WL.batched_sides(256, 1)]
     jobs = [(sides[i], 1000 + i, 3, 3) for i in range(0, 256, 4)]
     t0 = time.perf_counter()
@@ -626,6 +639,55 @@ def bench_comparators(steps=50, warmup=5):
     return out
 
 
+TRAFFIC_APP = {"R": 8192, "L": 4096, "density": 0.2, "vmax": 5, "p": 0.25, "alpha": 0.5}
+
+
+def bench_traffic(steps=30, warmup=3):
+    """Traffic (Fig. 6g, Nagel-Schreckenberg) on 8192 open roads of 4096
+    cells, 20% occupied (6.7 M cars), L2 flushed before every step, CUDA
+    events per step. Algorithmic bytes per step: 21 per car visited (road, x,
+    v read; x, v written; the new occupancy mark), 13 per source visited, and
+    the occupancy grid read once and cleared once (2 bytes per cell)."""
+    import torch
+    from paper_1809_07444_gb300 import workloads as WL
+    from paper_1809_07444_gb300.apps import Traffic
+
+    c = TRAFFIC_APP
+    R, L = c["R"], c["L"]
+    w = Traffic(R, L, WL.traffic_initial(R, L, SEED, c["density"], c["vmax"]), SEED, vmax=c["vmax"], p=c["p"],
+                alpha=c["alpha"])
+    w.step(warmup)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ctr0 = w.heap.counters()
+    cars0 = w.count()
+    evs = [_ev() for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record()
+        w.step(1)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    ctr1 = w.heap.counters()
+    visits = ctr1["visits"] - ctr0["visits"]
+    src_visits = R * steps
+    car_visits = visits - src_visits
+    vsum = ctr1["app3"] - ctr0["app3"]
+    alg = car_visits * 21 + src_visits * 13 + 2 * R * L * steps
+    peak, peak_kind = _peaks()
+    del w, flush
+    torch.cuda.empty_cache()
+    return {"workload": "traffic %d roads x %d cells, %.0f%% occupied, vmax %d, p %.2f, alpha %.2f, steps %d-%d, "
+                        "L2 flushed before every step" % (R, L, 100 * c["density"], c["vmax"], c["p"], c["alpha"],
+                                                          warmup + 1, warmup + steps),
+            "ms_per_step": t * 1e3 / steps, "car_updates_per_s": car_visits / t, "object_updates_per_s": visits / t,
+            "cars_at_start": cars0, "flow_per_cell": vsum / (R * L * steps),
+            "entered": ctr1["app0"] - ctr0["app0"], "left": ctr1["app1"] - ctr0["app1"],
+            "algorithmic_gbs": alg / t / 1e9, "hbm_frac": alg / t / 1e9 / peak, "peak_gbs": peak,
+            "peak_kind": peak_kind, "launches_per_step": 4, "memsets_per_step": 1}
+
+
 def bench_space(heap_bytes=32 << 20, steps=100):
     """Fig. 8: the largest wa-tor torus a 32 MB heap runs for 100 steps
     without running out of memory, per tuning, with the peak bytes of live
@@ -766,7 +828,7 @@ def bench_served(seconds=20.0, n_jobs=10000, arena_gb=64, lo=128, hi=4096, steps
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel on this workload, mean over the 50 timed steps of a default run
 # (None for a kernel not captured as it is now).
-TRAFFIC = {"F2": 74.7e6}
+TRAFFIC = {}
 
 
 def roofline(phases, peak, peak_kind):
@@ -809,6 +871,7 @@ LEGS = {
     "space": lambda a: bench_space(),
     "comparators": lambda a: bench_comparators(),
     "nbody": lambda a: bench_nbody(),
+    "traffic": lambda a: bench_traffic(),
     "served": lambda a: bench_served(a.served_seconds),
 }
 
@@ -876,6 +939,7 @@ def main():
         line["space_efficiency"] = bench_space()
         line["comparators"] = bench_comparators()
         line["nbody_65536"] = bench_nbody()
+        line["traffic"] = bench_traffic()
         if args.served_seconds > 0:
             line["served"] = bench_served(args.served_seconds)
             # the same arrival process with jobs small enough to finish within
