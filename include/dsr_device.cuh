@@ -507,7 +507,7 @@ __device__ __forceinline__ dsr_u64 dsr_heap_key(const dsr_dev_heap& H) {
  * by shuffle. Returns DSR_NULL (and sets DSR_ERR_OOM or DSR_ERR_RETRY) on
  * failure. The new object's fields are not initialised. */
 #ifndef DSR_SPLIT_GROUP
-#define DSR_SPLIT_GROUP 4  /* lanes per leader once a round came up short */
+#define DSR_SPLIT_GROUP 4  /* most lanes per leader once a round came up short */
 #endif
 __device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
     const unsigned act = __activemask();
@@ -519,8 +519,9 @@ __device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
     // A block that offered fewer slots than the group needed means the
     // active blocks are nearly full (a fragmented heap), where one leader
     // would walk the holes one block at a time: the lanes still unserved
-    // then split into groups of at most DSR_SPLIT_GROUP lanes, whose leaders
-    // search in parallel from different starting points.
+    // then split into groups of as many lanes as that block offered (at
+    // least 1, at most DSR_SPLIT_GROUP), whose leaders search in parallel
+    // from different starting points.
     unsigned grp = peers;
     const unsigned lt = (1u << lane) - 1;
     for (unsigned round = 0;; ++round) {
@@ -544,7 +545,9 @@ __device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
         if (grank < n) return (bid << 6) | (dsr_u64)dsr_nth_bit(bits, grank);
         unsigned rest = grp;  // the unserved lanes: grp without its n lowest
         for (int k = 0; k < n; ++k) rest &= rest - 1;
-        grp = __match_any_sync(rest, (unsigned)(__popc(rest & lt) / DSR_SPLIT_GROUP));
+        // expect the next blocks to offer about what this one did
+        const int gsz = n < 1 ? 1 : (n > DSR_SPLIT_GROUP ? DSR_SPLIT_GROUP : n);
+        grp = __match_any_sync(rest, (unsigned)(__popc(rest & lt) / gsz));
     }
 }
 
