@@ -506,49 +506,38 @@ __device__ __forceinline__ dsr_u64 dsr_heap_key(const dsr_dev_heap& H) {
  * all of them, in as few atomics as the free slots allow, and hands them out
  * by shuffle. Returns DSR_NULL (and sets DSR_ERR_OOM or DSR_ERR_RETRY) on
  * failure. The new object's fields are not initialised. */
-#ifndef DSR_SPLIT_GROUP
-#define DSR_SPLIT_GROUP 4  /* most lanes per leader once a round came up short */
-#endif
 __device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
     const unsigned act = __activemask();
     const unsigned peers = __match_any_sync(act, dsr_heap_key(H) | (dsr_u64)T);
     const unsigned lane = dsr_lane();
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1));
+    const int need = __popc(peers);
     const unsigned hint = (blockIdx.x * 0x9E3779B1u) ^ ((threadIdx.x >> 5) * 0x85EBCA77u) ^ (unsigned)T;
-    // Each round a group leader takes as many slots as the block it finds
-    // (or a new block) offers; the lowest-ranked lanes of the group get them.
-    // A block that offered fewer slots than the group needed means the
-    // active blocks are nearly full (a fragmented heap), where one leader
-    // would walk the holes one block at a time: the lanes still unserved
-    // then split into groups of as many lanes as that block offered (at
-    // least 1, at most DSR_SPLIT_GROUP), whose leaders search in parallel
-    // from different starting points.
-    unsigned grp = peers;
-    const unsigned lt = (1u << lane) - 1;
-    for (unsigned round = 0;; ++round) {
-        const int gleader = __ffs(grp) - 1;
-        const int grank = __popc(grp & lt);
+    dsr_ref mine = DSR_NULL;
+    int served = 0;
+    // Each round the leader takes as many slots as the block it finds (or a
+    // new block) offers, until the group is served.
+    while (served < need) {
         dsr_u64 bid = 0, bits = 0;
         uint32_t st = 0;
-        if ((int)lane == gleader) {
-            const dsr_grab g = dsr_reserve(H, T, __popc(grp), hint + round * 0x632BE5ABu + (unsigned)gleader);
+        if ((int)lane == leader) {
+            const dsr_grab g = dsr_reserve(H, T, need - served, hint + (unsigned)served);
             bid = g.bid;
             bits = g.bits;
             st = g.status;
             if (st) atomicOr(H.err, st);
             else dsr_count(H.ctr, DSR_CTR_ALLOCS, (dsr_u64)__popcll(bits));
         }
-        bid = __shfl_sync(grp, bid, gleader);
-        bits = __shfl_sync(grp, bits, gleader);
-        st = __shfl_sync(grp, st, gleader);
-        if (st) return DSR_NULL;
+        bid = __shfl_sync(peers, bid, leader);
+        bits = __shfl_sync(peers, bits, leader);
+        st = __shfl_sync(peers, st, leader);
+        if (st) break;
         const int n = __popcll(bits);
-        if (grank < n) return (bid << 6) | (dsr_u64)dsr_nth_bit(bits, grank);
-        unsigned rest = grp;  // the unserved lanes: grp without its n lowest
-        for (int k = 0; k < n; ++k) rest &= rest - 1;
-        // expect the next blocks to offer about what this one did
-        const int gsz = n < 1 ? 1 : (n > DSR_SPLIT_GROUP ? DSR_SPLIT_GROUP : n);
-        grp = __match_any_sync(rest, (unsigned)(__popc(rest & lt) / gsz));
+        if (rank >= served && rank < served + n) mine = (bid << 6) | (dsr_u64)dsr_nth_bit(bits, rank - served);
+        served += n;
     }
+    return mine;
 }
 
 /* delete: callable by any subset of a warp's lanes, with any mix of heaps.
