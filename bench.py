@@ -828,7 +828,7 @@ def bench_served(seconds=20.0, n_jobs=10000, arena_gb=64, lo=128, hi=4096, steps
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel on this workload, mean over the 50 timed steps of a default run
 # (None for a kernel not captured as it is now).
-TRAFFIC = {}
+TRAFFIC = {"F2": 74.9e6}
 
 
 def roofline(phases, peak, peak_kind):
