@@ -96,6 +96,17 @@ def lib():
         L.orc_traffic_hash.argtypes = [vp, vp, vp]
         L.orc_traffic_dump.restype = i64
         L.orc_traffic_dump.argtypes = [vp, vp, i64, vp]
+
+        L.orc_sugarscape_create.restype = vp
+        L.orc_sugarscape_create.argtypes = [vp, vp, vp, i64]
+        L.orc_sugarscape_destroy.argtypes = [vp]
+        L.orc_sugarscape_step.argtypes = [vp, i32, vp]
+        L.orc_sugarscape_count.restype = i64
+        L.orc_sugarscape_count.argtypes = [vp]
+        L.orc_sugarscape_hash.restype = u64
+        L.orc_sugarscape_hash.argtypes = [vp]
+        L.orc_sugarscape_dump.restype = i64
+        L.orc_sugarscape_dump.argtypes = [vp, vp, i64, vp]
         _lib = L
     return _lib
 
@@ -386,3 +397,54 @@ class Traffic:
         src = np.zeros((self.R, 3), dtype=np.int32)
         assert lib().orc_traffic_dump(self._h, _ptr(cars), n, _ptr(src)) == n
         return cars[:n], (src[:0] if self.periodic else src)
+
+
+class _SugarParams(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("seed", C.c_uint64), ("alpha", C.c_int32),
+                ("endow_lo", C.c_int32), ("endow_hi", C.c_int32), ("metab_lo", C.c_int32), ("metab_hi", C.c_int32),
+                ("vision_lo", C.c_int32), ("vision_hi", C.c_int32), ("age_lo", C.c_int32), ("age_hi", C.c_int32)]
+
+
+class Sugarscape:
+    """Sugarscape (Epstein-Axtell rules M, G_alpha, R) as four do-alls per
+    step; rules in orc_sugarscape.cpp.
+
+    cap: uint8[H, W] capacities; agents0: int32[n, 7] (x, y, sugar,
+    metabolism, vision, age, max_age)."""
+
+    def __init__(self, W, H, cap, agents0, seed, alpha=1, endow=(5, 25), metab=(1, 4), vision=(1, 6),
+                 max_age=(60, 100)):
+        c = np.ascontiguousarray(cap, dtype=np.uint8).reshape(-1)
+        a = np.ascontiguousarray(agents0, dtype=np.int32).reshape(-1, 7)
+        assert c.size == W * H
+        self.W, self.H = W, H
+        self._p = _SugarParams(W, H, seed, alpha, endow[0], endow[1], metab[0], metab[1], vision[0], vision[1],
+                               max_age[0], max_age[1])
+        self._h = lib().orc_sugarscape_create(C.byref(self._p), _ptr(c), _ptr(a), len(a))
+        assert self._h, "invalid sugarscape parameters or agents"
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_sugarscape_destroy(self._h)
+            self._h = None
+
+    def step(self, n=1):
+        """Advance n steps; returns int64[n, 5] events (moves, starved, aged,
+        replacements placed elsewhere, sugar harvested)."""
+        ev = np.zeros((max(n, 1), 5), dtype=np.int64)
+        lib().orc_sugarscape_step(self._h, n, _ptr(ev))
+        return ev[:n]
+
+    def count(self):
+        return int(lib().orc_sugarscape_count(self._h))
+
+    def hash(self):
+        return int(lib().orc_sugarscape_hash(self._h))
+
+    def dump(self):
+        """(agents int32[n, 8] sorted, sugar int32[H, W])."""
+        n = self.count()
+        a = np.zeros((max(n, 1), 8), dtype=np.int32)
+        sg = np.zeros(self.W * self.H, dtype=np.int32)
+        assert lib().orc_sugarscape_dump(self._h, _ptr(a), n, _ptr(sg)) == n
+        return a[:n], sg.reshape(self.H, self.W)

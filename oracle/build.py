@@ -9,7 +9,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["orc_rng.cpp", "orc_hbitmap.cpp", "orc_gol.cpp", "orc_wator.cpp", "orc_nbody.cpp", "orc_traffic.cpp"]
+SOURCES = ["orc_rng.cpp", "orc_hbitmap.cpp", "orc_gol.cpp", "orc_wator.cpp", "orc_nbody.cpp", "orc_traffic.cpp", "orc_sugarscape.cpp"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -21,7 +21,7 @@
  *     container consistency).
  *   - SMMO applications over a trivial allocator (Section 1.1, Fig. 6):
  *     game-of-life, wa-tor, n-body with merging collisions (FP64), traffic
- *     (Nagel-Schreckenberg).
+ *     (Nagel-Schreckenberg), sugarscape (Epstein-Axtell rules M, G, R).
  *
  * Parity status: every function here is pinned by tests under tests/ against
  * closed forms, published values, invariants or brute force, except where a
@@ -157,6 +157,33 @@ void         orc_traffic_hash(const orc_traffic* t, uint64_t* car_hash, uint64_t
  * NULL) [R*3]: (road, entered, blocked) by road (open roads). Returns the
  * number of cars, or -1 if cap is too small. */
 int64_t      orc_traffic_dump(const orc_traffic* t, int32_t* cars_out, int64_t cap, int32_t* sources_out);
+
+/* ---- sugarscape (rules in orc_sugarscape.cpp) -------------------------- */
+typedef struct {
+    int32_t W, H;
+    uint64_t seed;
+    int32_t alpha;                   /* growback per step */
+    int32_t endow_lo, endow_hi;      /* initial sugar of a new agent */
+    int32_t metab_lo, metab_hi;
+    int32_t vision_lo, vision_hi;    /* W, H >= 2 * vision_hi + 1 */
+    int32_t age_lo, age_hi;          /* maximum age */
+} orc_sugarscape_params;
+typedef struct orc_sugarscape orc_sugarscape;
+/* cap[W*H] in {0..4}; agents0[n][7] = (x, y, sugar, metabolism, vision, age,
+ * max_age), at distinct cells. */
+orc_sugarscape* orc_sugarscape_create(const orc_sugarscape_params* p, const uint8_t* cap,
+                                      const int32_t* agents0, int64_t n_agents);
+void            orc_sugarscape_destroy(orc_sugarscape* s);
+/* events_out (may be NULL) receives, per step, 5 counts: moves, agents
+ * starved, agents that reached their maximum age, replacements placed away
+ * from the dead agent's cell, and the sugar harvested. */
+void            orc_sugarscape_step(orc_sugarscape* s, int n_steps, int64_t* events_out);
+int64_t         orc_sugarscape_count(const orc_sugarscape* s);
+uint64_t        orc_sugarscape_hash(const orc_sugarscape* s);
+/* agents_out[cap*8] (x, y, sugar, metabolism, vision, age, max_age, dead)
+ * sorted; sugar_out (may be NULL) [W*H] the sugar of every cell. Returns the
+ * number of agents, or -1 if cap is too small. */
+int64_t         orc_sugarscape_dump(const orc_sugarscape* s, int32_t* agents_out, int64_t cap, int32_t* sugar_out);
 
 #ifdef __cplusplus
 }
