@@ -3,7 +3,8 @@
  *
  * The paper evaluates its allocator with SMMO applications (Fig. 6): among
  * them game-of-life (cellular automaton), wator (agent-based predator-prey),
- * nbody / collisions (particle systems) and traffic (Nagel-Schreckenberg). It names them without rules;
+ * nbody / collisions (particle systems), traffic (Nagel-Schreckenberg) and
+ * sugarscape (Epstein-Axtell). It names them without rules;
  * the rules implemented here are stated at each entry point and are the same
  * as the oracle's.
  *
@@ -286,6 +287,51 @@ int dsr_traffic_step(dsr_traffic* t, int n_steps, void* stream);
 /* Device pointer to the current occupancy grid (uint8[R * L], 1 = car). */
 int dsr_traffic_occupancy(const dsr_traffic* t, const void** grid_dev);
 int dsr_traffic_destroy(dsr_traffic* t);
+
+/* ---- sugarscape (Fig. 6f; Epstein and Axtell's rules M, G_alpha, R) -----
+ * W x H torus of sugar cells (capacity 0..4, sugar starts at capacity and
+ * grows back by alpha a step up to it). Type: 0 Agent {x, y, sugar,
+ * metabolism, vision, age, max_age, dead}. Step t:
+ *   A1 do-all Agent: target = among the own cell and the cells up to
+ *      `vision` away in the order N (y-1), E (x+1), S (y+1), W (x-1) that no
+ *      agent occupies, the most sugar, then the nearest, then candidate
+ *      (r >> 32) mod k with r = rand(seed, 12, t, own cell); a target other
+ *      than the own cell is claimed, the lowest own cell index wins.
+ *   A2 do-all Agent: the winner moves; every agent takes all the sugar of its
+ *      cell, pays its metabolism and ages by 1; it dies (dead = 1) if its
+ *      sugar is below 0 or its age reached max_age.
+ *   A3 do-all Agent: a dead agent draws c = (rand(seed, 13, t, own) >> 32)
+ *      mod (W * H) and claims c if no agent occupies it (lowest own wins).
+ *   A4 do-all Agent: a dead agent is replaced by a new agent (age 0; sugar,
+ *      metabolism, vision, max_age = lo + (r >> 32) mod (hi - lo + 1) with
+ *      r = rand(seed, 8..11, t, new cell)) at c if it won c, else in its
+ *      own cell, and deletes itself.
+ * rand as for the wa-tor rules. Workspace (dsr_sugarscape_workspace_bytes,
+ * which depends on the heap): per-cell capacity, occupancy, last-harvest
+ * step and two claim words, a target per heap slot, and event counters.
+ * Requires W, H >= 2 * vision_hi + 1, vision_hi <= 64, W * H < 2^31. */
+typedef struct {
+    int32_t W, H;
+    uint64_t seed;
+    int32_t alpha;
+    int32_t endow_lo, endow_hi, metab_lo, metab_hi, vision_lo, vision_hi, age_lo, age_hi;
+} dsr_sugarscape_params;
+typedef struct dsr_sugarscape dsr_sugarscape;
+int dsr_sugarscape_types(dsr_type_desc* out /* 1 entry */);
+int dsr_sugarscape_workspace_bytes(const dsr_heap* heap, const dsr_sugarscape_params* p, size_t* out);
+/* cap_dev: device uint8[W * H]; agents0_dev: device int32[n_agents][7] =
+ * (x, y, sugar, metabolism, vision, age, max_age) at distinct cells. */
+int dsr_sugarscape_create(dsr_heap* heap, const dsr_sugarscape_params* p, const void* cap_dev,
+                          const void* agents0_dev, int64_t n_agents, void* workspace_dev, void* stream,
+                          dsr_sugarscape** out);
+int dsr_sugarscape_step(dsr_sugarscape* s, int n_steps, void* stream);
+/* Cumulative events (host uint64[5]): moves, agents starved, agents that
+ * reached their maximum age, replacements placed away from the dead agent's
+ * cell, sugar harvested. Synchronises `stream`. */
+int dsr_sugarscape_events(dsr_sugarscape* s, void* stream, uint64_t* out);
+/* The sugar of every cell at the start of the next step (device int32[W*H]). */
+int dsr_sugarscape_sugar(dsr_sugarscape* s, void* out_dev, void* stream);
+int dsr_sugarscape_destroy(dsr_sugarscape* s);
 
 #ifdef __cplusplus
 }

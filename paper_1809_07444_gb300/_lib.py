@@ -63,6 +63,12 @@ class TrafficParams(C.Structure):
                 ("a_thr", C.c_uint64)]
 
 
+class SugarscapeParams(C.Structure):
+    _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("seed", C.c_uint64), ("alpha", C.c_int32),
+                ("endow_lo", C.c_int32), ("endow_hi", C.c_int32), ("metab_lo", C.c_int32), ("metab_hi", C.c_int32),
+                ("vision_lo", C.c_int32), ("vision_hi", C.c_int32), ("age_lo", C.c_int32), ("age_hi", C.c_int32)]
+
+
 class NBodyParams(C.Structure):
     _fields_ = [("G", C.c_float), ("eps", C.c_float), ("dt", C.c_float), ("r_merge", C.c_float)]
 
@@ -156,6 +162,14 @@ SIGNATURES = {
     "dsr_traffic_step": (_i, [_vp, _i, _vp]),
     "dsr_traffic_occupancy": (_i, [_vp, C.POINTER(_vp)]),
     "dsr_traffic_destroy": (_i, [_vp]),
+    "dsr_sugarscape_types": (_i, [C.POINTER(TypeDesc)]),
+    "dsr_sugarscape_workspace_bytes": (_i, [_vp, C.POINTER(SugarscapeParams), C.POINTER(_sz)]),
+    "dsr_sugarscape_create": (_i, [_vp, C.POINTER(SugarscapeParams), _vp, _vp, C.c_int64, _vp, _vp,
+                                   C.POINTER(_vp)]),
+    "dsr_sugarscape_step": (_i, [_vp, _i, _vp]),
+    "dsr_sugarscape_events": (_i, [_vp, _vp, C.POINTER(_u64)]),
+    "dsr_sugarscape_sugar": (_i, [_vp, _vp, _vp]),
+    "dsr_sugarscape_destroy": (_i, [_vp]),
     "dsr_group_create": (_i, [C.POINTER(TypeDesc), _i, _vp, _sz, _i, C.POINTER(Tuning), _vp, C.POINTER(_vp)]),
     "dsr_group_destroy": (_i, [_vp]),
     "dsr_group_add_heap": (_i, [_vp, _u64, _sz, _vp, C.POINTER(_i), C.POINTER(_vp), C.POINTER(_vp)]),

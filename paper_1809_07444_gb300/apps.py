@@ -11,6 +11,7 @@ from .heap import Heap, _stream_ptr, heap_bytes_for_blocks
 GOL_TYPES = [[4, 4, 4], [4, 4]]          # Cell {alive, count, idx}, Alive {x, y}
 WATOR_TYPES = [[4, 4, 4], [4, 4, 4, 4]]  # Fish {x, y, timer}, Shark {x, y, timer, energy}
 TRAFFIC_TYPES = [[4, 4, 4], [4, 4, 4]]   # Car {road, x, v}, Source {road, entered, blocked}
+SUGAR_TYPES = [[4] * 8]                  # Agent {x, y, sugar, metabolism, vision, age, max_age, dead}
 
 
 def _sorted_rows(a):
@@ -564,3 +565,64 @@ class Traffic:
         n = self.R * self.L
         off = g.value - self.workspace.data_ptr()
         return self.workspace[off:off + n].cpu().numpy().reshape(self.R, self.L)
+
+
+class Sugarscape:
+    """Sugarscape (Epstein-Axtell rules M, G_alpha, R) on a W x H torus,
+    driven through libdsr (rules in include/dsr_apps.h).
+
+    cap: uint8[H, W] capacities (0..4); agents0: int32[n, 7] (x, y, sugar,
+    metabolism, vision, age, max_age) at distinct cells.
+    """
+
+    def __init__(self, W, H, cap, agents0, seed, alpha=1, endow=(5, 25), metab=(1, 4), vision=(1, 6),
+                 max_age=(60, 100), heap_bytes=None, tuning=None, stream=None):
+        self.lib = L.load()
+        self.W, self.H = W, H
+        self.params = L.SugarscapeParams(W, H, seed, alpha, endow[0], endow[1], metab[0], metab[1], vision[0],
+                                         vision[1], max_age[0], max_age[1])
+        a0 = np.ascontiguousarray(agents0, dtype=np.int32).reshape(-1, 7)
+        if heap_bytes is None:
+            heap_bytes = heap_bytes_for_blocks(SUGAR_TYPES, _blocks_for(len(a0) + 64, [64], tuning=tuning), tuning)
+        self.heap = Heap(SUGAR_TYPES, heap_bytes, names=["Agent"], tuning=tuning, stream=stream)
+        ws = C.c_size_t(0)
+        L.check(self.lib.dsr_sugarscape_workspace_bytes(self.heap.handle, C.byref(self.params), C.byref(ws)),
+                "dsr_sugarscape_workspace_bytes")
+        self.workspace = torch.empty(ws.value, dtype=torch.uint8, device="cuda")
+        c = torch.as_tensor(np.ascontiguousarray(cap, dtype=np.uint8).reshape(-1)).cuda()
+        a = torch.as_tensor(a0.reshape(-1)).cuda() if len(a0) else torch.zeros(1, dtype=torch.int32, device="cuda")
+        h = C.c_void_p()
+        L.check(self.lib.dsr_sugarscape_create(self.heap.handle, C.byref(self.params), C.c_void_p(c.data_ptr()),
+                                               C.c_void_p(a.data_ptr()), len(a0),
+                                               C.c_void_p(self.workspace.data_ptr()), _stream_ptr(stream),
+                                               C.byref(h)), "dsr_sugarscape_create")
+        self.handle = h
+        self._keep = (c, a)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.dsr_sugarscape_destroy(self.handle)
+            self.handle = None
+
+    def step(self, n=1, stream=None):
+        L.check(self.lib.dsr_sugarscape_step(self.handle, n, _stream_ptr(stream)), "dsr_sugarscape_step")
+
+    def count(self):
+        return int(self.heap.stats()["live_objects"][0])
+
+    def events(self, stream=None):
+        """Cumulative (moves, starved, aged, replacements placed elsewhere, sugar harvested)."""
+        out = (C.c_uint64 * 5)()
+        L.check(self.lib.dsr_sugarscape_events(self.handle, _stream_ptr(stream), out), "dsr_sugarscape_events")
+        return tuple(int(v) for v in out)
+
+    def dump(self):
+        """(agents int32[n, 8] sorted, sugar int32[H, W])."""
+        a, _ = self.heap.dump(0)
+        sg = torch.empty(self.W * self.H, dtype=torch.int32, device="cuda")
+        L.check(self.lib.dsr_sugarscape_sugar(self.handle, C.c_void_p(sg.data_ptr()), _stream_ptr()),
+                "dsr_sugarscape_sugar")
+        return _sorted_rows(a.view(np.int32)), sg.cpu().numpy().reshape(self.H, self.W)
+
+    def hash(self):
+        return self.heap.hash(0)

@@ -17,6 +17,11 @@ Shapes and distributions follow the workloads the applications run on:
     distance;
   - traffic: R roads of L cells, each cell holds a car with probability
     `density`, with a velocity uniform in {0, ..., vmax};
+  - sugarscape: W x H torus with two sugar hills (capacity 4 at the peaks,
+    (W/4, H/4) and (3W/4, 3H/4), falling by 1 every W/10 cells of distance,
+    floor at 0); each cell holds an agent with probability `density`, with
+    sugar uniform in [5, 25], metabolism in [1, 4], vision in [1, 6],
+    maximum age in [60, 100] and an age uniform below it;
   - batched wa-tor: side lengths log-uniform in [64, 1024];
   - served jobs: Poisson arrivals, game-of-life or wa-tor with equal odds,
     sides log-uniform in [128, 4096], step counts uniform in [50, 1000].
@@ -48,6 +53,26 @@ def traffic_initial(R, L, seed, density=0.2, vmax=5):
     occupied = rng.random((R, L)) < density
     v = rng.integers(0, vmax + 1, size=(R, L))
     return np.where(occupied, v, -1).astype(np.int8)
+
+
+def sugarscape_initial(W, H, seed, density=0.1):
+    """(cap uint8[H, W], agents int32[n, 7] = x, y, sugar, metabolism,
+    vision, age, max_age)."""
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:H, 0:W]
+    step = max(W, H) / 10.0
+    cap = np.zeros((H, W), dtype=np.int64)
+    for px, py in ((W / 4, H / 4), (3 * W / 4, 3 * H / 4)):
+        dx = np.minimum(np.abs(x - px), W - np.abs(x - px))
+        dy = np.minimum(np.abs(y - py), H - np.abs(y - py))
+        cap = np.maximum(cap, 4 - np.floor(np.hypot(dx, dy) / step).astype(np.int64))
+    cap = np.clip(cap, 0, 4).astype(np.uint8)
+    cells = np.flatnonzero(rng.random(W * H) < density)
+    n = len(cells)
+    max_age = rng.integers(60, 101, n)
+    agents = np.stack([cells % W, cells // W, rng.integers(5, 26, n), rng.integers(1, 5, n), rng.integers(1, 7, n),
+                       (rng.random(n) * max_age).astype(np.int64), max_age], 1).astype(np.int32)
+    return cap, agents
 
 
 def nbody_initial(n, seed, r_merge=2e-3, margin=1e-5, max_tries=64):
