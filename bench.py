@@ -125,8 +125,8 @@ def oracle_config_rates():
     of life 64x64 (100 generations, one core), n-body 65,536 bodies in FP64
     (one step, rows split over all cores), the batched workload (every
     fourth of the 256 instances, 3 steps each after 3 warm-up steps, one
-    spawned process per core), and traffic 8192 x 4096 (3 steps after 1
-    warm-up step, one core)."""
+    spawned process per core), traffic 8192 x 4096 (3 steps after 1 warm-up
+    step, one core) and sugarscape 4096 x 4096 (2 steps after 1, one core)."""
     import multiprocessing
     import oracle as O
     from paper_1809_07444_gb300 import workloads as WL
@@ -158,6 +158,14 @@ def oracle_config_rates():
     dt = time.perf_counter() - t0
     out["traffic"] = {"car_updates_per_s": cars / dt, "cores": 1, "sample": "steps 2-4"}
     del tr
+    cap, ag = WL.sugarscape_initial(SUGAR_SIDE, SUGAR_SIDE, SEED)
+    sg = O.Sugarscape(SUGAR_SIDE, SUGAR_SIDE, cap, ag, SEED)
+    sg.step(1)
+    t0 = time.perf_counter()
+    sg.step(2)
+    dt = time.perf_counter() - t0
+    out["sugarscape"] = {"agent_steps_per_s": 2 * len(ag) / dt, "cores": 1, "sample": "steps 2-3"}
+    del sg
     sides = [int(s) for s in WL.batched_sides(256, 1)]
     jobs = [(sides[i], 1000 + i, 3, 3) for i in range(0, 256, 4)]
     t0 = time.perf_counter()
@@ -688,6 +696,53 @@ def bench_traffic(steps=30, warmup=3):
             "peak_kind": peak_kind, "launches_per_step": 4, "memsets_per_step": 1}
 
 
+SUGAR_SIDE = 4096
+
+
+def bench_sugarscape(steps=30, warmup=3):
+    """Sugarscape (Fig. 6f) on a 4096 x 4096 torus, 10% of the cells holding
+    an agent (1.68 M agents), L2 flushed before every step, CUDA events per
+    step. Object-updates: four do-alls visit every agent each step.
+    Algorithmic bytes per agent per step: A1 reads x, y, vision (12) and the
+    cells in sight (occupancy, capacity, harvest step: 6 bytes a cell, 4 x
+    vision cells, vision 3.5 on average) and writes the intent (4); A2 reads
+    six fields and the intent (28), writes sugar, age, dead (12) and its
+    cell's harvest step (capacity and step read, step written: 9); A3 and A4
+    read the dead flag (4 each)."""
+    import torch
+    from paper_1809_07444_gb300 import workloads as WL
+    from paper_1809_07444_gb300.apps import Sugarscape
+
+    cap, agents = WL.sugarscape_initial(SUGAR_SIDE, SUGAR_SIDE, SEED)
+    g = Sugarscape(SUGAR_SIDE, SUGAR_SIDE, cap, agents, SEED)
+    g.step(warmup)
+    torch.cuda.synchronize()
+    ev0 = g.events()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    evs = [_ev() for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record()
+        g.step(1)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    t = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    ev1 = g.events()
+    n = len(agents)
+    per_agent = (12 + 6 * 4 * 3.5 + 4) + (28 + 12 + 9) + 4 + 4
+    alg = n * per_agent * steps
+    peak, peak_kind = _peaks()
+    del g, flush
+    torch.cuda.empty_cache()
+    d = [b - a for a, b in zip(ev0, ev1)]
+    return {"workload": "sugarscape %dx%d, %d agents, steps %d-%d, L2 flushed before every step"
+                        % (SUGAR_SIDE, SUGAR_SIDE, n, warmup + 1, warmup + steps),
+            "ms_per_step": t * 1e3 / steps, "agent_steps_per_s": n * steps / t,
+            "object_updates_per_s": 4 * n * steps / t, "moves": d[0], "deaths": d[1] + d[2],
+            "algorithmic_gbs": alg / t / 1e9, "hbm_frac": alg / t / 1e9 / peak, "peak_gbs": peak,
+            "peak_kind": peak_kind, "launches_per_step": 5}
+
+
 def bench_space(heap_bytes=32 << 20, steps=100):
     """Fig. 8: the largest wa-tor torus a 32 MB heap runs for 100 steps
     without running out of memory, per tuning, with the peak bytes of live
@@ -872,6 +927,7 @@ LEGS = {
     "comparators": lambda a: bench_comparators(),
     "nbody": lambda a: bench_nbody(),
     "traffic": lambda a: bench_traffic(),
+    "sugarscape": lambda a: bench_sugarscape(),
     "served": lambda a: bench_served(a.served_seconds),
 }
 
@@ -940,6 +996,7 @@ def main():
         line["comparators"] = bench_comparators()
         line["nbody_65536"] = bench_nbody()
         line["traffic"] = bench_traffic()
+        line["sugarscape"] = bench_sugarscape()
         if args.served_seconds > 0:
             line["served"] = bench_served(args.served_seconds)
             # the same arrival process with jobs small enough to finish within

@@ -309,7 +309,8 @@ int dsr_traffic_destroy(dsr_traffic* t);
  * rand as for the wa-tor rules. Workspace (dsr_sugarscape_workspace_bytes,
  * which depends on the heap): per-cell capacity, occupancy, last-harvest
  * step and two claim words, a target per heap slot, and event counters.
- * Requires W, H >= 2 * vision_hi + 1, vision_hi <= 64, W * H < 2^31. */
+ * Requires W, H >= 2 * vision_hi + 1, vision_hi <= 64, W * H < 2^31; at
+ * most 2^28 - 2 steps (DSR_E_INVALID beyond). */
 typedef struct {
     int32_t W, H;
     uint64_t seed;
@@ -320,7 +321,8 @@ typedef struct dsr_sugarscape dsr_sugarscape;
 int dsr_sugarscape_types(dsr_type_desc* out /* 1 entry */);
 int dsr_sugarscape_workspace_bytes(const dsr_heap* heap, const dsr_sugarscape_params* p, size_t* out);
 /* cap_dev: device uint8[W * H]; agents0_dev: device int32[n_agents][7] =
- * (x, y, sugar, metabolism, vision, age, max_age) at distinct cells. */
+ * (x, y, sugar, metabolism, vision, age, max_age) at distinct cells. Both
+ * are read by kernels queued on `stream`: keep them until those have run. */
 int dsr_sugarscape_create(dsr_heap* heap, const dsr_sugarscape_params* p, const void* cap_dev,
                           const void* agents0_dev, int64_t n_agents, void* workspace_dev, void* stream,
                           dsr_sugarscape** out);

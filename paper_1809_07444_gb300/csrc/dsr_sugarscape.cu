@@ -19,7 +19,10 @@
 // Sugar grows back lazily: a cell keeps the step of its last harvest h, and
 // its sugar at the start of step t is min(cap, alpha * (t - h)) (cap if
 // never harvested), which equals applying G_alpha at the end of every step,
-// without a pass over all cells.
+// without a pass over all cells. A cell is one 32-bit word: bit 31 set
+// while an agent (alive or dead) is on it, bits 28-30 its capacity, bits
+// 0-27 its last harvest step + 1 (0: never), so that the choice reads one
+// word per cell in sight. Steps are limited to 2^28 - 2.
 #include <climits>
 
 #include "dsr_apps.h"
@@ -29,18 +32,16 @@ namespace {
 enum { AGENT = 0 };
 enum { F_X, F_Y, F_SUGAR, F_METAB, F_VISION, F_AGE, F_MAXAGE, F_DEAD, NF };
 enum { EV_MOVES, EV_STARVED, EV_AGED, EV_AWAY, EV_HARVEST, N_EV };
-constexpr int32_t NEVER = INT_MIN;       // harvest step of a cell never harvested
 constexpr uint32_t NO_CLAIM = 0xFFFFFFFFu;
+constexpr uint32_t OCC = 0x80000000u, CAP_SHIFT = 28, STEP_MASK = 0x0FFFFFFFu;
 
 struct SugarWs {
-    const uint8_t* cap;  // [n] capacity
-    uint8_t* occ;        // [n] 1 = an agent (alive or dead) is on the cell
-    int32_t* harvested;  // [n] step of the last harvest, NEVER if none
+    uint32_t* cell;      // [n] occupancy bit, capacity, last harvest step + 1
     uint32_t* claim;     // [n] A1 claims (lowest own cell wins), NO_CLAIM
     uint32_t* claim2;    // [n] A3 claims
     uint32_t* intent;    // [heap slots] A1 target of each agent slot
     dsr_u64 n_slots;
-    dsr_u64* events;     // [N_EV] cumulative
+    dsr_u64* events;     // [DSR_CTR_SLOTS][N_EV] cumulative, one row per SM slot
 };
 
 struct SugarArgs {
@@ -53,11 +54,11 @@ __device__ __forceinline__ int32_t* fld(const dsr_dev_heap& H, dsr_ref r, int f)
     return dsr_field<int32_t>(H, AGENT, r, f);
 }
 
-__device__ __forceinline__ int32_t sugar_at(const SugarArgs& a, int64_t c) {
-    const int32_t cap = a.ws.cap[c];
-    const int32_t h = a.ws.harvested[c];
-    if (h == NEVER) return cap;
-    const int64_t d = a.step - h;  // steps of growback since the harvest
+__device__ __forceinline__ int32_t sugar_of(const SugarArgs& a, uint32_t st) {
+    const int32_t cap = (int32_t)((st >> CAP_SHIFT) & 7u);
+    const uint32_t h1 = st & STEP_MASK;
+    if (h1 == 0) return cap;  // never harvested
+    const int64_t d = a.step - (int64_t)(h1 - 1);  // steps of growback since the harvest
     if (d >= cap) return cap;        // alpha >= 1: full again
     const int64_t v = (int64_t)a.p.alpha * d;
     return v < cap ? (int32_t)v : cap;
@@ -68,11 +69,16 @@ __device__ __forceinline__ int32_t draw(const SugarArgs& a, dsr_u64 stream, int6
     return lo + (int32_t)(r % (dsr_u64)(hi - lo + 1));
 }
 
-// Sum of a per-lane count over the calling lanes, one atomic per warp.
+// Sum of a per-lane count over the calling lanes, one atomic per warp, on
+// the row of the warp's SM (rows spread the atomics over many addresses).
 __device__ __forceinline__ void count_event(const SugarArgs& a, int k, unsigned v) {
     const unsigned act = __activemask();
     v = __reduce_add_sync(act, v);
-    if (v && dsr_lane() == (unsigned)(__ffs(act) - 1)) atomicAdd(a.ws.events + k, (dsr_u64)v);
+    if (v && dsr_lane() == (unsigned)(__ffs(act) - 1)) {
+        unsigned smid;
+        asm("mov.u32 %0, %%smid;" : "=r"(smid));
+        atomicAdd(a.ws.events + (smid % DSR_CTR_SLOTS) * N_EV + k, (dsr_u64)v);
+    }
 }
 
 struct MChoose {
@@ -81,34 +87,37 @@ struct MChoose {
         const int32_t x = *fld(H, self, F_X), y = *fld(H, self, F_Y), vision = *fld(H, self, F_VISION);
         const int32_t W = a.p.W, Hh = a.p.H;
         const int64_t own = (int64_t)y * W + x;
-        int32_t best = sugar_at(a, own), best_d = 0, k = 1;
-        int64_t cand[4] = {own, own, own, own};
+        int32_t best = sugar_of(a, a.ws.cell[own]), best_d = 0;
+        unsigned dirs = 0;  // directions (bit 0 N, 1 E, 2 S, 3 W) of the candidates at distance best_d
         for (int32_t d = 1; d <= vision; ++d) {
+            const int32_t yn = y - d < 0 ? y - d + Hh : y - d, ys = y + d >= Hh ? y + d - Hh : y + d;
+            const int32_t xe = x + d >= W ? x + d - W : x + d, xw = x - d < 0 ? x - d + W : x - d;
+            const uint32_t st[4] = {a.ws.cell[(int64_t)yn * W + x], a.ws.cell[(int64_t)y * W + xe],
+                                    a.ws.cell[(int64_t)ys * W + x], a.ws.cell[(int64_t)y * W + xw]};
 #pragma unroll
-            for (int dir = 0; dir < 4; ++dir) {  // N, E, S, W
-                int32_t cx = x, cy = y;
-                if (dir == 0) cy = y - d < 0 ? y - d + Hh : y - d;
-                if (dir == 1) cx = x + d >= W ? x + d - W : x + d;
-                if (dir == 2) cy = y + d >= Hh ? y + d - Hh : y + d;
-                if (dir == 3) cx = x - d < 0 ? x - d + W : x - d;
-                const int64_t c = (int64_t)cy * W + cx;
-                if (a.ws.occ[c]) continue;
-                const int32_t v = sugar_at(a, c);
+            for (int dir = 0; dir < 4; ++dir) {
+                if (st[dir] & OCC) continue;
+                const int32_t v = sugar_of(a, st[dir]);
                 if (v > best) {
                     best = v;
                     best_d = d;
-                    k = 1;
-                    cand[0] = c;
+                    dirs = 1u << dir;
                 } else if (v == best && d == best_d) {
-                    cand[k++] = c;
+                    dirs |= 1u << dir;
                 }
             }
         }
-        int64_t t = cand[0];
-        if (k > 1) {
-            const dsr_u64 r = dsr_rand(a.p.seed, 12, (dsr_u64)a.step, (dsr_u64)own) >> 32;
-            const int32_t pick = (int32_t)(r % (dsr_u64)k);
-            t = pick == 1 ? cand[1] : pick == 2 ? cand[2] : pick == 3 ? cand[3] : cand[0];
+        int64_t t = own;
+        if (best_d > 0) {
+            const int k = __popc(dirs);
+            int pick = 0;
+            if (k > 1) pick = (int)((dsr_rand(a.p.seed, 12, (dsr_u64)a.step, (dsr_u64)own) >> 32) % (dsr_u64)k);
+            const int dir = dsr_nth_bit(dirs, pick);
+            const int32_t d = best_d;
+            if (dir == 0) t = (int64_t)(y - d < 0 ? y - d + Hh : y - d) * W + x;
+            if (dir == 1) t = (int64_t)y * W + (x + d >= W ? x + d - W : x + d);
+            if (dir == 2) t = (int64_t)(y + d >= Hh ? y + d - Hh : y + d) * W + x;
+            if (dir == 3) t = (int64_t)y * W + (x - d < 0 ? x - d + W : x - d);
         }
         if (dsr_check(self < a.ws.n_slots, H.err, H.dbg, 8, self)) a.ws.intent[self] = (uint32_t)t;
         if (t != own) atomicMin(a.ws.claim + t, (uint32_t)own);
@@ -126,15 +135,16 @@ struct MMove {
         unsigned moved = 0;
         if (t != own && a.ws.claim[t] == (uint32_t)own) {
             a.ws.claim[t] = NO_CLAIM;  // only the winner matches, so the reset cannot make a loser win
-            a.ws.occ[own] = 0;
-            a.ws.occ[t] = 1;
+            a.ws.cell[own] &= ~OCC;     // this agent is the only writer of both cells in this do-all
+            a.ws.cell[t] |= OCC;
             *fld(H, self, F_X) = (int32_t)(t % a.p.W);
             *fld(H, self, F_Y) = (int32_t)(t / a.p.W);
             c = t;
             moved = 1;
         }
-        const int32_t got = sugar_at(a, c);
-        a.ws.harvested[c] = (int32_t)a.step;
+        const uint32_t st = a.ws.cell[c];
+        const int32_t got = sugar_of(a, st);
+        a.ws.cell[c] = (st & ~STEP_MASK) | (uint32_t)(a.step + 1);
         const int32_t sugar = *fld(H, self, F_SUGAR) + got - *fld(H, self, F_METAB);
         const int32_t age = *fld(H, self, F_AGE) + 1;
         *fld(H, self, F_SUGAR) = sugar;
@@ -159,7 +169,7 @@ struct MReplaceClaim {
         if (!*fld(H, self, F_DEAD)) return;
         const int64_t own = (int64_t)*fld(H, self, F_Y) * a.p.W + *fld(H, self, F_X);
         const int64_t c = replacement_cell(a, own);
-        if (!a.ws.occ[c]) atomicMin(a.ws.claim2 + c, (uint32_t)own);
+        if (!(a.ws.cell[c] & OCC)) atomicMin(a.ws.claim2 + c, (uint32_t)own);
     }
 };
 
@@ -173,14 +183,14 @@ struct MReplace {
         unsigned away = 0;
         if (a.ws.claim2[c] == (uint32_t)own) {
             a.ws.claim2[c] = NO_CLAIM;
-            a.ws.occ[own] = 0;
-            a.ws.occ[c] = 1;
+            a.ws.cell[own] &= ~OCC;
+            a.ws.cell[c] |= OCC;
             at = c;
             away = 1;
         }
         count_event(a, EV_AWAY, away);
+        dsr_delete(H, self);  // first, so that the new agent may take the slot
         const dsr_ref r = dsr_new(H, AGENT);
-        dsr_delete(H, self);
         if (r == DSR_NULL) return;  // out of memory: DSR_ERR_OOM is set
         *fld(H, r, F_X) = (int32_t)(at % a.p.W);
         *fld(H, r, F_Y) = (int32_t)(at / a.p.W);
@@ -206,19 +216,20 @@ __global__ void k_sugar_init(const __grid_constant__ dsr_dev_heap H, const int32
         if (r == DSR_NULL) continue;
         for (int f = 0; f < 7; ++f) *fld(H, r, f) = src[f];
         *fld(H, r, F_DEAD) = 0;
-        ws.occ[(int64_t)src[1] * W + src[0]] = 1;
+        ws.cell[(int64_t)src[1] * W + src[0]] |= OCC;
     }
 }
 
-__global__ void k_sugar_fill(int32_t* harvested, int64_t n) {
+// Cells from the capacities: unoccupied, never harvested.
+__global__ void k_sugar_fill(uint32_t* cell, const uint8_t* cap, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        harvested[i] = NEVER;
+        cell[i] = (uint32_t)(cap[i] & 7u) << CAP_SHIFT;
 }
 
 __global__ void k_sugar_read(SugarArgs a, int32_t* out) {
     const int64_t n = (int64_t)a.p.W * a.p.H;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = sugar_at(a, i);
+        out[i] = sugar_of(a, a.ws.cell[i]);
 }
 
 const int kAgentFields[NF] = {4, 4, 4, 4, 4, 4, 4, 4};
@@ -241,18 +252,14 @@ size_t r256(size_t x) { return (x + 255) / 256 * 256; }
 
 size_t ws_bytes(const dsr_sugarscape_params& p, dsr_u64 slots) {
     const size_t n = (size_t)p.W * p.H;
-    return 2 * r256(n) + 3 * r256(n * 4) + r256(slots * 4) + 256;
+    return 3 * r256(n * 4) + r256(slots * 4) + r256(DSR_CTR_SLOTS * N_EV * 8);
 }
 
 SugarWs carve(void* base, const dsr_sugarscape_params& p, dsr_u64 slots) {
     const size_t n = (size_t)p.W * p.H;
     uint8_t* q = static_cast<uint8_t*>(base);
     SugarWs w;
-    w.cap = q;
-    q += r256(n);
-    w.occ = q;
-    q += r256(n);
-    w.harvested = reinterpret_cast<int32_t*>(q);
+    w.cell = reinterpret_cast<uint32_t*>(q);
     q += r256(n * 4);
     w.claim = reinterpret_cast<uint32_t*>(q);
     q += r256(n * 4);
@@ -299,18 +306,16 @@ extern "C" int dsr_sugarscape_create(dsr_heap* heap, const dsr_sugarscape_params
     g->args.p = *p;
     g->args.step = 0;
     SugarWs& w = g->args.ws;
-    cudaError_t e = cudaMemcpyAsync(const_cast<uint8_t*>(w.cap), cap_dev, (size_t)n, cudaMemcpyDeviceToDevice, s);
-    if (!e) e = cudaMemsetAsync(w.occ, 0, (size_t)n, s);
-    if (!e) e = cudaMemsetAsync(w.claim, 0xFF, (size_t)n * 4, s);
+    cudaError_t e = cudaMemsetAsync(w.claim, 0xFF, (size_t)n * 4, s);
     if (!e) e = cudaMemsetAsync(w.claim2, 0xFF, (size_t)n * 4, s);
-    if (!e) e = cudaMemsetAsync(w.events, 0, 256, s);
+    if (!e) e = cudaMemsetAsync(w.events, 0, DSR_CTR_SLOTS * N_EV * 8, s);
     if (e) {
         dsr__set_cuda_error(e, "dsr_sugarscape_create");
         delete g;
         return DSR_E_CUDA;
     }
     const int ctas = heap->sm_count * 4;
-    k_sugar_fill<<<ctas, 256, 0, s>>>(w.harvested, n);
+    k_sugar_fill<<<ctas, 256, 0, s>>>(w.cell, static_cast<const uint8_t*>(cap_dev), n);
     if (n_agents) {
         int64_t c2 = (n_agents + 255) / 256;
         if (c2 > heap->sm_count * 8) c2 = heap->sm_count * 8;
@@ -327,7 +332,7 @@ extern "C" int dsr_sugarscape_create(dsr_heap* heap, const dsr_sugarscape_params
 }
 
 extern "C" int dsr_sugarscape_step(dsr_sugarscape* g, int n_steps, void* stream) {
-    if (!g || n_steps < 0) return DSR_E_INVALID;
+    if (!g || n_steps < 0 || g->args.step + n_steps > (int64_t)STEP_MASK - 1) return DSR_E_INVALID;
     cudaStream_t s = dsr__stream(stream);
     for (int i = 0; i < n_steps; ++i) {
         // A1-A4 visit the same live set (nothing is created or deleted before
@@ -345,11 +350,16 @@ extern "C" int dsr_sugarscape_step(dsr_sugarscape* g, int n_steps, void* stream)
 extern "C" int dsr_sugarscape_events(dsr_sugarscape* g, void* stream, uint64_t* out) {
     if (!g || !out) return DSR_E_INVALID;
     cudaStream_t s = dsr__stream(stream);
-    cudaError_t e = cudaMemcpyAsync(out, g->args.ws.events, N_EV * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    static thread_local dsr_u64 rows[DSR_CTR_SLOTS * N_EV];
+    cudaError_t e = cudaMemcpyAsync(rows, g->args.ws.events, sizeof rows, cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
     if (e) {
         dsr__set_cuda_error(e, "dsr_sugarscape_events");
         return DSR_E_CUDA;
+    }
+    for (int k = 0; k < N_EV; ++k) {
+        out[k] = 0;
+        for (int r = 0; r < DSR_CTR_SLOTS; ++r) out[k] += rows[r * N_EV + k];
     }
     return DSR_OK;
 }
