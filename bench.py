@@ -600,7 +600,8 @@ def bench_gol(W=64, gens=100, reps=3):
         del g
     lat.sort()
     return {"workload": "game of life %dx%d, %d generations" % (W, W, gens), "gens_per_s": statistics.median(rates),
-            "gen_ms_p50": lat[len(lat) // 2], "gen_ms_p99": lat[int(len(lat) * 0.99)], "launches_per_gen": 6}
+            "gen_ms_p50": lat[len(lat) // 2], "gen_ms_p99": lat[int(len(lat) * 0.99)], "kernels_per_gen": 6,
+            "graph": "one graph launch per generation"}
 
 
 def bench_comparators(steps=50, warmup=5):

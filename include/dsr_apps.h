@@ -42,6 +42,9 @@ int dsr_gol_workspace_bytes(int W, int H, size_t* out);
  * initial Alive objects inside the heap. */
 int dsr_gol_create(dsr_heap* heap, int W, int H, const void* alive0_dev, void* workspace_dev, void* stream,
                    dsr_gol** out);
+/* The first call captures one generation (its six launches) into a CUDA
+ * graph on a stream of its own; every generation is then one graph launch
+ * on `stream`. Make the first call outside any stream capture. */
 int dsr_gol_step(dsr_gol* g, int n_gen, void* stream);
 int dsr_gol_destroy(dsr_gol* g);
 

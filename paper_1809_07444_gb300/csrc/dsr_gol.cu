@@ -109,6 +109,8 @@ bool heap_matches(const dsr_heap* h) {
 struct dsr_gol {
     dsr_heap* heap;
     GolArgs args;
+    cudaStream_t capture = nullptr;   // stream the generation is captured on
+    cudaGraphExec_t exec = nullptr;   // one generation (6 launches) as a graph
 };
 
 extern "C" int dsr_gol_types(dsr_type_desc* out) {
@@ -146,19 +148,55 @@ extern "C" int dsr_gol_create(dsr_heap* heap, int W, int H, const void* alive0_d
     return DSR_OK;
 }
 
+static int issue_generation(dsr_gol* g, cudaStream_t s) {
+    int rc = dsr__doall<MCount>(g->heap, CELL, g->args, s);
+    if (!rc) rc = dsr__doall<MDie>(g->heap, ALIVE, g->args, s);
+    if (!rc) rc = dsr__doall<MBirth>(g->heap, CELL, g->args, s);
+    return rc;
+}
+
+// A generation's six launches take a few microseconds each on a 64 x 64
+// board, so the generation is captured once into a CUDA graph (its kernel
+// arguments never change) and replayed: one launch per generation.
 extern "C" int dsr_gol_step(dsr_gol* g, int n_gen, void* stream) {
     if (!g || n_gen < 0) return DSR_E_INVALID;
     cudaStream_t s = dsr__stream(stream);
+    if (!g->exec && n_gen > 0) {
+        cudaError_t e = g->capture ? cudaSuccess : cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
+        cudaGraph_t graph = nullptr;
+        if (!e) e = cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal);
+        if (e) {
+            dsr__set_cuda_error(e, "dsr_gol_step capture");
+            return DSR_E_CUDA;
+        }
+        const int rc = issue_generation(g, g->capture);
+        e = cudaStreamEndCapture(g->capture, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (!e) e = cudaGraphInstantiate(&g->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e) {
+            dsr__set_cuda_error(e, "dsr_gol_step instantiate");
+            g->exec = nullptr;
+            return DSR_E_CUDA;
+        }
+    }
     for (int i = 0; i < n_gen; ++i) {
-        int rc = dsr__doall<MCount>(g->heap, CELL, g->args, s);
-        if (!rc) rc = dsr__doall<MDie>(g->heap, ALIVE, g->args, s);
-        if (!rc) rc = dsr__doall<MBirth>(g->heap, CELL, g->args, s);
-        if (rc) return rc;
+        const cudaError_t e = cudaGraphLaunch(g->exec, s);
+        if (e) {
+            dsr__set_cuda_error(e, "dsr_gol_step launch");
+            return DSR_E_CUDA;
+        }
     }
     return DSR_OK;
 }
 
 extern "C" int dsr_gol_destroy(dsr_gol* g) {
+    if (!g) return DSR_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->capture) cudaStreamDestroy(g->capture);
     delete g;
     return DSR_OK;
 }
