@@ -125,3 +125,20 @@ def test_bitmap_fanout_rejects_bad_widths_and_too_many_levels(lib):
     # 16-bit containers reach DSR_MAX_LEVELS (6) levels at 16^6 blocks
     assert _plan(lib, [[4, 4]], 16 ** 6, fanout=16)[0] == 0
     assert _plan(lib, [[4, 4]], 16 ** 6 + 1, fanout=16)[0] == L.E_INVALID
+
+
+def test_traffic_parameters_are_checked_on_the_host(lib):
+    from paper_1809_07444_gb300 import _lib as L
+    ok = L.TrafficParams(16, 100, 5, 5, 0, 0, 1, 1 << 30, 1 << 31)
+    n = C.c_size_t(0)
+    assert lib.dsr_traffic_workspace_bytes(C.byref(ok), C.byref(n)) == 0
+    assert n.value == 2 * ((16 * 100 + 255) // 256 * 256)
+    bad = [
+        L.TrafficParams(16, 5, 5, 5, 0, 0, 1, 0, 0),           # road no longer than vmax
+        L.TrafficParams(16, 100, 0, 0, 0, 0, 1, 0, 0),         # vmax 0
+        L.TrafficParams(16, 100, 5, 6, 0, 0, 1, 0, 0),         # entry faster than vmax
+        L.TrafficParams(0, 100, 5, 5, 0, 0, 1, 0, 0),          # no road
+        L.TrafficParams(16, 100, 5, 5, 0, 0, 1, (1 << 32) + 1, 0),  # probability above 1
+    ]
+    for p in bad:
+        assert lib.dsr_traffic_workspace_bytes(C.byref(p), C.byref(n)) == L.E_INVALID
