@@ -1,6 +1,7 @@
 """The checked build (libdsr_check.so: device-side bounds and handle checks
 that record the first failure and skip the access, short retry caps) runs
-the applications to the same results with no failed check. Each case runs
+the applications (game of life, wa-tor, batched wa-tor, traffic,
+sugarscape) to the same results with no failed check. Each case runs
 in a child process, because a process loads one of the two libraries."""
 import os
 import subprocess
@@ -21,7 +22,7 @@ import oracle as O
 from paper_1809_07444_gb300 import _lib as L
 assert L.LIB_PATH.endswith("libdsr_check.so"), L.LIB_PATH
 from paper_1809_07444_gb300 import workloads as WL
-from paper_1809_07444_gb300.apps import Gol, Wator, WatorBatch
+from paper_1809_07444_gb300.apps import Gol, Wator, WatorBatch, Traffic, Sugarscape
 from helpers import check_invariants
 
 g, gr = Gol(64, 64, WL.gol_initial(64, 64, 1)), O.Gol(64, 64, WL.gol_initial(64, 64, 1))
@@ -43,7 +44,17 @@ for _ in range(20):
     for slot, r in refs:
         r.step(1)
         assert b.hash(slot) == r.hash()
-for hp in (g.heap, w.heap):
+v0 = WL.traffic_initial(37, 211, 3, 0.3)
+t, tr = Traffic(37, 211, v0, 5), O.Traffic(37, 211, v0, 5)
+for _ in range(30):
+    t.step(1); tr.step(1)
+    assert t.hash() == tr.hash()
+cap, ag = WL.sugarscape_initial(37, 29, 3, 0.3)
+sg, sr = Sugarscape(37, 29, cap, ag, 7), O.Sugarscape(37, 29, cap, ag, 7)
+for _ in range(30):
+    sg.step(1); sr.step(1)
+    assert sg.hash() == sr.hash()
+for hp in (g.heap, w.heap, t.heap, sg.heap):
     st = hp.stats()
     assert st["error_flags"] == 0, st
     check_invariants(hp)
