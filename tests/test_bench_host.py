@@ -1,0 +1,59 @@
+"""CPU checks of the benchmark's host logic: the algorithmic byte model of
+the wa-tor phases, the choice of the roofline kernel, the reference arm's
+JSON line (the oracle, run on the host), and the space-efficiency bisection
+on a synthetic predicate."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_phase_bytes_follow_the_documented_model():
+    # per visited object + 12 per listed block + per event
+    assert bench.phase_bytes("F1", 1000, 20, 0, 0, 0) == 68 * 1000 + 12 * 20
+    assert bench.phase_bytes("F2", 1000, 20, 300, 100, 0) == 20 * 1000 + 12 * 20 + 28 * 300 + 16 * 100
+    assert bench.phase_bytes("S0", 50, 2, 0, 0, 7) == 8 * 50 + 12 * 2 + 16 * 7
+    assert bench.phase_bytes("S2", 50, 2, 30, 5, 9) == 20 * 50 + 12 * 2 + 36 * 30 + 8 * 9 + 20 * 5
+
+
+def test_roofline_takes_the_slowest_method_kernel():
+    phases = {p: {"method_ms_per_step": 0.01, "gbs": 100.0, "kernel": "k" + p, "bytes_per_launch": 1.0}
+              for p in bench.PHASES}
+    phases["S1"].update(method_ms_per_step=0.2, gbs=500.0)
+    r = bench.roofline(phases, 1000.0, "measured")
+    assert r["phase"] == "S1" and r["achieved"] == 500.0 and r["frac"] == 0.5
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["kernel"] == "kS1"
+
+
+def test_reference_arm_prints_the_oracle_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
+    assert line["value"] > 0 and line["steps"] == 2 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.parametrize("limit", [17, 40, 100, 333])
+def test_space_bisection_finds_the_largest_fitting_side(limit):
+    pytest.importorskip("torch")
+    from paper_1809_07444_gb300 import space
+
+    calls = []
+
+    def fits(side):
+        calls.append(side)
+        return side <= limit, side * 10
+
+    side, peak = space._bisect(fits)
+    assert side == limit and peak == limit * 10
+    assert len(calls) < 40
