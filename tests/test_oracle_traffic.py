@@ -113,3 +113,14 @@ def test_invariants_on_random_open_roads():
         assert src[:, 1].sum() == entered
         assert (src[:, 1] + src[:, 2] <= s + 1).all()
         assert ev[2] <= n - ev[0] + ev[1] and ev[3] <= vmax * ev[2]
+
+
+@pytest.mark.parametrize("p", [0.0, 0.25, 0.5, 1.0 / 3.0, 0.999999, 1.0])
+def test_probability_thresholds_agree_with_the_binding(p):
+    # both sides turn a probability into the 32-bit threshold on their own;
+    # the GPU path's draws are compared against the binding's value
+    pytest.importorskip("torch")
+    from paper_1809_07444_gb300.apps import prob_threshold
+
+    assert O.prob_threshold(p) == prob_threshold(p)
+    assert O.prob_threshold(p) == int(p * 2 ** 32) if p < 1 else O.prob_threshold(p) == 2 ** 32
