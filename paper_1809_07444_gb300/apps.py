@@ -514,6 +514,8 @@ class Traffic:
 
     def __init__(self, R, L, v0, seed, vmax=5, p=0.25, alpha=0.5, v_entry=None, periodic=False,
                  heap_bytes=None, tuning=None, stream=None):
+        if np.asarray(v0).size != R * L:
+            raise ValueError("v0 must have R * L cells")
         self.lib = _LIBMOD.load()
         self.R, self.L, self.periodic = R, L, bool(periodic)
         self.params = _LIBMOD.TrafficParams(R, L, vmax, vmax if v_entry is None else v_entry, int(bool(periodic)), 0,
@@ -577,11 +579,18 @@ class Sugarscape:
 
     def __init__(self, W, H, cap, agents0, seed, alpha=1, endow=(5, 25), metab=(1, 4), vision=(1, 6),
                  max_age=(60, 100), heap_bytes=None, tuning=None, stream=None):
+        a0 = np.ascontiguousarray(agents0, dtype=np.int32).reshape(-1, 7)
+        if len(a0):  # the kernels assume one agent per cell, on the torus
+            if (a0[:, 0] < 0).any() or (a0[:, 0] >= W).any() or (a0[:, 1] < 0).any() or (a0[:, 1] >= H).any():
+                raise ValueError("agent outside the W x H torus")
+            if len(np.unique(a0[:, 1].astype(np.int64) * W + a0[:, 0])) != len(a0):
+                raise ValueError("two agents on one cell")
+        if np.asarray(cap).size != W * H:
+            raise ValueError("cap must have W * H cells")
         self.lib = L.load()
         self.W, self.H = W, H
         self.params = L.SugarscapeParams(W, H, seed, alpha, endow[0], endow[1], metab[0], metab[1], vision[0],
                                          vision[1], max_age[0], max_age[1])
-        a0 = np.ascontiguousarray(agents0, dtype=np.int32).reshape(-1, 7)
         if heap_bytes is None:
             heap_bytes = heap_bytes_for_blocks(SUGAR_TYPES, _blocks_for(len(a0) + 64, [64], tuning=tuning), tuning)
         self.heap = Heap(SUGAR_TYPES, heap_bytes, names=["Agent"], tuning=tuning, stream=stream)
