@@ -112,9 +112,8 @@ __device__ __forceinline__ dsr_u64 dsr_atom_cas_acq_rel(dsr_u64* p, dsr_u64 cmp,
     return old;
 }
 __device__ __forceinline__ void dsr_atom_exch_release(dsr_u64* p, dsr_u64 v) {
-    dsr_u64 old;
+    [[maybe_unused]] dsr_u64 old;  // the exchange's result is not needed
     asm volatile("atom.release.gpu.global.exch.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
-    (void)old;
 }
 
 /* Device self-checks, compiled in with -DDSR_DEVICE_CHECKS: a failed check

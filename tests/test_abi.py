@@ -142,3 +142,15 @@ def test_traffic_parameters_are_checked_on_the_host(lib):
     ]
     for p in bad:
         assert lib.dsr_traffic_workspace_bytes(C.byref(p), C.byref(n)) == L.E_INVALID
+
+
+def test_a_user_method_compiles_against_the_public_headers(tmp_path):
+    # include/dsr_device.cuh is the interface for methods written outside the
+    # library: a method struct, dsr_new / dsr_field, and the do-all kernel
+    from paper_1809_07444_gb300 import build_ext
+    import subprocess
+    src = os.path.join(ROOT, "tests", "user_method.cu")
+    r = subprocess.run([build_ext.nvcc(), "-c", src, "-o", str(tmp_path / "user_method.o"), "-std=c++17",
+                        "-I", os.path.join(ROOT, "include"), "-Werror", "all-warnings"] + build_ext.ARCH,
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
