@@ -1,11 +1,10 @@
 """Served form on the GPU: jobs admitted by free bytes and stepped together are each bit-exact vs the oracle,
 and a job's result is the same alone as in the mix."""
-import numpy as np
 import pytest
 
 import oracle as O
 from paper_1809_07444_gb300 import workloads as WL
-from paper_1809_07444_gb300.serve import GOL, WATOR, Server, summarize
+from paper_1809_07444_gb300.serve import WATOR, Server, summarize
 
 pytestmark = pytest.mark.gpu
 
