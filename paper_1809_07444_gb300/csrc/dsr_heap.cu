@@ -253,7 +253,8 @@ __global__ void __launch_bounds__(256) k_scan(const __grid_constant__ dsr_dev_he
 }
 
 // Statistics: out[0] free blocks; out[1 + 3T + {0,1,2}] allocated blocks,
-// active blocks, live objects of type T.
+// active blocks, live objects of type T. Bit b of leaf word i stands for
+// block (i << shift) + b, shift = log2 of the bitmap fan-out (64, 32 or 16).
 __global__ void k_stats(const __grid_constant__ dsr_dev_heap H, dsr_u64* out) {
     const dsr_u64 tid = (dsr_u64)blockIdx.x * blockDim.x + threadIdx.x;
     const dsr_u64 stride = (dsr_u64)gridDim.x * blockDim.x;
@@ -264,6 +265,7 @@ __global__ void k_stats(const __grid_constant__ dsr_dev_heap H, dsr_u64* out) {
     for (int t = 0; t < H.n_types; ++t) {
         dsr_u64 na = 0, nact = 0, live = 0;
         const dsr_u64 v = H.valid[t];
+        const unsigned sh = H.alloc_bm[t].shift;
         for (dsr_u64 i = tid; i < nw; i += stride) {
             dsr_u64 a = H.alloc_bm[t].lvl[0][i];
             na += __popcll(a);
@@ -271,7 +273,7 @@ __global__ void k_stats(const __grid_constant__ dsr_dev_heap H, dsr_u64* out) {
             while (a) {
                 const int b = __ffsll((long long)a) - 1;
                 a &= a - 1;
-                live += __popcll(v & ~H.obj[i * 64 + b]);
+                live += __popcll(v & ~H.obj[(i << sh) + (dsr_u64)b]);
             }
         }
         if (na) atomicAdd(out + 1 + 3 * t, na);

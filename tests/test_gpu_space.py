@@ -2,7 +2,9 @@
 fixed heap runs without running out of memory."""
 import pytest
 
+import oracle as O
 from paper_1809_07444_gb300 import space
+from paper_1809_07444_gb300 import workloads as WL
 
 pytestmark = pytest.mark.gpu
 
@@ -13,6 +15,9 @@ def test_max_side_fits_and_the_next_sizes_do_not():
     assert side > 16
     ok, peak2 = space.wator_fits(side, heap, steps)
     assert ok and peak2 == peak  # deterministic
+    for tun in ({"fanout": 16}, {"fanout": 32, "cap_min": 32}):
+        ok3, peak3 = space.wator_fits(side, heap * 2, steps, tuning=tun)
+        assert ok3 and peak3 == peak  # live counts do not depend on the fan-out
     assert 0 < peak <= heap
     # a clearly larger torus does not fit the same heap
     assert not space.wator_fits(int(side * 1.25) + 2, heap, steps)[0]
@@ -31,6 +36,18 @@ def test_experiment_reports_every_setting():
     assert [r["tuning"] for r in rows[:3]] == ["default", {"cap_min": 32}, {"fanout": 16}]
     assert [r["allocator"] for r in rows] == ["dsr"] * 3 + ["BitmapAlloc"] * 2
     assert all(r["max_side"] > 0 and 0 < r["efficiency"] <= 1 for r in rows)
+    # every row's peak live bytes is the oracle's peak over the same run
+    # (the live counts come from dsr_heap_stats, at fan-out 64 and 16)
+    for r in rows:
+        side = r["max_side"]
+        ref = O.Wator(side, side, WL.wator_initial(side, side, 1), seed=1)
+        peak = 0
+        for _ in range(out["steps"]):
+            ref.step(1)
+            f, sh = ref.counts()
+            peak = max(peak, f * space.OBJECT_BYTES[0] + sh * space.OBJECT_BYTES[1])
+        assert r["peak_live_bytes"] == peak, (r, peak)
+        assert r["efficiency"] == peak / out["heap_bytes"]
 
 
 def test_bitmap_capacities_fill_the_heap():

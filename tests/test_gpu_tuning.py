@@ -11,7 +11,7 @@ from paper_1809_07444_gb300 import workloads as WL
 from paper_1809_07444_gb300.apps import Gol, Wator, WatorBatch
 from paper_1809_07444_gb300.heap import Heap, heap_bytes_for_blocks
 
-from helpers import check_invariants
+from helpers import check_invariants, check_stats
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +53,9 @@ def test_wator_under_tuning(tun):
     assert np.array_equal(fg, fr) and np.array_equal(sg, sr)
     assert gpu.heap.stats()["error_flags"] == 0
     check_invariants(gpu.heap, list(ref.counts()))
+    # dsr_heap_stats at this fan-out: its live counts are the oracle's
+    assert tuple(gpu.counts()) == tuple(ref.counts())
+    check_stats(gpu.heap)
 
 
 @pytest.mark.parametrize("tun", TUNINGS[:2])
@@ -74,6 +77,8 @@ def test_batched_wator_under_tuning(tun):
         assert hp.layout().fanout == tun["fanout"]
         assert hp.stats()["error_flags"] == 0
         check_invariants(hp, list(ref.counts()))
+        assert tuple(b.counts(slot)) == tuple(ref.counts())
+        check_stats(hp)
 
 
 @pytest.mark.parametrize("fanout", [32, 16])
@@ -88,11 +93,13 @@ def test_allocator_many_levels_narrow_fanout(fanout):
     h.bench_alloc(refs, 2, 3)
     live = check_invariants(h)
     assert live.sum() == n
+    assert sum(check_stats(h)["live_objects"]) == n
     r = refs.cpu().numpy().view(np.uint64)
     assert len(np.unique(r)) == n
     from paper_1809_07444_gb300 import _lib as L
     h.parallel_do(0, L.METHOD_DELETE_IF, L.DeleteIfArgs(3, 1))
     check_invariants(h)
+    check_stats(h)
     for t in range(2):
         h.parallel_do(t, L.METHOD_DELETE_IF, L.DeleteIfArgs(1, 0))  # everything left
     st = h.stats()
@@ -106,3 +113,36 @@ def test_autotuner_picks_a_runnable_setting_on_a_small_batch():
     best, v, table = AT.search(AT.wator_batch_measure(sides, seeds, steps=3, warmup=1), space)
     assert v > 0 and all(best[k] in space[k] for k in space)
     assert all(x is not None and x > 0 for x in table.values())
+
+
+@pytest.mark.parametrize("fanout", [64, 32, 16])
+def test_heap_stats_match_block_states_at_every_fanout(fanout):
+    # dsr_heap_stats against the counts the block states of Fig. 2 give for
+    # the same snapshot, on a block count that is not a multiple of
+    # 64 * fanout (a ragged last leaf word), after allocation, churn and
+    # partial and complete deletion
+    import ctypes as C
+
+    from paper_1809_07444_gb300 import _lib as L
+
+    types = [[4, 4], [4, 4, 4, 4], [4]]
+    tun = {"fanout": fanout}
+    h = Heap(types, heap_bytes_for_blocks(types, 8192 + 777, tun), tuning=tun)
+    M = h.layout().n_blocks
+    assert M >= 8192 + 777 and M % (64 * fanout) != 0
+    n = 90_000
+    refs = torch.empty(n, dtype=torch.int64, device="cuda")
+    h.bench_alloc(refs, 3, 11)
+    st = check_stats(h)
+    assert sum(st["live_objects"]) == n and st["error_flags"] == 0
+    replaced = torch.zeros(1, dtype=torch.int64, device="cuda")
+    L.check(h.lib.dsr_bench_churn(h.handle, n, 3, 12, C.c_void_p(refs.data_ptr()), C.c_void_p(replaced.data_ptr()),
+                                  None), "dsr_bench_churn")
+    st = check_stats(h)
+    assert sum(st["live_objects"]) == n and int(replaced.item()) > 0
+    h.parallel_do(1, L.METHOD_DELETE_IF, L.DeleteIfArgs(3, 1))
+    check_stats(h)
+    for t in range(3):
+        h.parallel_do(t, L.METHOD_DELETE_IF, L.DeleteIfArgs(1, 0))
+    st = check_stats(h)
+    assert st["free_blocks"] == M and st["live_objects"] == [0, 0, 0] and st["error_flags"] == 0

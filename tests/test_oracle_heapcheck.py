@@ -136,3 +136,24 @@ def test_flags_each_planted_violation():
     def structure(g):
         g["words_per_level"] = g["words_per_level"][:1]
     plant(structure, O.INV_STRUCTURE)
+
+
+@pytest.mark.parametrize("width", [64, 32, 16])
+def test_expected_stats_counts_block_states(width):
+    # the block and object counts the GPU statistics are checked against,
+    # on a synthetic consistent heap whose free blocks partly keep the type
+    # byte of their last use (a reclaimed block: type T, no free slot, free)
+    from helpers import expected_stats
+    M, caps = 64 * width + 333, (64, 40)
+    h, live = _heap(5, M, caps=caps, width=width)
+    rng = np.random.default_rng(9)
+    free = h["block_type"] == 0xFF
+    reused = free & (rng.random(M) < 0.5)
+    h["block_type"][reused] = rng.integers(0, 2, int(reused.sum()))
+    st = expected_stats(h)
+    assert st["free_blocks"] == int(free.sum())
+    for t, c in enumerate(caps):
+        mine = (h["block_type"] == t) & ~free
+        assert st["allocated_blocks"][t] == int(mine.sum())
+        assert st["active_blocks"][t] == int((mine & (h["obj_free"] != 0)).sum())
+        assert st["live_objects"][t] == int(live[t])
