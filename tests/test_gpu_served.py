@@ -1,10 +1,11 @@
 """Served form on the GPU: jobs admitted by free bytes and stepped together are each bit-exact vs the oracle,
 and a job's result is the same alone as in the mix."""
+import numpy as np
 import pytest
 
 import oracle as O
 from paper_1809_07444_gb300 import workloads as WL
-from paper_1809_07444_gb300.serve import WATOR, Server, summarize
+from paper_1809_07444_gb300.serve import GOL, WATOR, Server, summarize
 
 pytestmark = pytest.mark.gpu
 
@@ -59,3 +60,66 @@ def test_poisson_arrivals_in_real_time():
     for d in rep["done"]:
         assert d["admitted"] >= d["arrival"] - 1e-3
         assert tuple(d["hash"]) == _oracle_hash(d)
+
+
+def _oracle_hash_job(job):
+    # runs in a spawned worker process
+    import oracle as O2
+    from paper_1809_07444_gb300 import workloads as WL2
+    side, seed, steps = job["side"], job["seed"], job["steps"]
+    if job["app"] == WATOR:
+        w = O2.Wator(side, side, WL2.wator_initial(side, side, seed), seed=seed)
+        w.step(steps)
+        return job["id"], w.hash()
+    g = O2.Gol(side, side, WL2.gol_initial(side, side, seed))
+    g.step(steps)
+    return job["id"], g.hash()
+
+
+def _stratified_sample(s, edges=(128, 256, 512, 1024, 2048, 4097), first=40, max_cell_steps=3e9):
+    """Jobs of the configured stream, stratified by application and side bin:
+    per (app, bin), among the first `first` jobs of the bin whose oracle run
+    costs at most `max_cell_steps` cell-steps (a bound on the test's time),
+    the first one, the one with the fewest and the one with the most steps."""
+    picked = []
+    n = len(s["arrival"])
+    for app in (GOL, WATOR):
+        for lo, hi in zip(edges[:-1], edges[1:]):
+            idx = [i for i in range(n) if s["app"][i] == app and lo <= s["side"][i] < hi
+                   and int(s["side"][i]) ** 2 * int(s["steps"][i]) <= max_cell_steps][:first]
+            assert idx, (app, lo, hi)
+            steps = [int(s["steps"][i]) for i in idx]
+            for i in {idx[0], idx[int(np.argmin(steps))], idx[int(np.argmax(steps))]}:
+                picked.append(i)
+    return sorted(set(picked))
+
+
+def test_configured_stream_stratified_sample_matches_oracle():
+    # The served workload's own stream (Poisson 200 jobs/s, 10,000 jobs, sides
+    # log-uniform in [128, 4096], 50-1000 steps): a stratified sample of its
+    # jobs at their configured sizes and step counts, served together, each
+    # final state hash against its own oracle run; the largest wa-tor job of
+    # the sample also alone, with the same result.
+    import multiprocessing as mp
+    import os
+
+    s = WL.served_jobs(10000, 2024)
+    ids = _stratified_sample(s)
+    assert len(ids) >= 24
+    jobs = [{"id": int(i), "arrival": 0.0, "app": int(s["app"][i]), "side": int(s["side"][i]),
+             "steps": int(s["steps"][i]), "seed": int(s["seed"][i])} for i in ids]
+    assert max(j["side"] for j in jobs) >= 3000 and max(j["steps"] for j in jobs) >= 950
+    assert min(j["side"] for j in jobs) < 256 and min(j["steps"] for j in jobs) <= 200
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(len(jobs), os.cpu_count() or 4)) as pool:
+        # the largest jobs first, so that the pool's tail is short
+        pending = pool.map_async(_oracle_hash_job, sorted(jobs, key=lambda j: -j["side"] ** 2 * j["steps"]), chunksize=1)
+        mix = Server(arena_bytes=48 << 30, max_jobs=64).run(jobs, realtime=False)
+        big = max((j for j in jobs if j["app"] == WATOR), key=lambda j: j["side"])
+        alone = Server(arena_bytes=8 << 30, max_jobs=4).run([dict(big)], realtime=False)
+        want = dict(pending.get())
+    assert mix["unfinished"] == 0 and len(mix["done"]) == len(jobs)
+    for d in mix["done"]:
+        assert tuple(d["hash"]) == tuple(want[d["id"]]), "job %d (app %d side %d steps %d)" % (
+            d["id"], d["app"], d["side"], d["steps"])
+    assert tuple(alone["done"][0]["hash"]) == tuple(want[big["id"]])

@@ -2,7 +2,7 @@
 G_alpha, R) with the oracle: the agents' state hash and the events every
 step, the sorted agents and the sugar of every cell at sampled steps, on
 ragged and minimum-size grids, sparse, dense and empty starts, two growback
-rates, and the full-size bench workload on sampled steps."""
+rates, and the full-size bench workload every step for 30 steps."""
 import numpy as np
 import pytest
 
@@ -62,14 +62,23 @@ def test_landscape_without_agents_stays_full():
     assert np.array_equal(g.dump()[1], cap.astype(np.int32))
 
 
-def test_bench_workload_sampled_steps():
-    # 4096 x 4096, 10% of the cells hold an agent (1.68 M agents)
+def test_bench_workload_every_step():
+    # 4096 x 4096, 10% of the cells hold an agent (1.68 M agents): agents'
+    # state hash and event counts every step for 30 steps, sorted agents and
+    # the sugar of every cell at steps 1, 15 and 30
     W = H = 4096
     cap, agents = WL.sugarscape_initial(W, H, 1)
     g, o = _pair(W, H, cap, agents, 1)
-    for n in (1, 2):
-        g.step(n)
-        o.step(n)
-        assert g.hash() == o.hash()
+    prev = g.events()
+    for s in range(1, 31):
+        g.step(1)
+        want = o.step(1)[0].tolist()
+        now = g.events()
+        assert [a - b for a, b in zip(now, prev)] == want, s
+        prev = now
+        assert g.hash() == o.hash(), s
+        if s in (1, 15, 30):
+            _check(g, o)
     assert g.count() == o.count() == len(agents)
     assert g.heap.stats()["error_flags"] == 0
+    check_invariants(g.heap)

@@ -3,7 +3,7 @@ oracle: the state hash of both object types after every step, the per-step
 event counts (cars entered, left, moved, velocity sum), the sorted object
 multisets and the occupancy grid, on open and periodic roads, with ragged
 sizes, empty starts and the model's limits; plus the full-size bench
-workload on sampled steps."""
+workload every step for 32 steps."""
 import numpy as np
 import pytest
 
@@ -82,15 +82,23 @@ def test_full_road_ring_is_stuck():
     assert g.events()[2] == 0  # nobody moved
 
 
-def test_bench_workload_sampled_steps():
+def test_bench_workload_every_step():
     # 8192 roads of 4096 cells, 20% occupied (6.7 M cars), open, p 0.25,
-    # alpha 0.5: hashes and counts after 1 and 3 steps
+    # alpha 0.5: state hash, car count and event counts every step for 32
+    # steps, full state at steps 1, 16 and 32
     R, L = 8192, 4096
     v0 = WL.traffic_initial(R, L, 1)
     g, o = _pair(R, L, v0, 1, vmax=5, p=0.25, alpha=0.5)
-    for n in (1, 2):
-        g.step(n)
-        o.step(n)
-        assert g.hash() == o.hash()
-        assert g.count() == o.count()
+    prev = g.events()
+    for s in range(1, 33):
+        g.step(1)
+        want = o.step(1)[0].tolist()
+        now = g.events()
+        assert [a - b for a, b in zip(now, prev)] == want, s
+        prev = now
+        assert g.hash() == o.hash(), s
+        assert g.count() == o.count(), s
+        if s in (1, 16, 32):
+            _check_state(g, o)
     assert g.heap.stats()["error_flags"] == 0
+    check_invariants(g.heap)

@@ -73,11 +73,12 @@ def test_wator_phase_timing_records_every_step():
     assert w.phase_times()[2] == 0
 
 
-def test_wator_2048_full_size_hash_parity():
-    # the 2048 x 2048 workload (30% fish, 3% sharks): state hash every step
-    # for the first 40 steps, full multisets at the end
+def test_wator_2048_full_size_all_500_steps():
+    # the 2048 x 2048 workload (30% fish, 3% sharks) for its full 500 steps:
+    # state hash and event counts every step, full multisets and the grid
+    # every 50 steps, heap invariants every 100
     W = H = 2048
-    _run_pair(W, H, WL.wator_initial(W, H, 1), 1, 40, full_every=20)
+    _run_pair(W, H, WL.wator_initial(W, H, 1), 1, 500, full_every=50, invariants_every=100)
 
 
 def test_wator_checkpoint_and_resume_bit_exact():
