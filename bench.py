@@ -397,13 +397,14 @@ def run_gpu(args, rank, world):
     hash_host.copy_(hash_dev, non_blocking=True)
     e1.record(stream)
     e1.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e_s = time.perf_counter() - t_host0  # host wall clock: ctypes, launches and copies included
+    e2e_dev_s = e0.elapsed_time(e1) / 1e3
     lib.dsr_wator_destroy(h2)
     c2 = sim.heap.counters()  # counters restarted at the reset
     hashed = sim.heap.stats()["live_objects"][0]  # objects the final hash do-all visited
     return {
         "dev_s": dev_s, "visits": visits, "allocfree": allocfree, "clocks": clk.summary(),
-        "phases": phases, "e2e_s": e2e_s, "e2e_visits": c2["visits"] - hashed,
+        "phases": phases, "e2e_s": e2e_s, "e2e_dev_s": e2e_dev_s, "e2e_visits": c2["visits"] - hashed,
         "h2d": k0_host.numel(), "d2h": 16, "stats": st,
     }
 
@@ -757,10 +758,11 @@ def bench_space(heap_bytes=32 << 20, steps=100):
 
 
 def bench_nbody(n=65536, steps=5):
-    """C3: n-body with merging, 65,536 bodies, FP32 on the GPU. FLOPs counted
-    as 20 per pair for the force (softened inverse-cube, three FMAs into the
-    acceleration) and 8 per pair for the merge-partner distance test, against
-    the FP32 FMA ceiling measured by dsr_bench_fma."""
+    """C3: n-body with merging, 65,536 bodies: FP32 pair forces, FP32-pair
+    state, FP64 near field (pairs within r_near), update and merges. FLOPs
+    counted as 20 per pair for the force (softened inverse-cube, three FMAs
+    into the acceleration) and 8 per pair for the merge-partner distance
+    test, against the FP32 FMA ceiling measured by dsr_bench_fma."""
     import torch
     from paper_1809_07444_gb300 import _lib as L
     from paper_1809_07444_gb300 import workloads as WL
@@ -778,6 +780,7 @@ def bench_nbody(n=65536, steps=5):
     e1.record()
     e1.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / steps
+    near = nb.near_pairs()
     flop = 28.0 * live0 * live0
     lib = L.load()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -795,9 +798,10 @@ def bench_nbody(n=65536, steps=5):
     peak = statistics.median(fl)
     del nb
     torch.cuda.empty_cache()
-    return {"workload": "n-body %d bodies (FP32), steps 3-%d" % (n, 2 + steps), "ms_per_step": t * 1e3,
+    return {"workload": "n-body %d bodies (FP32 pair forces), steps 3-%d" % (n, 2 + steps), "ms_per_step": t * 1e3,
             "bodies": live0, "tflops": flop / t / 1e12, "fp32_fma_peak_tflops": peak / 1e12,
-            "frac_of_fma_peak": flop / t / peak, "bound": "alu", "flop_per_pair": 28}
+            "frac_of_fma_peak": flop / t / peak, "bound": "alu", "flop_per_pair": 28,
+            "near_pairs_last_step": near, "r_near": nb.params.r_near}
 
 
 def bench_batched(n_inst=256, steps=20, one_by_one_steps=3):
@@ -882,21 +886,70 @@ def bench_served(seconds=20.0, n_jobs=10000, arena_gb=64, lo=128, hi=4096, steps
 
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel on this workload, mean over the 50 timed steps of a default run
-# (None for a kernel not captured as it is now).
-TRAFFIC = {"F2": 74.9e6}
+# kernel on this workload, mean over the timed launches of one capture, with
+# the (steps, warmup) window it was taken on. The bench reports it only when
+# it runs that window (the population, hence the bytes of a launch, changes
+# from step to step); a kernel changed since its capture has no entry.
+TRAFFIC = {}
 
 
-def roofline(phases, peak, peak_kind):
+def roofline(phases, peak, peak_kind, steps, warmup):
     """HBM roofline of the method kernel with the largest share of the step."""
     p = max(PHASES, key=lambda q: phases[q]["method_ms_per_step"])
     ph = phases[p]
     achieved = ph["gbs"]
+    cap = TRAFFIC.get(p)
+    same_window = cap is not None and (cap["steps"], cap["warmup"]) == (steps, warmup)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": TRAFFIC.get(p), "kernel": ph["kernel"], "phase": p,
+            "traffic": cap["bytes"] if same_window else None,
+            "traffic_window": ({"steps": cap["steps"], "warmup": cap["warmup"], "source": cap["source"]}
+                               if cap is not None else None),
+            "kernel": ph["kernel"], "phase": p,
             "algorithmic_bytes_per_launch": ph["bytes_per_launch"], "launch_ms": ph["method_ms_per_step"],
             "timing": "CUDA events on the launching stream around every launch of the timed steps",
             "peak_source": ("measured hbm_gbs" if peak_kind == "measured" else "fallback 6.8 TB/s")}
+
+
+def summary(line):
+    """The headline figures of every leg in a few hundred characters: the
+    plain and batched forms side by side (the metric's "batched vs plain"),
+    allocation, the HBM roofline fractions, n-body and the served form."""
+    def g(d, *keys):
+        for k in keys:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+
+    def r3(x):
+        return float("%.4g" % x) if isinstance(x, (int, float)) else x
+
+    out = {"plain_object_updates_per_s": r3(line["value"]), "plain_ms_per_step": r3(line["ms_per_step"]),
+           "e2e_object_updates_per_s": r3(g(line, "e2e", "value")),
+           "dominant_kernel_frac_of_hbm": r3(g(line, "roofline", "frac"))}
+    b = line.get("batched")
+    if b:
+        out["batched_object_updates_per_s"] = r3(b["object_updates_per_s"])
+        out["batched_vs_plain"] = r3(b["object_updates_per_s"] / line["value"])
+        out["batched_vs_one_by_one"] = r3(b.get("speedup_vs_one_by_one"))
+    a = g(line, "alloc_free_microbench", "rows")
+    if a:
+        two = [x for x in a if x["types"] == 2 and x["objects"] == 1 << 24]
+        if two:
+            out["allocs_per_s"] = r3(two[0]["allocs_per_s"])
+            out["frees_per_s"] = r3(two[0]["frees_per_s"])
+    st = line.get("streaming_doall")
+    if st:
+        out["streaming_frac_of_hbm_100pct_fill"] = {k: r3(g(v, "100%", "frac")) for k, v in st.items()}
+    nb = line.get("nbody_65536")
+    if nb:
+        out["nbody_ms_per_step"] = r3(nb.get("ms_per_step"))
+    for k in ("served", "served_small"):
+        sv = line.get(k)
+        if sv:
+            out[k] = {q: r3(sv.get(q)) for q in ("jobs_done", "step_ms_p50", "step_ms_p99", "job_s_p50",
+                                                  "job_s_p99", "admit_ms_p50", "admit_ms_p99")}
+    return out
 
 
 def combine_ranks(times, counts, world, device):
@@ -976,9 +1029,10 @@ def main():
         "alloc_free_per_s": allocfree / dev_s,
         "phases": r["phases"], "clocks": r["clocks"],
         "e2e": {"value": e2e_visits / e2e_s, "unit": UNIT, "h2d_bytes_per_step": r["h2d"] / args.steps,
-                "d2h_bytes_per_step": r["d2h"] / args.steps},
+                "d2h_bytes_per_step": r["d2h"] / args.steps, "timing": "host wall clock around the C-ABI calls",
+                "device_s": r["e2e_dev_s"], "host_s": e2e_s},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
-        "roofline": roofline(r["phases"], peak, peak_kind),
+        "roofline": roofline(r["phases"], peak, peak_kind, args.steps, args.warmup),
     }
     if not args.no_cpu_baseline:
         rate, n, el = oracle_wator_rate(args.cpu_seconds)
@@ -1005,6 +1059,7 @@ def main():
             line["served_small"] = bench_served(args.served_seconds, n_jobs=2000, arena_gb=16, lo=64, hi=512,
                                                 steps_lo=50, steps_hi=200,
                                                 label="a 2,000-job stream with sides in [64, 512] and 50-200 steps")
+    line["summary"] = summary(line)  # last key: the end of the line is what a log tail keeps
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -27,9 +27,38 @@ def test_roofline_takes_the_slowest_method_kernel():
     phases = {p: {"method_ms_per_step": 0.01, "gbs": 100.0, "kernel": "k" + p, "bytes_per_launch": 1.0}
               for p in bench.PHASES}
     phases["S1"].update(method_ms_per_step=0.2, gbs=500.0)
-    r = bench.roofline(phases, 1000.0, "measured")
+    r = bench.roofline(phases, 1000.0, "measured", 20, 5)
     assert r["phase"] == "S1" and r["achieved"] == 500.0 and r["frac"] == 0.5
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["kernel"] == "kS1"
+
+
+def test_roofline_traffic_only_from_its_own_window(monkeypatch):
+    # DRAM traffic measured by ncu over one (steps, warmup) window is
+    # reported only for a run of that same window
+    phases = {p: {"method_ms_per_step": 0.01, "gbs": 100.0, "kernel": "k" + p, "bytes_per_launch": 1.0}
+              for p in bench.PHASES}
+    phases["F2"].update(method_ms_per_step=0.2)
+    monkeypatch.setattr(bench, "TRAFFIC", {"F2": {"bytes": 5.0e7, "steps": 20, "warmup": 5, "source": "x"}})
+    assert bench.roofline(phases, 1000.0, "measured", 20, 5)["traffic"] == 5.0e7
+    other = bench.roofline(phases, 1000.0, "measured", 50, 5)
+    assert other["traffic"] is None and other["traffic_window"]["steps"] == 20
+    monkeypatch.setattr(bench, "TRAFFIC", {})
+    assert bench.roofline(phases, 1000.0, "measured", 20, 5)["traffic"] is None
+
+
+def test_summary_carries_batched_and_plain_side_by_side():
+    line = {"value": 2.0e10, "ms_per_step": 0.3, "e2e": {"value": 1.9e10}, "roofline": {"frac": 0.1},
+            "batched": {"object_updates_per_s": 3.0e10, "speedup_vs_one_by_one": 10.0},
+            "alloc_free_microbench": {"rows": [{"types": 2, "objects": 1 << 24, "allocs_per_s": 5e9,
+                                                "frees_per_s": 6e10}]},
+            "streaming_doall": {"K4": {"100%": {"frac": 0.99}}}, "nbody_65536": {"ms_per_step": 3.0},
+            "served": {"jobs_done": 5, "step_ms_p50": 1.0, "step_ms_p99": 2.0, "job_s_p50": 3.0, "job_s_p99": 4.0,
+                       "admit_ms_p50": 0.5, "admit_ms_p99": 0.9}}
+    s = bench.summary(line)
+    assert s["batched_vs_plain"] == 1.5 and s["plain_object_updates_per_s"] == 2.0e10
+    assert s["allocs_per_s"] == 5e9 and s["streaming_frac_of_hbm_100pct_fill"] == {"K4": 0.99}
+    assert s["served"]["admit_ms_p99"] == 0.9
+    assert len(json.dumps(s)) < 1200  # fits the tail a log keeps
 
 
 def test_reference_arm_prints_the_oracle_line():
