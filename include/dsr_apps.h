@@ -58,6 +58,15 @@ int dsr_gol_batch_instance_bytes(const dsr_gol_batch* b, int W, int H, uint64_t 
 int dsr_gol_batch_add(dsr_gol_batch* b, int W, int H, uint64_t n_blocks, const void* alive0_dev, void* stream,
                       int* inst_out);
 int dsr_gol_batch_remove(dsr_gol_batch* b, int inst);
+/* A batch in the arena of an existing group (dsr_group_create_shared): its
+ * instances compete for the same free bytes as that group's heaps, e.g. a
+ * wa-tor batch's (dsr_wator_batch_group). */
+int dsr_gol_batch_create_shared(dsr_group* pool_of, int max_instances, const dsr_tuning* tune, void* stream,
+                                dsr_gol_batch** out);
+/* Capture the batched generation into its CUDA graph now if the set of
+ * instances changed since the last capture (dsr_gol_batch_step does it
+ * otherwise, on its first call after the change). Host work only. */
+int dsr_gol_batch_prepare(dsr_gol_batch* b);
 int dsr_gol_batch_step(dsr_gol_batch* b, int n_gen, void* stream);
 int dsr_gol_batch_heap(dsr_gol_batch* b, int inst, dsr_heap** out);
 int dsr_gol_batch_group(dsr_gol_batch* b, dsr_group** out);
@@ -192,6 +201,14 @@ int dsr_wator_batch_add(dsr_wator_batch* b, const dsr_wator_params* p, uint64_t 
  * work on it (synchronise the stream first). */
 int dsr_wator_batch_remove(dsr_wator_batch* b, int inst);
 /* n_steps batched steps of every instance, queued on `stream`. */
+/* A batch in the arena of an existing group (dsr_group_create_shared), e.g. a
+ * game-of-life batch's (dsr_gol_batch_group). */
+int dsr_wator_batch_create_shared(dsr_group* pool_of, int max_instances, const dsr_tuning* tune, void* stream,
+                                  dsr_wator_batch** out);
+/* Capture the batched step into its CUDA graph now if the set of instances
+ * changed since the last capture (otherwise dsr_wator_batch_step does it).
+ * Host work only. */
+int dsr_wator_batch_prepare(dsr_wator_batch* b);
 int dsr_wator_batch_step(dsr_wator_batch* b, int n_steps, void* stream);
 /* The heap of an instance (for dsr_heap_hash, dsr_heap_dump, dsr_heap_stats). */
 int dsr_wator_batch_heap(dsr_wator_batch* b, int inst, dsr_heap** out);
@@ -200,18 +217,40 @@ int dsr_wator_batch_group(dsr_wator_batch* b, dsr_group** out);
 int dsr_wator_batch_destroy(dsr_wator_batch* b);
 
 /* ---- n-body with merging collisions ------------------------------------
- * FP32. Types: 0 Body {id (int32), x, y, z, vx, vy, vz, m (float)}. One step:
- * a_i = G sum_j m_j d_ij / (|d_ij|^2 + eps^2)^(3/2); v += a dt; x += v dt;
+ * Fig. 6b ("collisions") and 6d ("nbody"); Fig. 1 names an Euler time step.
+ * Types: 0 Body {id (int32); x, y, z, vx, vy, vz, m (float); then the low
+ * words xl, yl, zl, vxl, vyl, vzl, ml (float)}: each state component is the
+ * FP32 pair (high word, low word) whose sum is its value, about 48
+ * significant bits. One step:
+ *   a_i = G sum_j m_j d_ij / (|d_ij|^2 + eps^2)^(3/2); v += a dt; x += v dt;
  * then, on the new positions, the partner of i is the body with the lowest
  * id j != i closer than r_merge; mutual partners merge (the lower id keeps
  * the summed mass and the mass-weighted mean position and velocity, the
- * higher id is deleted). Workspace (dsr_nbody_workspace_bytes): dense
- * per-slot arrays for all M * 64 slots of the heap, the slice buffers of the
- * split all-pairs kernels (sized from the device's SM count and the
- * kernels' occupancy, so query it on the device that will run the step),
- * and a merge log of log_cap entries. */
+ * higher id is deleted).
+ * Arithmetic: the update, the merge distance test (FP32 candidates, FP64
+ * decision) and the merges run in FP64. The all-pairs sum runs in
+ *   DSR_NBODY_PAIRS_FP32  FP32 on the high words, except for pairs closer
+ *                         than r_near (an FP32 test on the high words), which
+ *                         are summed in FP64 from the full state in the order
+ *                         of the partners' ids; r_near = 0 leaves every pair
+ *                         in FP32;
+ *   DSR_NBODY_PAIRS_FP64  FP64 from the full state for every pair (r_near is
+ *                         not used).
+ * Close encounters amplify rounding: on the 65,536-body workload the FP32
+ * pair mode stays within 1e-4 relative of an FP64 reference for 23 steps,
+ * the FP64 pair mode for all 50.
+ * Workspace (dsr_nbody_workspace_bytes): dense per-slot arrays for all
+ * M * 64 slots of the heap, room for max(32 * M * 64, 2^20) near pairs (more
+ * in one step sets DSR_ERR_CAPACITY; the excess pairs stay in the FP32 sum),
+ * the slice buffers of the split all-pairs kernels (sized from the device's
+ * SM count and the kernels' occupancy, so query it on the device that will
+ * run the step), and a merge log of log_cap entries. */
+#define DSR_NBODY_PAIRS_FP32 0
+#define DSR_NBODY_PAIRS_FP64 1
 typedef struct {
-    float G, eps, dt, r_merge;
+    double G, eps, dt, r_merge, r_near;
+    int32_t pair_precision; /* DSR_NBODY_PAIRS_FP32 or DSR_NBODY_PAIRS_FP64 */
+    int32_t pad_;
 } dsr_nbody_params;
 typedef struct dsr_nbody dsr_nbody;
 int dsr_nbody_types(dsr_type_desc* out /* 1 entry */);
@@ -223,18 +262,23 @@ int dsr_nbody_step(dsr_nbody* nb, int n_steps, void* stream);
 /* Device pointers to the merge log (int32[log_cap][3]: step, survivor id,
  * absorbed id, in arbitrary order within a step) and its uint64 count. */
 int dsr_nbody_merge_log(dsr_nbody* nb, void** log_dev, void** count_dev);
+/* Device pointer to the uint32 count of near pairs (closer than r_near) the
+ * last step found. */
+int dsr_nbody_near_pairs(dsr_nbody* nb, void** count_dev);
 int dsr_nbody_destroy(dsr_nbody* nb);
 
 /* Allocation-free n-body step (the paper has no counterpart). Same steps and
  * results as dsr_nbody_step, for callers that cannot call cudaMalloc: code
  * that runs where device allocation is not allowed or not available, such as
- * a plugin handed device memory by a host program that owns it all, or work
- * queued while a stream is being captured into a CUDA graph. Instead of a
+ * a plugin that is handed its device memory by a host program that owns all
+ * of it and forbids allocations of its own. Instead of a
  * caller-allocated workspace, the per-slot scratch of a step (dense
- * positions, velocities, ids, partners; 56 bytes per slot) and the step
+ * state before and after the update, ids, partners, far-field sums and
+ * near-pair lists: 180 bytes per slot and 12 per near pair) and the step
  * counter live in a static device array inside this library, sized for
- * DSR_NOALLOC_MAX_SLOTS slots (about 0.9 MB), which every GPU that loads the
- * library holds until the process exits. The call allocates nothing: no
+ * DSR_NOALLOC_MAX_SLOTS slots and DSR_NOALLOC_PAIRS_PER_SLOT near pairs per
+ * slot (about 6.1 MB), which every GPU that loads the library holds until the
+ * process exits. The call allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine.
  *   heap        a heap whose type 0 is Body (dsr_nbody_types) and whose block
  *               count times 64 is at most DSR_NOALLOC_MAX_SLOTS; a larger
@@ -245,11 +289,16 @@ int dsr_nbody_destroy(dsr_nbody* nb);
  *               is 0); log_count_dev: device uint64 that receives, added to
  *               its current value, the number of merges.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Every call shares the one array and it keeps
- * the last call's contents: calls that overlap on the GPU (other streams, or
- * other threads) race, so order them on one stream. */
+ * (cudaGetSymbolAddress) with that device current, and later calls reuse it;
+ * make that first call before any stream capture. The address belongs to
+ * the device's current context: after cudaDeviceReset (or any teardown of
+ * the primary context) it is stale, so do not call this entry point again
+ * in that process. Every call shares the one array and it keeps the last
+ * call's contents (the step counter is set at the start of each call): calls
+ * that overlap on the GPU (other streams, or other threads) race, so order
+ * them on one stream. */
 #define DSR_NOALLOC_MAX_SLOTS 16384
+#define DSR_NOALLOC_PAIRS_PER_SLOT 16
 int dsr_nbody_step_noalloc(dsr_heap* heap, const dsr_nbody_params* p, int n_steps, uint64_t step0, void* log_dev,
                            uint64_t log_cap, void* log_count_dev, void* stream);
 

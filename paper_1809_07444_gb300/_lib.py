@@ -16,6 +16,7 @@ MAX_LEVELS = 6
 
 OK, E_INVALID, E_OOM, E_CUDA, E_DEVICE, E_TOO_LARGE = 0, 1, 2, 3, 4, 5
 NOALLOC_MAX_SLOTS = 16384
+NOALLOC_PAIRS_PER_SLOT = 16
 CTR_COUNT = 8  # event counters per heap (DSR_CTR_COUNT)
 ERR_OOM, ERR_RETRY, ERR_DOUBLE_FREE, ERR_BAD_HANDLE, ERR_CAPACITY = 1, 2, 4, 8, 16
 
@@ -69,8 +70,12 @@ class SugarscapeParams(C.Structure):
                 ("vision_lo", C.c_int32), ("vision_hi", C.c_int32), ("age_lo", C.c_int32), ("age_hi", C.c_int32)]
 
 
+NBODY_PAIRS_FP32, NBODY_PAIRS_FP64 = 0, 1
+
+
 class NBodyParams(C.Structure):
-    _fields_ = [("G", C.c_float), ("eps", C.c_float), ("dt", C.c_float), ("r_merge", C.c_float)]
+    _fields_ = [("G", C.c_double), ("eps", C.c_double), ("dt", C.c_double), ("r_merge", C.c_double),
+                ("r_near", C.c_double), ("pair_precision", C.c_int32), ("pad_", C.c_int32)]
 
 
 class CountArgs(C.Structure):
@@ -154,6 +159,7 @@ SIGNATURES = {
     "dsr_nbody_create": (_i, [_vp, C.POINTER(NBodyParams), _vp, _i, _vp, _u64, _vp, C.POINTER(_vp)]),
     "dsr_nbody_step": (_i, [_vp, _i, _vp]),
     "dsr_nbody_merge_log": (_i, [_vp, C.POINTER(_vp), C.POINTER(_vp)]),
+    "dsr_nbody_near_pairs": (_i, [_vp, C.POINTER(_vp)]),
     "dsr_nbody_destroy": (_i, [_vp]),
     "dsr_nbody_step_noalloc": (_i, [_vp, C.POINTER(NBodyParams), _i, _u64, _vp, _u64, _vp, _vp]),
     "dsr_traffic_types": (_i, [C.POINTER(TypeDesc)]),
@@ -171,6 +177,7 @@ SIGNATURES = {
     "dsr_sugarscape_sugar": (_i, [_vp, _vp, _vp]),
     "dsr_sugarscape_destroy": (_i, [_vp]),
     "dsr_group_create": (_i, [C.POINTER(TypeDesc), _i, _vp, _sz, _i, C.POINTER(Tuning), _vp, C.POINTER(_vp)]),
+    "dsr_group_create_shared": (_i, [C.POINTER(TypeDesc), _i, _vp, _i, C.POINTER(Tuning), _vp, C.POINTER(_vp)]),
     "dsr_group_destroy": (_i, [_vp]),
     "dsr_group_add_heap": (_i, [_vp, _u64, _sz, _vp, C.POINTER(_i), C.POINTER(_vp), C.POINTER(_vp)]),
     "dsr_group_remove_heap": (_i, [_vp, _i]),
@@ -181,6 +188,8 @@ SIGNATURES = {
     "dsr_group_check_record": (_i, [_vp, C.POINTER(_u32), C.POINTER(_u64)]),
     "dsr_heap_check_record": (_i, [_vp, C.POINTER(_u32), C.POINTER(_u64)]),
     "dsr_wator_batch_create": (_i, [_vp, _sz, _i, C.POINTER(Tuning), _vp, C.POINTER(_vp)]),
+    "dsr_wator_batch_create_shared": (_i, [_vp, _i, C.POINTER(Tuning), _vp, C.POINTER(_vp)]),
+    "dsr_wator_batch_prepare": (_i, [_vp]),
     "dsr_wator_batch_instance_bytes": (_i, [_vp, _i, _i, _u64, C.POINTER(_sz)]),
     "dsr_wator_batch_add": (_i, [_vp, C.POINTER(WatorParams), _u64, _vp, _vp, C.POINTER(_i)]),
     "dsr_wator_batch_remove": (_i, [_vp, _i]),
@@ -190,6 +199,8 @@ SIGNATURES = {
     "dsr_wator_batch_group": (_i, [_vp, C.POINTER(_vp)]),
     "dsr_wator_batch_destroy": (_i, [_vp]),
     "dsr_gol_batch_create": (_i, [_vp, _sz, _i, C.POINTER(Tuning), _vp, C.POINTER(_vp)]),
+    "dsr_gol_batch_create_shared": (_i, [_vp, _i, C.POINTER(Tuning), _vp, C.POINTER(_vp)]),
+    "dsr_gol_batch_prepare": (_i, [_vp]),
     "dsr_gol_batch_instance_bytes": (_i, [_vp, _i, _i, _u64, C.POINTER(_sz)]),
     "dsr_gol_batch_add": (_i, [_vp, _i, _i, _u64, _vp, _vp, C.POINTER(_i)]),
     "dsr_gol_batch_remove": (_i, [_vp, _i]),

