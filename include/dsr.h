@@ -257,6 +257,15 @@ int dsr_heap_inject_oom(dsr_heap* heap, uint32_t n, void* stream);
 typedef struct dsr_group dsr_group;
 int dsr_group_create(const dsr_type_desc* types, int n_types, void* arena_dev, size_t arena_bytes, int max_heaps,
                      const dsr_tuning* tune, void* stream, dsr_group** out);
+/* A group of other types in the same arena as `with` (no counterpart in the
+ * paper): its tables and heaps are carved first fit from the free bytes that
+ * every group of that arena draws on, so groups of different applications
+ * share one pool of memory instead of fixed parts of it. The arena stays
+ * owned by the caller and must outlive every group in it; the groups may be
+ * destroyed in any order (a destroyed group's bytes return to the pool).
+ * Calls on groups of one arena must not run concurrently on the host. */
+int dsr_group_create_shared(const dsr_type_desc* types, int n_types, dsr_group* with, int max_heaps,
+                            const dsr_tuning* tune, void* stream, dsr_group** out);
 int dsr_group_destroy(dsr_group* g);
 /* Carve a heap of at least n_blocks blocks plus extra_bytes of caller scratch
  * (256-byte aligned, returned in *extra_dev) and queue its reset on `stream`.
@@ -269,7 +278,7 @@ int dsr_group_add_heap(dsr_group* g, uint64_t n_blocks, size_t extra_bytes, void
 int dsr_group_remove_heap(dsr_group* g, int index);
 /* Bytes a heap of n_blocks blocks plus extra_bytes takes in a group arena. */
 int dsr_group_heap_bytes(const dsr_group* g, uint64_t n_blocks, size_t extra_bytes, size_t* out);
-/* Free bytes of the arena, and the largest free range. */
+/* Free bytes of the arena (shared by every group in it), and the largest free range. */
 int dsr_group_free_bytes(const dsr_group* g, size_t* total_free, size_t* largest_free);
 int dsr_group_heap_count(const dsr_group* g);
 /* Builds compiled with -DDSR_DEVICE_CHECKS check indices and handles on the

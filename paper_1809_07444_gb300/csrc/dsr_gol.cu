@@ -254,10 +254,27 @@ struct dsr_gol_batch {
     dsr_group* group;
     GolArgs* table_d;
     std::vector<GolArgs> table_h;
+    bool table_pooled = false;  // the table came from the group's pool (shared arena)
     cudaStream_t capture;
     cudaGraphExec_t exec = nullptr;
     uint64_t exec_epoch = ~0ull;
 };
+
+// The rest of a batch's creation once its group and table exist.
+static int finish_gol_batch(dsr_gol_batch* b, int max_instances, void* stream, dsr_gol_batch** out) {
+    b->table_h.assign(max_instances, GolArgs{nullptr, 0, 0});
+    cudaError_t e = cudaMemsetAsync(b->table_d, 0, gol_table_bytes(max_instances), dsr__stream(stream));
+    if (!e) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_gol_batch_create");
+        if (b->table_pooled) dsr__group_give_bytes(b->group, b->table_d, gol_table_bytes(max_instances));
+        dsr_group_destroy(b->group);
+        delete b;
+        return DSR_E_CUDA;
+    }
+    *out = b;
+    return DSR_OK;
+}
 
 extern "C" int dsr_gol_batch_create(void* arena_dev, size_t arena_bytes, int max_instances, const dsr_tuning* tune,
                                     void* stream, dsr_gol_batch** out) {
@@ -274,17 +291,30 @@ extern "C" int dsr_gol_batch_create(void* arena_dev, size_t arena_bytes, int max
         return rc;
     }
     b->table_d = static_cast<GolArgs*>(arena_dev);
-    b->table_h.assign(max_instances, GolArgs{nullptr, 0, 0});
-    cudaError_t e = cudaMemsetAsync(b->table_d, 0, tb, dsr__stream(stream));
-    if (!e) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
-    if (e) {
-        dsr__set_cuda_error(e, "dsr_gol_batch_create");
+    return finish_gol_batch(b, max_instances, stream, out);
+}
+
+extern "C" int dsr_gol_batch_create_shared(dsr_group* pool_of, int max_instances, const dsr_tuning* tune,
+                                           void* stream, dsr_gol_batch** out) {
+    if (!pool_of || !out || max_instances < 1) return DSR_E_INVALID;
+    dsr_type_desc types[2];
+    dsr_gol_types(types);
+    dsr_gol_batch* b = new dsr_gol_batch;
+    int rc = dsr_group_create_shared(types, 2, pool_of, max_instances, tune, stream, &b->group);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    void* t = nullptr;
+    rc = dsr__group_take_bytes(b->group, gol_table_bytes(max_instances), &t);
+    if (rc) {
         dsr_group_destroy(b->group);
         delete b;
-        return DSR_E_CUDA;
+        return rc;
     }
-    *out = b;
-    return DSR_OK;
+    b->table_d = static_cast<GolArgs*>(t);
+    b->table_pooled = true;
+    return finish_gol_batch(b, max_instances, stream, out);
 }
 
 extern "C" int dsr_gol_batch_instance_bytes(const dsr_gol_batch* b, int W, int H, uint64_t n_blocks, size_t* out) {
@@ -334,35 +364,45 @@ extern "C" int dsr_gol_batch_remove(dsr_gol_batch* b, int inst) {
 
 // One batched generation: three group do-alls (6 launches), captured into a
 // CUDA graph once per set of instances.
+static int ensure_gol_graph(dsr_gol_batch* b) {
+    if (b->exec_epoch == b->group->epoch) return DSR_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_gol_batch_step capture");
+        return DSR_E_CUDA;
+    }
+    GolBatchArgs a{b->table_d};
+    int rc = dsr__group_doall<GCount>(b->group, CELL, a, b->capture);
+    if (!rc) rc = dsr__group_doall<GDie>(b->group, ALIVE, a, b->capture);
+    if (!rc) rc = dsr__group_doall<GBirth>(b->group, CELL, a, b->capture);
+    e = cudaStreamEndCapture(b->capture, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (!e) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_gol_batch_step instantiate");
+        b->exec = nullptr;
+        return DSR_E_CUDA;
+    }
+    b->exec_epoch = b->group->epoch;
+    return DSR_OK;
+}
+
+extern "C" int dsr_gol_batch_prepare(dsr_gol_batch* b) {
+    if (!b) return DSR_E_INVALID;
+    return ensure_gol_graph(b);
+}
+
 extern "C" int dsr_gol_batch_step(dsr_gol_batch* b, int n_gen, void* stream) {
     if (!b || n_gen < 0) return DSR_E_INVALID;
-    if (b->exec_epoch != b->group->epoch) {
-        if (b->exec) cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
-        if (e) {
-            dsr__set_cuda_error(e, "dsr_gol_batch_step capture");
-            return DSR_E_CUDA;
-        }
-        GolBatchArgs a{b->table_d};
-        int rc = dsr__group_doall<GCount>(b->group, CELL, a, b->capture);
-        if (!rc) rc = dsr__group_doall<GDie>(b->group, ALIVE, a, b->capture);
-        if (!rc) rc = dsr__group_doall<GBirth>(b->group, CELL, a, b->capture);
-        e = cudaStreamEndCapture(b->capture, &graph);
-        if (rc) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-        if (!e) e = cudaGraphInstantiate(&b->exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        if (e) {
-            dsr__set_cuda_error(e, "dsr_gol_batch_step instantiate");
-            b->exec = nullptr;
-            return DSR_E_CUDA;
-        }
-        b->exec_epoch = b->group->epoch;
-    }
+    const int rc = ensure_gol_graph(b);
+    if (rc) return rc;
     cudaStream_t s = dsr__stream(stream);
     for (int i = 0; i < n_gen; ++i) {
         cudaError_t e = cudaGraphLaunch(b->exec, s);
@@ -390,6 +430,7 @@ extern "C" int dsr_gol_batch_destroy(dsr_gol_batch* b) {
     if (!b) return DSR_E_INVALID;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     cudaStreamDestroy(b->capture);
+    if (b->table_pooled) dsr__group_give_bytes(b->group, b->table_d, gol_table_bytes((int)b->table_h.size()));
     dsr_group_destroy(b->group);
     delete b;
     return DSR_OK;

@@ -123,10 +123,51 @@ static int upload_tables(dsr_group* g, cudaStream_t s) {
     return DSR_OK;
 }
 
-extern "C" int dsr_group_create(const dsr_type_desc* types, int n_types, void* arena_dev, size_t arena_bytes,
-                                int max_heaps, const dsr_tuning* tune, void* stream, dsr_group** out) {
-    if (!out || !arena_dev || max_heaps < 1 || (reinterpret_cast<uintptr_t>(arena_dev) & 255)) return DSR_E_INVALID;
-    *out = nullptr;
+bool dsr__pool_take(dsr_pool& p, size_t need, size_t* off) {
+    auto it = p.free_ranges.begin();
+    for (; it != p.free_ranges.end(); ++it)
+        if (it->second >= need) break;
+    if (it == p.free_ranges.end()) return false;
+    *off = it->first;
+    const size_t rest = it->second - need;
+    p.free_ranges.erase(it);
+    if (rest) p.free_ranges[*off + need] = rest;
+    return true;
+}
+
+void dsr__pool_give(dsr_pool& p, size_t off, size_t size) {
+    auto next = p.free_ranges.lower_bound(off);
+    if (next != p.free_ranges.end() && off + size == next->first) {
+        size += next->second;
+        p.free_ranges.erase(next);
+    }
+    auto prev = p.free_ranges.lower_bound(off);
+    if (prev != p.free_ranges.begin()) {
+        --prev;
+        if (prev->first + prev->second == off) {
+            off = prev->first;
+            size += prev->second;
+            p.free_ranges.erase(prev);
+        }
+    }
+    p.free_ranges[off] = size;
+}
+
+int dsr__group_take_bytes(dsr_group* g, size_t bytes, void** out) {
+    size_t off = 0;
+    if (!dsr__pool_take(*g->pool, round_up(bytes, 1024), &off)) return DSR_E_OOM;
+    *out = g->arena + off;
+    return DSR_OK;
+}
+
+void dsr__group_give_bytes(dsr_group* g, void* p, size_t bytes) {
+    dsr__pool_give(*g->pool, (size_t)(static_cast<uint8_t*>(p) - g->arena), round_up(bytes, 1024));
+}
+
+// A group in `pool`: its tables and lists are carved first fit from the pool,
+// sized so that the group's heaps could take the whole arena.
+static int group_create_in(std::shared_ptr<dsr_pool> pool, const dsr_type_desc* types, int n_types, int max_heaps,
+                           const dsr_tuning* tune, void* stream, dsr_group** out) {
     // Smallest heap footprint per block, to size the group's lists.
     size_t one = 0;
     int rc = dsr_heap_bytes_for_blocks(types, n_types, 1, tune, &one);
@@ -135,7 +176,7 @@ extern "C" int dsr_group_create(const dsr_type_desc* types, int n_types, void* a
     rc = dsr_heap_bytes_for_blocks(types, n_types, 1025, tune, &two);
     if (rc) return rc;
     const size_t per_block = (two - one) / 1024;  // marginal bytes of one more block
-    const uint64_t max_blocks = arena_bytes / (per_block ? per_block : 1);
+    const uint64_t max_blocks = pool->bytes / (per_block ? per_block : 1);
     const uint64_t max_chunks = max_blocks / 256 + (uint64_t)max_heaps;
     size_t off = 0;
     const size_t o_heaps = off;
@@ -152,13 +193,19 @@ extern "C" int dsr_group_create(const dsr_type_desc* types, int n_types, void* a
     off = round_up(off + max_blocks * 8, 256);
     const size_t o_cnt = off;
     off = round_up(off + 256, 1024);
-    if (off >= arena_bytes) return DSR_E_OOM;
+    size_t base = 0;
+    if (!dsr__pool_take(*pool, off, &base)) return DSR_E_OOM;
 
     dsr_group* g = new (std::nothrow) dsr_group;
-    if (!g) return DSR_E_OOM;
-    uint8_t* a = static_cast<uint8_t*>(arena_dev);
-    g->arena = a;
-    g->arena_bytes = arena_bytes;
+    if (!g) {
+        dsr__pool_give(*pool, base, off);
+        return DSR_E_OOM;
+    }
+    uint8_t* a = pool->arena + base;
+    g->pool = pool;
+    g->arena = pool->arena;
+    g->tables_off = base;
+    g->tables_bytes = off;
     g->max_heaps = max_heaps;
     g->max_chunks = max_chunks;
     g->n_types = n_types;
@@ -187,12 +234,12 @@ extern "C" int dsr_group_create(const dsr_type_desc* types, int n_types, void* a
     g->dev.err = reinterpret_cast<uint32_t*>(a + o_cnt + 8);
     g->dev.dbg = reinterpret_cast<dsr_u64*>(a + o_cnt + 16);
     g->dev.R_cap = max_blocks;
-    g->free_ranges[off] = arena_bytes - off;
     cudaError_t e = cudaGetDevice(&g->device);
     if (!e) e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device);
     if (!e) e = cudaMemsetAsync(a + o_cnt, 0, 256, dsr__stream(stream));
     if (e) {
         dsr__set_cuda_error(e, "dsr_group_create");
+        dsr__pool_give(*pool, base, off);
         delete g;
         return DSR_E_CUDA;
     }
@@ -200,9 +247,33 @@ extern "C" int dsr_group_create(const dsr_type_desc* types, int n_types, void* a
     return DSR_OK;
 }
 
+extern "C" int dsr_group_create(const dsr_type_desc* types, int n_types, void* arena_dev, size_t arena_bytes,
+                                int max_heaps, const dsr_tuning* tune, void* stream, dsr_group** out) {
+    if (!out || !arena_dev || max_heaps < 1 || (reinterpret_cast<uintptr_t>(arena_dev) & 255)) return DSR_E_INVALID;
+    *out = nullptr;
+    auto pool = std::make_shared<dsr_pool>();
+    pool->arena = static_cast<uint8_t*>(arena_dev);
+    pool->bytes = arena_bytes / 1024 * 1024;
+    if (pool->bytes == 0) return DSR_E_OOM;
+    pool->free_ranges[0] = pool->bytes;
+    return group_create_in(pool, types, n_types, max_heaps, tune, stream, out);
+}
+
+extern "C" int dsr_group_create_shared(const dsr_type_desc* types, int n_types, dsr_group* with, int max_heaps,
+                                       const dsr_tuning* tune, void* stream, dsr_group** out) {
+    if (!out || !with || max_heaps < 1) return DSR_E_INVALID;
+    *out = nullptr;
+    return group_create_in(with->pool, types, n_types, max_heaps, tune, stream, out);
+}
+
 extern "C" int dsr_group_destroy(dsr_group* g) {
     if (!g) return DSR_E_INVALID;
-    for (dsr_heap* h : g->heaps) dsr_heap_destroy(h);
+    for (int i = 0; i < g->max_heaps; ++i) {
+        if (!g->heaps[i]) continue;
+        dsr_heap_destroy(g->heaps[i]);
+        dsr__pool_give(*g->pool, g->offsets[i], g->sizes[i]);  // for the other groups of a shared pool
+    }
+    dsr__pool_give(*g->pool, g->tables_off, g->tables_bytes);
     delete g;
     return DSR_OK;
 }
@@ -233,19 +304,12 @@ extern "C" int dsr_group_add_heap(dsr_group* g, uint64_t n_blocks, size_t extra_
     // blocks); its range is rounded up so that the extra bytes after it stay
     // aligned.
     const size_t need = round_up(hb, 1024) + round_up(extra_bytes, 1024);
-    // first fit
-    auto it = g->free_ranges.begin();
-    for (; it != g->free_ranges.end(); ++it)
-        if (it->second >= need) break;
-    if (it == g->free_ranges.end()) return DSR_E_OOM;
-    const size_t off = it->first;
-    const size_t rest = it->second - need;
-    g->free_ranges.erase(it);
-    if (rest) g->free_ranges[off + need] = rest;
+    size_t off = 0;
+    if (!dsr__pool_take(*g->pool, need, &off)) return DSR_E_OOM;
     dsr_heap* h = nullptr;
     rc = dsr_heap_create(g->types.data(), g->n_types, g->arena + off, hb, &g->tune, stream, &h);
     if (rc) {
-        g->free_ranges[off] = need;  // give it back (neighbours stay split; fine)
+        dsr__pool_give(*g->pool, off, need);
         return rc;
     }
     g->heaps[slot] = h;
@@ -270,30 +334,14 @@ extern "C" int dsr_group_remove_heap(dsr_group* g, int index) {
     if (!g || index < 0 || index >= g->max_heaps || !g->heaps[index]) return DSR_E_INVALID;
     dsr_heap_destroy(g->heaps[index]);
     g->heaps[index] = nullptr;
-    size_t off = g->offsets[index], size = g->sizes[index];
-    // coalesce with neighbours
-    auto next = g->free_ranges.lower_bound(off);
-    if (next != g->free_ranges.end() && off + size == next->first) {
-        size += next->second;
-        g->free_ranges.erase(next);
-    }
-    auto prev = g->free_ranges.lower_bound(off);
-    if (prev != g->free_ranges.begin()) {
-        --prev;
-        if (prev->first + prev->second == off) {
-            off = prev->first;
-            size += prev->second;
-            g->free_ranges.erase(prev);
-        }
-    }
-    g->free_ranges[off] = size;
+    dsr__pool_give(*g->pool, g->offsets[index], g->sizes[index]);
     return upload_tables(g, nullptr);
 }
 
 extern "C" int dsr_group_free_bytes(const dsr_group* g, size_t* total_free, size_t* largest_free) {
     if (!g) return DSR_E_INVALID;
     size_t t = 0, l = 0;
-    for (auto& kv : g->free_ranges) {
+    for (auto& kv : g->pool->free_ranges) {
         t += kv.second;
         if (kv.second > l) l = kv.second;
     }

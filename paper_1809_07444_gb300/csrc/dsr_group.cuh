@@ -3,13 +3,29 @@
 #pragma once
 
 #include <map>
+#include <memory>
 #include <vector>
 
 #include "dsr_internal.cuh"
 
-struct dsr_group {
+// The bytes of one caller-owned arena, handed out first fit. Every group
+// carved from the arena holds the pool (dsr_group_create makes one,
+// dsr_group_create_shared joins another group's); its tables, its heaps and
+// the application's instance tables all come from it.
+struct dsr_pool {
     uint8_t* arena;
-    size_t arena_bytes;
+    size_t bytes;
+    std::map<size_t, size_t> free_ranges;  // offset -> bytes
+};
+// First fit of `need` bytes (a multiple of 1024); false if no range is large enough.
+bool dsr__pool_take(dsr_pool& p, size_t need, size_t* off);
+// Return a range, merged with its free neighbours.
+void dsr__pool_give(dsr_pool& p, size_t off, size_t size);
+
+struct dsr_group {
+    std::shared_ptr<dsr_pool> pool;
+    uint8_t* arena;                        // pool->arena
+    size_t tables_off, tables_bytes;       // this group's tables and lists in the arena
     int max_heaps;
     uint64_t max_chunks;
     int n_types;
@@ -21,7 +37,6 @@ struct dsr_group {
     std::vector<dsr_heap*> heaps;          // slot -> heap (nullptr = free slot)
     std::vector<size_t> offsets, sizes;    // slot -> range in the arena
     std::vector<dsr_dev_heap> views;       // host copies of the device views
-    std::map<size_t, size_t> free_ranges;  // offset -> bytes
     std::vector<uint32_t> chunk_heap_h, chunk_base_h;
     uint32_t n_chunks = 0;
     uint64_t epoch = 0;                    // bumped whenever the set of heaps changes
@@ -30,6 +45,12 @@ struct dsr_group {
     uint32_t* chunk_base_d;
     dsr_group_dev dev;
 };
+
+// Bytes for an application's own tables from the group's pool (a multiple
+// of 1024, 1024-aligned); DSR_E_OOM if none is free. Give them back before
+// the group is destroyed.
+int dsr__group_take_bytes(dsr_group* g, size_t bytes, void** out);
+void dsr__group_give_bytes(dsr_group* g, void* p, size_t bytes);
 
 void dsr__group_launch_scan(const dsr_group* g, int type, cudaStream_t s, unsigned visits_per_object = 1);
 int dsr__group_grid(const dsr_group* g, const void* kernel, int threads);

@@ -602,12 +602,29 @@ struct dsr_wator_batch {
     dsr_group* group;
     WatorInst* table_d;              // [max_instances] device views
     std::vector<WatorInst> table_h;  // host mirror
+    bool table_pooled = false;       // the table came from the group's pool (shared arena)
     cudaStream_t capture;            // private stream used only to capture the step graph
     cudaGraphExec_t exec = nullptr;
     uint64_t exec_epoch = ~0ull;
 };
 
 static size_t table_bytes(int max_instances) { return ((size_t)max_instances * sizeof(WatorInst) + 1023) / 1024 * 1024; }
+
+// The rest of a batch's creation once its group and table exist.
+static int finish_batch(dsr_wator_batch* b, int max_instances, void* stream, dsr_wator_batch** out) {
+    b->table_h.assign(max_instances, WatorInst{});
+    cudaError_t e = cudaMemsetAsync(b->table_d, 0, table_bytes(max_instances), dsr__stream(stream));
+    if (!e) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_wator_batch_create");
+        if (b->table_pooled) dsr__group_give_bytes(b->group, b->table_d, table_bytes(max_instances));
+        dsr_group_destroy(b->group);
+        delete b;
+        return DSR_E_CUDA;
+    }
+    *out = b;
+    return DSR_OK;
+}
 
 extern "C" int dsr_wator_batch_create(void* arena_dev, size_t arena_bytes, int max_instances, const dsr_tuning* tune,
                                       void* stream, dsr_wator_batch** out) {
@@ -624,17 +641,30 @@ extern "C" int dsr_wator_batch_create(void* arena_dev, size_t arena_bytes, int m
         return rc;
     }
     b->table_d = static_cast<WatorInst*>(arena_dev);
-    b->table_h.assign(max_instances, WatorInst{});
-    cudaError_t e = cudaMemsetAsync(b->table_d, 0, tb, dsr__stream(stream));
-    if (!e) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
-    if (e) {
-        dsr__set_cuda_error(e, "dsr_wator_batch_create");
+    return finish_batch(b, max_instances, stream, out);
+}
+
+extern "C" int dsr_wator_batch_create_shared(dsr_group* pool_of, int max_instances, const dsr_tuning* tune,
+                                             void* stream, dsr_wator_batch** out) {
+    if (!pool_of || !out || max_instances < 1) return DSR_E_INVALID;
+    dsr_type_desc types[2];
+    dsr_wator_types(types);
+    dsr_wator_batch* b = new dsr_wator_batch;
+    int rc = dsr_group_create_shared(types, 2, pool_of, max_instances, tune, stream, &b->group);
+    if (rc) {
+        delete b;
+        return rc;
+    }
+    void* t = nullptr;
+    rc = dsr__group_take_bytes(b->group, table_bytes(max_instances), &t);
+    if (rc) {
         dsr_group_destroy(b->group);
         delete b;
-        return DSR_E_CUDA;
+        return rc;
     }
-    *out = b;
-    return DSR_OK;
+    b->table_d = static_cast<WatorInst*>(t);
+    b->table_pooled = true;
+    return finish_batch(b, max_instances, stream, out);
 }
 
 extern "C" int dsr_wator_batch_instance_bytes(const dsr_wator_batch* b, int W, int H, uint64_t n_blocks, size_t* out) {
@@ -695,32 +725,42 @@ static int issue_batch_step(dsr_wator_batch* b, cudaStream_t s) {
 // One batched step is 10 launches (5 fused scans, 5 method kernels) over all
 // instances; it is captured once into a CUDA graph and replayed until the set
 // of instances changes.
+static int ensure_graph(dsr_wator_batch* b) {
+    if (b->exec_epoch == b->group->epoch) return DSR_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_wator_batch_step capture");
+        return DSR_E_CUDA;
+    }
+    const int rc = issue_batch_step(b, b->capture);
+    e = cudaStreamEndCapture(b->capture, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (!e) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e) {
+        dsr__set_cuda_error(e, "dsr_wator_batch_step instantiate");
+        b->exec = nullptr;
+        return DSR_E_CUDA;
+    }
+    b->exec_epoch = b->group->epoch;
+    return DSR_OK;
+}
+
+extern "C" int dsr_wator_batch_prepare(dsr_wator_batch* b) {
+    if (!b) return DSR_E_INVALID;
+    return ensure_graph(b);
+}
+
 extern "C" int dsr_wator_batch_step(dsr_wator_batch* b, int n_steps, void* stream) {
     if (!b || n_steps < 0) return DSR_E_INVALID;
-    if (b->exec_epoch != b->group->epoch) {
-        if (b->exec) cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
-        if (e) {
-            dsr__set_cuda_error(e, "dsr_wator_batch_step capture");
-            return DSR_E_CUDA;
-        }
-        const int rc = issue_batch_step(b, b->capture);
-        e = cudaStreamEndCapture(b->capture, &graph);
-        if (rc) {
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-        if (!e) e = cudaGraphInstantiate(&b->exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        if (e) {
-            dsr__set_cuda_error(e, "dsr_wator_batch_step instantiate");
-            b->exec = nullptr;
-            return DSR_E_CUDA;
-        }
-        b->exec_epoch = b->group->epoch;
-    }
+    const int rc = ensure_graph(b);
+    if (rc) return rc;
     cudaStream_t s = dsr__stream(stream);
     for (int i = 0; i < n_steps; ++i) {
         cudaError_t e = cudaGraphLaunch(b->exec, s);
@@ -755,6 +795,7 @@ extern "C" int dsr_wator_batch_destroy(dsr_wator_batch* b) {
     if (!b) return DSR_E_INVALID;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     cudaStreamDestroy(b->capture);
+    if (b->table_pooled) dsr__group_give_bytes(b->group, b->table_d, table_bytes((int)b->table_h.size()));
     dsr_group_destroy(b->group);
     delete b;
     return DSR_OK;

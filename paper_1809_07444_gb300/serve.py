@@ -1,15 +1,22 @@
 """Serving: continuous batching of game-of-life and wa-tor jobs on one GPU.
 
 Jobs arrive over time (a Poisson stream), each with its application, grid
-side, step count and seed. A job is admitted as soon as its heap and
-workspace fit in the free bytes of its application's arena (first fit; jobs
-that do not fit wait, later smaller jobs may pass them). Admitted jobs stay
-resident on the device and advance together: one tick is one batched step of
-every resident wa-tor job and one batched generation of every resident
-game-of-life job (group do-alls replayed from a CUDA graph). A job that has
-done its steps leaves at the tick boundary: its final state hash is queued on
-the stream and its bytes are returned, so the next waiting job can start on
-the following tick.
+side, step count and seed. Both applications draw on one device arena (a
+wa-tor batch and a game-of-life batch sharing its free bytes). A job is
+admitted as soon as its heap and workspace fit in the arena's free bytes
+(first fit; jobs that do not fit wait, later smaller jobs may pass them).
+Admitted jobs stay resident on the device and advance together: one tick is
+one batched step of every resident wa-tor job and one batched generation of
+every resident game-of-life job (group do-alls replayed from a CUDA graph).
+A job that has done its steps leaves at the tick boundary: its final state
+hash is read and its bytes are returned, so the next waiting job can start
+on the following tick.
+
+Per tick the report separates the device time of the batched step
+(step_ms, CUDA events around the graph replays alone) from the host time
+spent changing the resident set: admitting jobs (their initial state copied
+in and created on the device) and re-capturing the step graphs when the set
+changed (admit_ms), and retiring finished jobs (retire_ms).
 
 Host code here only schedules (admission, retirement, bookkeeping); every
 step runs in libdsr.so.
@@ -28,11 +35,14 @@ WATOR, GOL = 1, 0
 
 
 class Server:
-    def __init__(self, arena_bytes=64 << 30, gol_fraction=0.4, max_jobs=4096, tuning=None):
-        self.wb = WatorBatch(int(arena_bytes * (1 - gol_fraction)) // 1024 * 1024, max_instances=max_jobs,
-                             tuning=tuning)
-        self.gb = GolBatch(int(arena_bytes * gol_fraction) // 1024 * 1024, max_instances=max_jobs, tuning=tuning)
+    def __init__(self, arena_bytes=64 << 30, max_jobs=4096, tuning=None):
+        self.wb = WatorBatch(int(arena_bytes) // 1024 * 1024, max_instances=max_jobs, tuning=tuning)
+        self.gb = GolBatch(share=self.wb, max_instances=max_jobs, tuning=tuning)
         self.stream = torch.cuda.current_stream()
+
+    def free_bytes(self):
+        """(free bytes, largest free range) of the shared arena."""
+        return self.wb.free_bytes()
 
     @staticmethod
     def _initial(job):
@@ -80,6 +90,7 @@ class Server:
         resident = {}  # (app, slot) -> [job, steps_left, admitted_at]
         done = []
         ticks = []  # (start event, end event, resident count)
+        admit_ms, retire_ms = [], []  # host time of ticks that changed the resident set
         t0 = time.perf_counter()
         visits = 0
 
@@ -95,6 +106,7 @@ class Server:
                 waiting.append(pending.popleft())
             # admission: first fit in arrival order among jobs whose initial
             # state is ready, bounded per tick
+            t_adm = time.perf_counter()
             admitted = 0
             kept = collections.deque()
             while waiting and admitted < max_admit_per_tick:
@@ -118,6 +130,15 @@ class Server:
                 elif waiting:
                     time.sleep(0.001)  # initial states still being generated
                 continue
+            # re-capture the step graphs now if the resident set changed, so
+            # that the tick's events time the replays alone
+            if self.wb.inst:
+                self.wb.prepare()
+            if self.gb.inst:
+                self.gb.prepare()
+            if admitted:
+                self.stream.synchronize()  # the admitted jobs' initial states are created
+                admit_ms.append((time.perf_counter() - t_adm) * 1e3)
             # one tick: a batched step of each application that has jobs
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(self.stream)
@@ -135,6 +156,7 @@ class Server:
             if finished:
                 b.synchronize()
                 t_done = now()
+                t_ret = time.perf_counter()
                 for key in finished:
                     app, slot = key
                     job, _, t_adm = resident.pop(key)
@@ -146,24 +168,33 @@ class Server:
                     done.append({"id": job["id"], "app": app, "side": int(job["side"]), "steps": int(job["steps"]),
                                  "seed": int(job["seed"]), "arrival": float(job["arrival"]), "admitted": t_adm,
                                  "completed": t_done, "hash": h})
+                retire_ms.append((time.perf_counter() - t_ret) * 1e3)
         pool.shutdown(wait=False, cancel_futures=True)
         torch.cuda.synchronize()
         wall = now()
         step_ms = [x.elapsed_time(y) for x, y, _ in ticks]
         for key, rec in resident.items():  # count the work of jobs still resident
             visits += self._batch(key[0]).heap(key[1]).counters()["visits"]
-        return {"done": done, "step_ms": step_ms, "wall_s": wall, "visits": visits,
+        return {"done": done, "step_ms": step_ms, "resident": [k for _, _, k in ticks], "admit_ms": admit_ms,
+                "retire_ms": retire_ms, "wall_s": wall, "visits": visits,
                 "unfinished": len(resident) + len(waiting) + len(pending)}
 
 
 def summarize(report):
-    """p50/p99 per-step and per-job latency, throughput."""
-    step = np.array(report["step_ms"]) if report["step_ms"] else np.zeros(1)
-    lat = np.array([d["completed"] - d["arrival"] for d in report["done"]]) if report["done"] else np.zeros(1)
+    """p50/p99 per-step (device) and per-job latency, the host time of
+    admissions and retirements, throughput."""
+    def pct(xs, q):
+        return float(np.percentile(np.array(xs), q)) if len(xs) else 0.0
+
+    lat = [d["completed"] - d["arrival"] for d in report["done"]]
     return {
         "jobs_done": len(report["done"]), "jobs_unfinished": report["unfinished"], "ticks": len(report["step_ms"]),
-        "step_ms_p50": float(np.percentile(step, 50)), "step_ms_p99": float(np.percentile(step, 99)),
-        "job_s_p50": float(np.percentile(lat, 50)), "job_s_p99": float(np.percentile(lat, 99)),
+        "step_ms_p50": pct(report["step_ms"], 50), "step_ms_p99": pct(report["step_ms"], 99),
+        "job_s_p50": pct(lat, 50), "job_s_p99": pct(lat, 99),
+        "admit_ms_p50": pct(report.get("admit_ms", []), 50), "admit_ms_p99": pct(report.get("admit_ms", []), 99),
+        "retire_ms_p50": pct(report.get("retire_ms", []), 50),
+        "retire_ms_p99": pct(report.get("retire_ms", []), 99),
+        "resident_p50": pct(report.get("resident", []), 50), "resident_max": max(report.get("resident", [0]) or [0]),
         "object_updates_per_s": report["visits"] / report["wall_s"] if report["wall_s"] else 0.0,
         "wall_s": report["wall_s"],
     }

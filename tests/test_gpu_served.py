@@ -30,7 +30,7 @@ def _oracle_hash(job):
 def test_served_jobs_match_oracle_and_queue_for_memory():
     jobs = _jobs(30, 3)
     # small arenas: not every job fits at once, so jobs wait for others to leave
-    srv = Server(arena_bytes=6 << 20, gol_fraction=0.4, max_jobs=64)
+    srv = Server(arena_bytes=6 << 20, max_jobs=64)
     rep = srv.run(jobs, realtime=False)
     assert rep["unfinished"] == 0 and len(rep["done"]) == len(jobs)
     waited = [d for d in rep["done"] if d["admitted"] > 0.0 and d["admitted"] > min(x["completed"] for x in rep["done"])]
@@ -39,6 +39,42 @@ def test_served_jobs_match_oracle_and_queue_for_memory():
         assert tuple(d["hash"]) == _oracle_hash(d), "job %d (app %d side %d)" % (d["id"], d["app"], d["side"])
     s = summarize(rep)
     assert s["jobs_done"] == 30 and s["step_ms_p99"] >= s["step_ms_p50"] > 0
+
+
+def test_one_arena_serves_either_application():
+    # the two applications draw on one pool of bytes: game-of-life instances
+    # alone fill most of the arena, and the bytes they return on leaving are
+    # what a wa-tor instance is then admitted into
+    srv = Server(arena_bytes=96 << 20, max_jobs=256)
+    total = srv.free_bytes()[0]
+    slots = []
+    while True:
+        slot = srv.gb.add(128, 128, WL.gol_initial(128, 128, len(slots)))
+        if slot is None:
+            break
+        slots.append(slot)
+    assert len(slots) > 4
+    assert total - srv.free_bytes()[0] > 0.8 * total
+    k0 = WL.wator_initial(256, 256, 1)
+    assert srv.wb.add(256, 256, k0, 1) is None
+    for slot in slots:
+        srv.gb.remove(slot)
+    assert srv.free_bytes()[0] == total
+    w = srv.wb.add(256, 256, k0, 1)
+    assert w is not None
+    ref = O.Wator(256, 256, k0, seed=1)
+    srv.wb.step(5)
+    ref.step(5)
+    assert srv.wb.hash(w) == ref.hash()
+
+
+def test_tick_report_separates_device_step_and_host_admission():
+    jobs = _jobs(20, 11)
+    rep = Server(arena_bytes=64 << 20, max_jobs=64).run(jobs, realtime=False)
+    s = summarize(rep)
+    assert s["jobs_done"] == 20 and len(rep["admit_ms"]) >= 1 and len(rep["retire_ms"]) >= 1
+    assert s["admit_ms_p99"] >= s["admit_ms_p50"] > 0 and s["step_ms_p50"] > 0
+    assert len(rep["resident"]) == s["ticks"] and s["resident_max"] >= 1
 
 
 def test_job_result_alone_equals_result_in_mix():

@@ -31,17 +31,29 @@ class FakeHeap:
         return {"visits": self.v}
 
 
-class FakeBatch:
-    """Capacity in cells: a job of side s needs s * s."""
+class FakeStream:
+    def synchronize(self):
+        pass
 
-    def __init__(self, capacity):
+
+class FakeBatch:
+    """Capacity in cells: a job of side s needs s * s. Batches made with
+    share=other draw on the other's capacity (one arena)."""
+
+    def __init__(self, capacity, share=None):
         self.capacity = capacity
         self.inst = {}  # slot -> (side, ticks stepped)
         self.next = 0
         self.log = []
+        self.peers = share.peers if share else []
+        self.peers.append(self)
+        self.prepared = 0
 
     def used(self):
-        return sum(s * s for s, _ in self.inst.values())
+        return sum(s * s for b in self.peers for s, _ in b.inst.values())
+
+    def prepare(self):
+        self.prepared += 1
 
     def add(self, W, H, start, seed=None):
         if self.used() + W * H > self.capacity:
@@ -68,11 +80,11 @@ class FakeBatch:
         del self.inst[slot]
 
 
-def _server(capacity):
+def _server(capacity, shared=False):
     s = serve.Server.__new__(serve.Server)
     s.wb = FakeBatch(capacity)
-    s.gb = FakeBatch(capacity)
-    s.stream = None
+    s.gb = FakeBatch(capacity, share=s.wb if shared else None)
+    s.stream = FakeStream()
     return s
 
 
@@ -131,3 +143,25 @@ def test_summary_of_a_report():
     out = serve.summarize(rep)
     assert out["jobs_done"] == 4 and out["jobs_unfinished"] == 0 and out["ticks"] == len(rep["step_ms"]) > 0
     assert out["step_ms_p50"] == 1.0
+
+
+def test_one_pool_for_both_applications():
+    # with one shared arena a stream of one application can use all of it,
+    # and the other application's jobs wait for those bytes
+    s = _server(capacity=4 * 32 * 32, shared=True)
+    jobs = [_job(i, 32, 3, app=serve.GOL) for i in range(4)] + [_job(9, 32, 2, app=serve.WATOR)]
+    rep = s.run(jobs, realtime=False, workers=1)
+    assert rep["unfinished"] == 0
+    done = {d["id"]: d for d in rep["done"]}
+    assert all(done[i]["admitted"] <= done[9]["admitted"] for i in range(4))
+    assert done[9]["admitted"] >= min(done[i]["completed"] for i in range(4))
+    assert s.gb.prepared > 0 and s.wb.prepared > 0
+
+
+def test_report_times_admissions_and_retirements():
+    s = _server(capacity=10 ** 9)
+    rep = s.run([_job(i, 8, 2 + i) for i in range(5)], realtime=False, workers=1)
+    out = serve.summarize(rep)
+    assert len(rep["admit_ms"]) >= 1 and len(rep["retire_ms"]) >= 1
+    assert out["admit_ms_p99"] >= out["admit_ms_p50"] >= 0 and 1 <= out["resident_max"] <= 5
+    assert len(rep["resident"]) == out["ticks"]
