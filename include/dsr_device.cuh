@@ -99,16 +99,21 @@ __device__ __forceinline__ dsr_u64 dsr_ld_relaxed(const dsr_u64* p) {
     return v;
 }
 
-/* 64-bit atomics with acquire/release ordering (PTX memory model), used where
- * a block's object bitmap publishes or guards its type byte. */
-__device__ __forceinline__ dsr_u64 dsr_atom_and_acq_rel(dsr_u64* p, dsr_u64 v) {
+/* 64-bit atomics with acquire or release ordering (PTX memory model), used
+ * where a block's object bitmap publishes or guards its type byte. The
+ * atomics that take a block's slots (reserve) or lock an empty block
+ * (reclaim) need only acquire: the type read and the bitmap updates that
+ * follow them must not be performed before them, while nothing before them
+ * is published through them. Acquire without release spares the memory
+ * barrier ahead of the atomic, which an allocation would wait on. */
+__device__ __forceinline__ dsr_u64 dsr_atom_and_acquire(dsr_u64* p, dsr_u64 v) {
     dsr_u64 old;
-    asm volatile("atom.acq_rel.gpu.global.and.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    asm volatile("atom.acquire.gpu.global.and.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
     return old;
 }
-__device__ __forceinline__ dsr_u64 dsr_atom_cas_acq_rel(dsr_u64* p, dsr_u64 cmp, dsr_u64 v) {
+__device__ __forceinline__ dsr_u64 dsr_atom_cas_acquire(dsr_u64* p, dsr_u64 cmp, dsr_u64 v) {
     dsr_u64 old;
-    asm volatile("atom.acq_rel.gpu.global.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "l"(p), "l"(cmp), "l"(v) : "memory");
+    asm volatile("atom.acquire.gpu.global.cas.b64 %0, [%1], %2, %3;" : "=l"(old) : "l"(p), "l"(cmp), "l"(v) : "memory");
     return old;
 }
 __device__ __forceinline__ void dsr_atom_exch_release(dsr_u64* p, dsr_u64 v) {
@@ -366,7 +371,7 @@ __device__ inline void dsr_release(const dsr_dev_heap& H, int T, dsr_u64 b, dsr_
         if (prev == 0) dsr_hb_set(H.active_bm[T], b, true, H.err);
         const dsr_u64 v = H.valid[T];
         if ((prev | bits) != v) return;
-        if (dsr_atom_cas_acq_rel(H.obj + b, v, 0ull) != v) return;
+        if (dsr_atom_cas_acquire(H.obj + b, v, 0ull) != v) return;
         const int T2 = dsr_block_type(H, b);  // ordered after the acquiring CAS
         dsr_hb_clear(H.active_bm[T2], b, true, H.err);
         if (H.valid[T2] == v) {
@@ -464,7 +469,7 @@ __device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsi
         bool emptied = false;
         for (int r = 0; r < DSR_CHASE_ROUNDS && snap; ++r) {
             const dsr_u64 want = dsr_rotl(dsr_lowest_bits(dsr_rotr(snap, rot), k - __popcll(got)), rot);
-            const dsr_u64 prev = dsr_atom_and_acq_rel(w, ~want);
+            const dsr_u64 prev = dsr_atom_and_acquire(w, ~want);
             got |= prev & want;
             snap = prev & ~want;
             emptied = prev != 0 && snap == 0;  // this atomic left no free slot
