@@ -55,7 +55,7 @@ WORKLOAD = {"workload": "wator-2048x2048", "grid": [W_SIDE, W_SIDE], "fish": 0.3
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="dsr", choices=["dsr", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -951,8 +951,9 @@ def summary(line):
     for k in ("served", "served_small"):
         sv = line.get(k)
         if sv:
-            out[k] = {q: r3(sv.get(q)) for q in ("jobs_done", "step_ms_p50", "step_ms_p99", "job_s_p50",
-                                                  "job_s_p99", "admit_ms_p50", "admit_ms_p99")}
+            out[k] = {q: r3(sv.get(q)) for q in ("jobs_done", "step_ms_p50", "step_ms_p99", "step_ms_per_mcell_p50",
+                                                  "step_ms_per_mcell_p99", "job_s_p50", "job_s_p99",
+                                                  "admit_ms_per_job_p50", "admit_ms_per_job_p99")}
     return out
 
 

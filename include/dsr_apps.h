@@ -239,12 +239,17 @@ int dsr_wator_batch_destroy(dsr_wator_batch* b);
  * Close encounters amplify rounding: on the 65,536-body workload the FP32
  * pair mode stays within 1e-4 relative of an FP64 reference for 23 steps,
  * the FP64 pair mode for all 50.
- * Workspace (dsr_nbody_workspace_bytes): dense per-slot arrays for all
- * M * 64 slots of the heap, room for max(32 * M * 64, 2^20) near pairs (more
- * in one step sets DSR_ERR_CAPACITY; the excess pairs stay in the FP32 sum),
- * the slice buffers of the split all-pairs kernels (sized from the device's
- * SM count and the kernels' occupancy, so query it on the device that will
- * run the step), and a merge log of log_cap entries. */
+ * Each step sorts the live bodies by cell of a K^3 grid over the unit cube
+ * (cells at least as wide as r_near and r_merge, K <= 32; positions outside
+ * the cube fall in the border cells), so that tiles of the all-pairs sum are
+ * spatially compact: tiles far from a row skip the near test, and the near
+ * field and the merge-partner search look only at the 27 cells around a
+ * body. Every sum has a fixed order: a step is deterministic.
+ * Workspace (dsr_nbody_workspace_bytes): the cell counts and offsets, the
+ * sorted per-body arrays for all M * 64 slots of the heap (rounded up to
+ * 1024), the slice buffers of the split all-pairs kernels (sized from the
+ * device's SM count and the kernels' occupancy, so query it on the device
+ * that will run the step), and a merge log of log_cap entries. */
 #define DSR_NBODY_PAIRS_FP32 0
 #define DSR_NBODY_PAIRS_FP64 1
 typedef struct {
@@ -262,8 +267,8 @@ int dsr_nbody_step(dsr_nbody* nb, int n_steps, void* stream);
 /* Device pointers to the merge log (int32[log_cap][3]: step, survivor id,
  * absorbed id, in arbitrary order within a step) and its uint64 count. */
 int dsr_nbody_merge_log(dsr_nbody* nb, void** log_dev, void** count_dev);
-/* Device pointer to the uint32 count of near pairs (closer than r_near) the
- * last step found. */
+/* Device pointer to the uint32 count of near-field pairs (closer than r_near,
+ * each counted from both bodies) of the last step. */
 int dsr_nbody_near_pairs(dsr_nbody* nb, void** count_dev);
 int dsr_nbody_destroy(dsr_nbody* nb);
 
@@ -272,13 +277,12 @@ int dsr_nbody_destroy(dsr_nbody* nb);
  * that runs where device allocation is not allowed or not available, such as
  * a plugin that is handed its device memory by a host program that owns all
  * of it and forbids allocations of its own. Instead of a
- * caller-allocated workspace, the per-slot scratch of a step (dense
- * state before and after the update, ids, partners, far-field sums and
- * near-pair lists: 180 bytes per slot and 12 per near pair) and the step
- * counter live in a static device array inside this library, sized for
- * DSR_NOALLOC_MAX_SLOTS slots and DSR_NOALLOC_PAIRS_PER_SLOT near pairs per
- * slot (about 6.1 MB), which every GPU that loads the library holds until the
- * process exits. The call allocates nothing: no
+ * caller-allocated workspace, the scratch of a step (cell counts and
+ * offsets, 384 KB; the sorted state before and after the update, handles,
+ * partners and far-field sums, 188 bytes per slot) and the step counter live
+ * in a static device array inside this library, sized for
+ * DSR_NOALLOC_MAX_SLOTS slots (about 3.5 MB), which every GPU that loads the
+ * library holds until the process exits. The call allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine.
  *   heap        a heap whose type 0 is Body (dsr_nbody_types) and whose block
  *               count times 64 is at most DSR_NOALLOC_MAX_SLOTS; a larger
@@ -298,7 +302,6 @@ int dsr_nbody_destroy(dsr_nbody* nb);
  * that overlap on the GPU (other streams, or other threads) race, so order
  * them on one stream. */
 #define DSR_NOALLOC_MAX_SLOTS 16384
-#define DSR_NOALLOC_PAIRS_PER_SLOT 16
 int dsr_nbody_step_noalloc(dsr_heap* heap, const dsr_nbody_params* p, int n_steps, uint64_t step0, void* log_dev,
                            uint64_t log_cap, void* log_count_dev, void* stream);
 

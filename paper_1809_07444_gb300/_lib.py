@@ -16,7 +16,6 @@ MAX_LEVELS = 6
 
 OK, E_INVALID, E_OOM, E_CUDA, E_DEVICE, E_TOO_LARGE = 0, 1, 2, 3, 4, 5
 NOALLOC_MAX_SLOTS = 16384
-NOALLOC_PAIRS_PER_SLOT = 16
 CTR_COUNT = 8  # event counters per heap (DSR_CTR_COUNT)
 ERR_OOM, ERR_RETRY, ERR_DOUBLE_FREE, ERR_BAD_HANDLE, ERR_CAPACITY = 1, 2, 4, 8, 16
 

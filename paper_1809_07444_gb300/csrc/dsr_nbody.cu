@@ -2,19 +2,26 @@
 // and 6d "nbody"; Fig. 1 names an Euler time step).
 //
 // One step is a do-all over Body whose block list R is built once and shared
-// by the step's kernels (no body is created or deleted until the last one):
-//   gather   each listed slot writes its body's state to dense arrays indexed
-//            by g = R index * 64 + slot (empty slots: mass 0);
-//   force    a_i = G sum_j m_j d_ij / (|d_ij|^2 + eps^2)^(3/2) over all dense
-//            entries, tiled through shared memory;
-//   update   v += a dt, x += v dt (semi-implicit Euler), written to the
-//            object and to the dense arrays of the updated state;
-//   partner  on the updated positions, the partner of i is the body with the
-//            lowest id j != i within r_merge;
+// by the step's kernels (no body is created or deleted until the last one).
+// The live bodies are first put in spatial order: a counting sort by cell of
+// a K^3 grid over the unit cube (positions outside it fall in the border
+// cells), cells in Morton order, the bodies of a cell by id. On that order:
+//   gather   sorted position p holds its body's state and handle; each tile
+//            of 256 positions gets the bounding box of its bodies;
+//   force    a_i = G sum_j m_j d_ij / (|d_ij|^2 + eps^2)^(3/2), all pairs,
+//            tiled through shared memory (FP32 or FP64 pairs, below);
+//   update   the far-field slices summed, the near field added (FP32 pairs:
+//            pairs closer than r_near, found in the 27 cells around the
+//            body's own, in FP64), then v += a dt, x += v dt (semi-implicit
+//            Euler) in FP64, written to the object;
+//   partner  the bodies are sorted again by the cells of their new
+//            positions; the partner of i is the body with the lowest id
+//            j != i within r_merge, found in the 27 cells around i's;
 //   merge    mutual partners merge: the lower id takes the summed mass and
 //            the mass-weighted position and velocity, the higher id deletes
 //            itself.
-// The last kernel's last CTA resets R.
+// The last kernel's last CTA resets R. Every sum is taken in a fixed order
+// (positions, tiles, slices, cells and ids), so a step is deterministic.
 //
 // Precision. The state is stored as FP32 pairs: each of x, y, z, vx, vy, vz
 // and m is a high word (its FP32 value) and a low word (the FP32 rounding of
@@ -24,7 +31,7 @@
 //   FP32 pairs  the sum runs in FP32 on the high words, except for pairs
 //               closer than r_near (an FP32 test on the high words decides),
 //               which are left out of it and added in FP64 from the full
-//               state, in the order of the partners' ids;
+//               state;
 //   FP64 pairs  every pair in FP64 from the full state.
 // Close encounters amplify whatever error a step makes: rounding the stored
 // positions to FP32 alone gives two bodies 2e-3 apart a separation error of
@@ -43,6 +50,11 @@ enum { ID = 0, PX = 1, PY = 2, PZ = 3, VX = 4, VY = 5, VZ = 6, MASS = 7 };
 constexpr int LO = 7;  // field f's low word is field f + LO (f = PX .. MASS)
 constexpr int N_FIELDS = 15;
 constexpr int TILE = 256;
+constexpr int RB = 4;      // bodies per thread in the FP32 force kernel
+constexpr int RB64 = 2;    // bodies per thread in the FP64 force kernel
+constexpr int ROW = 1024;  // sorted positions are padded to a multiple of this (TILE * RB)
+constexpr int KMAX = 32;   // cells per axis at most
+constexpr uint32_t NKEYS = KMAX * KMAX * KMAX;  // Morton keys of 5-bit cell coordinates
 
 // Four doubles in one 32-byte aligned record (x, y, z, m or vx, vy, vz, 0).
 struct __align__(32) D4 {
@@ -51,27 +63,32 @@ struct __align__(32) D4 {
 __device__ __forceinline__ D4 d4(double x, double y, double z, double w) { return D4{x, y, z, w}; }
 
 struct NbWs {
-    float4* pos;       // [S] high words x, y, z, m before the update (m = 0: empty slot)
-    D4* pd;            // [S] full x, y, z, m before the update
-    float4* npos;      // [S] high words x, y, z, m after the update
-    D4* npd;           // [S] full x, y, z, m after the update
-    D4* nvd;           // [S] full vx, vy, vz after the update
-    int32_t* id;       // [S] body id, INT_MAX for an empty slot
-    int32_t* partner;  // [S] dense index of the partner, -1 if none
-    float4* part;      // [ns][stride] FP32 far-field sums per slice of j tiles
-    D4* part64;        // [ns][stride] FP64 sums per slice (FP64 pairs; the same bytes as part)
-    int2* pbest;       // [ns][stride] lowest partner id and its index per slice (split kernels)
-    uint32_t* ncnt;    // [S] near pairs of body g
-    uint32_t* noff;    // [S + 1] exclusive prefix sum of ncnt
-    uint32_t* ncur;    // [S] fill cursors
-    int2* pairs;       // [pair_cap] near pairs (i, j), in the order they were found
-    int32_t* csr;      // [pair_cap] j of the near pairs, grouped by i
-    uint32_t* npairs;  // near pairs found this step
+    // spatial order
+    uint32_t* ccount;  // [NKEYS] bodies per cell (zero between sorts)
+    uint32_t* coff;    // [NKEYS + 1] first sorted position of each cell (positions before the update)
+    uint32_t* coff2;   // [NKEYS + 1] the same for the positions after the update
+    uint32_t* ckey;    // [P] cell key of each element being sorted
+    uint32_t* perm;    // [P] dense slot of each sorted position
+    uint32_t* perm2;   // [P] sorted position of each entry of the second order
+    uint32_t* n_live;  // bodies in this step
+    uint32_t* npairs;  // near-field pairs of this step (each counted from both bodies)
+    // per sorted position p (padded to a multiple of ROW with empty entries)
+    float4* pos;       // high words x, y, z, m before the update (m = 0: empty)
+    D4* pd;            // full x, y, z, m before the update
+    int32_t* id;       // body id, INT_MAX for an empty entry
+    dsr_u64* sref;     // the body's handle
+    float4* tbox;      // [2 per tile] bounding box (low corner, high corner) of a tile's bodies
+    float4* npos;      // high words x, y, z, m after the update
+    D4* npd;           // full x, y, z, m after the update
+    D4* nvd;           // full vx, vy, vz after the update
+    int32_t* partner;  // sorted position of the partner, -1 if none
+    float4* part;      // [ns][P] FP32 far-field sums per slice of j tiles
+    D4* part64;        // [ns][P] FP64 sums per slice (FP64 pairs; the same bytes as part)
     int32_t* log;      // [log_cap][3] merges: step, survivor id, absorbed id
     dsr_u64* log_n;    // merges logged so far
     dsr_u64* step;     // device step counter
     dsr_u64 log_cap;
-    uint32_t pair_cap;
+    int32_t K;         // cells per axis
 };
 
 struct NbArgs {
@@ -93,10 +110,6 @@ __device__ __forceinline__ void put2(const dsr_dev_heap& H, dsr_ref r, int f, do
     *fld(H, r, f + LO) = __double2float_rn(v - (double)hi);
 }
 
-__device__ __forceinline__ float4 ws_load(const float4* p, uint32_t g, uint32_t n) {
-    return g < n ? p[g] : make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
 // Compensated (Kahan) accumulation: s += x with the lost low part kept in c.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     const float y = x - c;
@@ -115,22 +128,181 @@ __device__ __forceinline__ dsr_ref slot_ref(const dsr_dev_heap& H, uint32_t g) {
     return ((dsr_u64)H.R_bid[g >> 6] << 6) | (g & 63);
 }
 
-__global__ void k_gather(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbWs ws) {
-    const uint32_t n = n_dense(H);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *ws.npairs = 0;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
-        ws.ncnt[g] = 0;
-        if (slot_live(H, g)) {
-            const dsr_ref r = slot_ref(H, g);
-            ws.pos[g] = make_float4(*fld(H, r, PX), *fld(H, r, PY), *fld(H, r, PZ), *fld(H, r, MASS));
-            ws.pd[g] = d4(get2(H, r, PX), get2(H, r, PY), get2(H, r, PZ), get2(H, r, MASS));
-            ws.id[g] = *dsr_field<int32_t>(H, BODY, r, ID);
+__device__ __forceinline__ uint32_t n_bodies(const NbWs& ws) { return *(volatile uint32_t*)ws.n_live; }
+// Sorted positions in use: the live bodies, padded to a whole row item.
+__device__ __forceinline__ uint32_t n_padded(const NbWs& ws) { return (n_bodies(ws) + ROW - 1) / ROW * ROW; }
+
+// ---------------------------------------------------------------------------
+// spatial order
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_coord(float x, int K) {
+    const float c = floorf(x * (float)K);  // monotone in x: bodies closer than a cell's width are in adjacent cells
+    return c < 0.f ? 0 : (c >= (float)K ? K - 1 : (int)c);
+}
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 5 bits to every third bit
+    uint32_t r = 0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+}
+__device__ __forceinline__ uint32_t cell_key(int cx, int cy, int cz) {
+    return spread3((uint32_t)cx) | (spread3((uint32_t)cy) << 1) | (spread3((uint32_t)cz) << 2);
+}
+__device__ __forceinline__ uint32_t cell_of(float x, float y, float z, int K) {
+    return cell_key(cell_coord(x, K), cell_coord(y, K), cell_coord(z, K));
+}
+
+// Count the elements of each cell. POST = false: the live dense slots (the
+// heap's state before the update); POST = true: the sorted positions below
+// n_live (the updated positions).
+template <bool POST>
+__global__ void k_cell_count(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbWs ws) {
+    const uint32_t n = POST ? n_bodies(ws) : n_dense(H);
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        uint32_t c;
+        if (POST) {
+            const float4 u = ws.npos[e];
+            c = cell_of(u.x, u.y, u.z, ws.K);
         } else {
-            ws.pos[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-            ws.pd[g] = d4(0.0, 0.0, 0.0, 0.0);
-            ws.id[g] = 0x7FFFFFFF;
+            if (!slot_live(H, e)) continue;
+            const dsr_ref r = slot_ref(H, e);
+            c = cell_of(*fld(H, r, PX), *fld(H, r, PY), *fld(H, r, PZ), ws.K);
+        }
+        ws.ckey[e] = c;
+        atomicAdd(ws.ccount + c, 1u);
+    }
+}
+
+// Exclusive prefix sum of the cell counts (one CTA of 1024 threads, each
+// summing 32 consecutive cells). For the first order the total is the live
+// body count, and the step's near-pair count starts at 0.
+__global__ void __launch_bounds__(1024) k_cell_scan(const __grid_constant__ NbWs ws, int post) {
+    __shared__ uint32_t part[1024];
+    constexpr uint32_t PER = NKEYS / 1024;
+    uint32_t* coff = post ? ws.coff2 : ws.coff;
+    const uint32_t lo = threadIdx.x * PER;
+    uint32_t s = 0;
+    for (uint32_t c = lo; c < lo + PER; ++c) s += ws.ccount[c];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (uint32_t d = 1; d < 1024; d <<= 1) {  // inclusive scan of the run sums
+        const uint32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (uint32_t c = lo; c < lo + PER; ++c) {
+        coff[c] = run;
+        run += ws.ccount[c];
+    }
+    if (threadIdx.x == 1023) {
+        coff[NKEYS] = part[1023];
+        if (!post) {
+            *ws.n_live = part[1023];
+            *ws.npairs = 0;
         }
     }
+}
+
+// Place every counted element in its cell's range (in arbitrary order within
+// the cell); the counts return to zero.
+template <bool POST>
+__global__ void k_cell_place(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbWs ws) {
+    const uint32_t n = POST ? n_bodies(ws) : n_dense(H);
+    const uint32_t* coff = POST ? ws.coff2 : ws.coff;
+    uint32_t* out = POST ? ws.perm2 : ws.perm;
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        if (!POST && !slot_live(H, e)) continue;
+        const uint32_t c = ws.ckey[e];
+        out[coff[c] + atomicSub(ws.ccount + c, 1u) - 1u] = e;
+    }
+}
+
+// Id of a placed element: of the body in dense slot e, or at sorted position e.
+template <bool POST>
+__device__ __forceinline__ int32_t elem_id(const dsr_dev_heap& H, const NbWs& ws, uint32_t e) {
+    return POST ? ws.id[e] : *dsr_field<int32_t>(H, BODY, slot_ref(H, e), ID);
+}
+
+// The elements of each cell in order of body id (ids are unique): one thread
+// per cell, insertion sort.
+template <bool POST>
+__global__ void k_cell_order(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbWs ws) {
+    const uint32_t* coff = POST ? ws.coff2 : ws.coff;
+    uint32_t* seg = POST ? ws.perm2 : ws.perm;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < NKEYS; c += gridDim.x * blockDim.x) {
+        const uint32_t a = coff[c], b = coff[c + 1];
+        for (uint32_t u = a + 1; u < b; ++u) {
+            const uint32_t x = seg[u];
+            const int32_t key = elem_id<POST>(H, ws, x);
+            uint32_t v = u;
+            while (v > a && elem_id<POST>(H, ws, seg[v - 1]) > key) {
+                seg[v] = seg[v - 1];
+                --v;
+            }
+            seg[v] = x;
+        }
+    }
+}
+
+// Sorted positions: one CTA per tile of 256. Each position gets its body's
+// state (or an empty entry past the live bodies), each tile the bounding box
+// of its bodies' high-word positions (empty: low corner +FLT_MAX).
+__global__ void __launch_bounds__(TILE) k_gather(const __grid_constant__ dsr_dev_heap H,
+                                                 const __grid_constant__ NbWs ws) {
+    __shared__ float red[6][TILE / 32];
+    const uint32_t nl = n_bodies(ws), np = n_padded(ws);
+    for (uint32_t t = blockIdx.x; t * TILE < np; t += gridDim.x) {
+        const uint32_t p = t * TILE + threadIdx.x;
+        float b[6] = {FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+        if (p < nl) {
+            const dsr_ref r = slot_ref(H, ws.perm[p]);
+            const float4 u = make_float4(*fld(H, r, PX), *fld(H, r, PY), *fld(H, r, PZ), *fld(H, r, MASS));
+            ws.pos[p] = u;
+            ws.pd[p] = d4(get2(H, r, PX), get2(H, r, PY), get2(H, r, PZ), get2(H, r, MASS));
+            ws.id[p] = *dsr_field<int32_t>(H, BODY, r, ID);
+            ws.sref[p] = r;
+            b[0] = b[3] = u.x, b[1] = b[4] = u.y, b[2] = b[5] = u.z;
+        } else {
+            ws.pos[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+            ws.pd[p] = d4(0.0, 0.0, 0.0, 0.0);
+            ws.id[p] = 0x7FFFFFFF;
+            ws.sref[p] = DSR_NULL;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const float v = __shfl_xor_sync(0xFFFFFFFFu, b[k], o);
+                b[k] = k < 3 ? fminf(b[k], v) : fmaxf(b[k], v);
+            }
+        }
+        __syncthreads();  // the previous tile's reduction has been read
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) red[k][threadIdx.x >> 5] = b[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int w = 1; w < TILE / 32; ++w)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) b[k] = k < 3 ? fminf(b[k], red[k][w]) : fmaxf(b[k], red[k][w]);
+            ws.tbox[2 * t] = make_float4(b[0], b[1], b[2], 0.f);
+            ws.tbox[2 * t + 1] = make_float4(b[3], b[4], b[5], 0.f);
+        }
+    }
+}
+
+// True unless every pair between the boxes [la, ha] and [lb, hb] is at least
+// r_near apart, with room for the rounding of the FP32 r^2 (the near test
+// then fails for all of them). Empty boxes are far from everything.
+__device__ __forceinline__ bool boxes_near(float4 la, float4 ha, float4 lb, float4 hb, float rn2) {
+    if (!(rn2 > 0.f) || la.x > ha.x || lb.x > hb.x) return false;
+    const float dx = fmaxf(0.f, fmaxf(lb.x - ha.x, la.x - hb.x));
+    const float dy = fmaxf(0.f, fmaxf(lb.y - ha.y, la.y - hb.y));
+    const float dz = fmaxf(0.f, fmaxf(lb.z - ha.z, la.z - hb.z));
+    return !(dx * dx + dy * dy + dz * dz >= rn2 * 1.0001f);
 }
 
 // 1/sqrt(x) by the PTX approximate reciprocal square root with subnormal
@@ -142,170 +314,176 @@ __device__ __forceinline__ float rsqrt_normal(float x) {
     return y;
 }
 
-// A near pair (i, j), found by the thread of body i: recorded for the FP64
-// near field. Returns false when the pair list is full (the pair then stays
-// in the FP32 sum, and the heap's DSR_ERR_CAPACITY bit reports it).
-__device__ __forceinline__ bool near_record(const dsr_dev_heap& H, const NbWs& ws, uint32_t gi, uint32_t gj) {
-    const uint32_t k = atomicAdd(ws.npairs, 1u);
-    if (k >= ws.pair_cap) {
-        atomicOr(H.err, DSR_ERR_CAPACITY);
-        return false;
-    }
-    ws.pairs[k] = make_int2((int)gi, (int)gj);
-    atomicAdd(ws.ncnt + gi, 1u);
-    return true;
-}
-
-// The rare branch of the force kernels: body gi lies within r_near of body
-// gj. The pair is recorded for the FP64 near field and must then be left out
-// of the FP32 sum (true); so must the body itself, whose term is 0 either
-// way. False: the pair stays in the FP32 sum (an empty slot, or a full list).
-__device__ __forceinline__ bool near_pair(const dsr_dev_heap& H, const NbWs& ws, uint32_t gi, uint32_t gj, float mj,
-                                          uint32_t n) {
-    if (gi == gj) return true;
-    if (gi >= n || mj <= 0.f || ws.pos[gi].w <= 0.f) return false;
-    return near_record(H, ws, gi, gj);
-}
-
 __device__ __forceinline__ float f_inf() { return __int_as_float(0x7F800000); }
 
-// Split all-pairs kernels, the ones dsr_nbody_step runs.
-//
-// Work items. A row item is TILE * RB bodies (RB per thread), the j tiles are
-// cut into `ns` slices, and a work item is one (row item, slice) pair; `ns`
-// follows from the dense count on the device (n_slices), so the items fill
-// about `grid` CTAs whatever the live count. Each item writes its partial
-// result to part[slice][g] (pbest for the partner search); the update and the
-// partner combine read the slices back in slice order, so the result does not
-// depend on which CTA ran which item.
+// The FP32 pair test shared by the force kernels and the near field: the
+// near field takes exactly the pairs the force kernels leave out.
+__device__ __forceinline__ float pair_r2(float4 pj, float px, float py, float pz, float eps2, float& dx, float& dy,
+                                         float& dz) {
+    dx = pj.x - px, dy = pj.y - py, dz = pj.z - pz;
+    return fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+}
+
+// ---------------------------------------------------------------------------
+// FP32 pair forces
+// ---------------------------------------------------------------------------
+// Split form. A row item is ROW = TILE * RB sorted positions (RB per thread:
+// position row * ROW + k * TILE + threadIdx.x), the j tiles are cut into
+// `ns` slices, and a work item is one (row item, slice) pair; `ns` follows
+// from the padded count on the device (n_slices), so the items fill about
+// `grid` CTAs whatever the live count. Each item writes its partial sums to
+// part[slice][p]; the update reads the slices back in slice order.
 //
 // Register blocking. Every lane of a warp reads the same j body from shared
-// memory (a broadcast), and at one body per thread the shared-memory return
-// path, not the FP32 pipe, sets the pace. With RB bodies per thread each
-// load feeds RB pairs.
-constexpr int RB = 4;  // bodies per thread in the split kernels
-
+// memory (a broadcast); with RB bodies per thread each load feeds RB pairs.
+//
+// Near tiles. A tile whose bounding box comes within r_near of the row's
+// runs the excluding loop: a pair closer than r_near (the same FP32 r^2 the
+// near field tests) gets r^2 = +inf, so rsqrt gives 0 and the pair adds
+// nothing. Other tiles run the plain loop. In spatial order few tiles are
+// near a row, and the choice is uniform across the CTA.
 __device__ __forceinline__ uint32_t n_slices(uint32_t nr, uint32_t nj, uint32_t grid) {
     if (!nr) return 0;
     const uint32_t k = grid / nr;
     return k < 1 ? 1 : (k > nj ? nj : k);
 }
 
-constexpr int RB64 = 2;  // bodies per thread in the FP64 kernel
-
 struct SplitShape {
-    uint32_t n, nj, nr, ns;  // dense count, j tiles, row items, slices
+    uint32_t n, nj, nr, ns;  // padded count, j tiles, row items, slices
 };
 
-// Work items of a split kernel with rb bodies per thread.
-__device__ __forceinline__ SplitShape split_shape(const dsr_dev_heap& H, uint32_t grid, int rb = RB) {
+__device__ __forceinline__ SplitShape split_shape(const NbWs& ws, uint32_t grid, int rb) {
     SplitShape q;
-    q.n = n_dense(H);
-    q.nj = (q.n + TILE - 1) / TILE;
-    q.nr = (q.n + TILE * rb - 1) / (TILE * rb);
+    q.n = n_padded(ws);
+    q.nj = q.n / TILE;
+    q.nr = q.n / (TILE * rb);
     q.ns = n_slices(q.nr, q.nj, grid);
     return q;
 }
 
-// FP32 far-field sums of one slice of j tiles for RB bodies per thread (body
-// k of a thread: row * TILE * RB + k * TILE + threadIdx.x), Kahan-compensated
-// across tiles. A pair within r_near goes to the near field (near_pair, a
-// branch that almost never runs: one compare per pair on the common path).
-// SOFT: eps^2 >= FLT_MIN, so r^2 >= eps^2 is a normal number for every pair,
-// the body itself included, and no zero-distance guard is needed.
+// One tile of j bodies for the thread's RB bodies, in chunks of CHUNK
+// pairs: a chunk is summed in FP32 and added to (a, c) with Kahan
+// compensation. In spatial order a tile's terms for a body point much the
+// same way, so a plain 256-term FP32 sum would round at the size of the
+// whole tile's pull; chunks bound that rounding to the size of 32 terms.
+constexpr int CHUNK = 32;
+
+template <bool SOFT, bool EXCLUDE>
+__device__ __forceinline__ void force_tile(const float4* sp, const float* px, const float* py, const float* pz,
+                                           float eps2, float rn2, float* ax, float* ay, float* az, float* cx,
+                                           float* cy, float* cz) {
+    for (int j0 = 0; j0 < TILE; j0 += CHUNK) {
+        float tx[RB], ty[RB], tz[RB];
+#pragma unroll
+        for (int k = 0; k < RB; ++k) tx[k] = ty[k] = tz[k] = 0.f;
+#pragma unroll 4
+        for (int j = j0; j < j0 + CHUNK; ++j) {
+            const float4 pj = sp[j];
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                float dx, dy, dz;
+                float r2 = pair_r2(pj, px[k], py[k], pz[k], eps2, dx, dy, dz);
+                if (EXCLUDE) r2 = r2 < rn2 ? f_inf() : r2;
+                const float inv = SOFT ? rsqrt_normal(r2) : (r2 > 0.f ? rsqrtf(r2) : 0.f);
+                const float w = pj.w * inv * inv * inv;
+                tx[k] = fmaf(w, dx, tx[k]);
+                ty[k] = fmaf(w, dy, ty[k]);
+                tz[k] = fmaf(w, dz, tz[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            kahan_add(ax[k], cx[k], tx[k]);
+            kahan_add(ay[k], cy[k], ty[k]);
+            kahan_add(az[k], cz[k], tz[k]);
+        }
+    }
+}
+
 template <bool SOFT>
-__global__ void __launch_bounds__(TILE) k_force_part(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbArgs a) {
+__global__ void __launch_bounds__(TILE) k_force_part(const __grid_constant__ dsr_dev_heap H,
+                                                     const __grid_constant__ NbArgs a) {
+    (void)H;
     __shared__ float4 sp[TILE];
-    const SplitShape q = split_shape(H, gridDim.x);
+    const SplitShape q = split_shape(a.ws, gridDim.x, RB);
     const float eps2 = (float)(a.p.eps * a.p.eps);
     const float rn2 = (float)(a.p.r_near * a.p.r_near);
     for (uint32_t item = blockIdx.x; item < q.nr * q.ns; item += gridDim.x) {
         const uint32_t row = item % q.nr, sl = item / q.nr;
-        const uint32_t g0 = row * TILE * RB + threadIdx.x;
+        const uint32_t g0 = row * ROW + threadIdx.x;
+        float4 rlo = a.ws.tbox[2 * RB * row], rhi = a.ws.tbox[2 * RB * row + 1];
+#pragma unroll
+        for (int k = 1; k < RB; ++k) {
+            const float4 l = a.ws.tbox[2 * (RB * row + k)], h = a.ws.tbox[2 * (RB * row + k) + 1];
+            rlo = make_float4(fminf(rlo.x, l.x), fminf(rlo.y, l.y), fminf(rlo.z, l.z), 0.f);
+            rhi = make_float4(fmaxf(rhi.x, h.x), fmaxf(rhi.y, h.y), fmaxf(rhi.z, h.z), 0.f);
+        }
         float px[RB], py[RB], pz[RB];
         float ax[RB], ay[RB], az[RB], cx[RB], cy[RB], cz[RB];
 #pragma unroll
         for (int k = 0; k < RB; ++k) {
-            const float4 u = ws_load(a.ws.pos, g0 + k * TILE, q.n);
+            const float4 u = a.ws.pos[g0 + k * TILE];
             px[k] = u.x, py[k] = u.y, pz[k] = u.z;
             ax[k] = ay[k] = az[k] = cx[k] = cy[k] = cz[k] = 0.f;
         }
         for (uint32_t t = q.nj * sl / q.ns; t < q.nj * (sl + 1) / q.ns; ++t) {
             __syncthreads();
-            sp[threadIdx.x] = ws_load(a.ws.pos, t * TILE + threadIdx.x, q.n);
+            sp[threadIdx.x] = a.ws.pos[t * TILE + threadIdx.x];
             __syncthreads();
-            float tx[RB], ty[RB], tz[RB];
-#pragma unroll
-            for (int k = 0; k < RB; ++k) tx[k] = ty[k] = tz[k] = 0.f;
-#pragma unroll 4
-            for (int j = 0; j < TILE; ++j) {
-                const float4 pj = sp[j];
-#pragma unroll
-                for (int k = 0; k < RB; ++k) {
-                    const float dx = pj.x - px[k], dy = pj.y - py[k], dz = pj.z - pz[k];
-                    float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-                    if (r2 < rn2 && near_pair(H, a.ws, g0 + k * TILE, t * TILE + j, pj.w, q.n)) r2 = f_inf();
-                    const float inv = SOFT ? rsqrt_normal(r2) : (r2 > 0.f ? rsqrtf(r2) : 0.f);
-                    const float w = pj.w * inv * inv * inv;
-                    tx[k] = fmaf(w, dx, tx[k]);
-                    ty[k] = fmaf(w, dy, ty[k]);
-                    tz[k] = fmaf(w, dz, tz[k]);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < RB; ++k) {
-                kahan_add(ax[k], cx[k], tx[k]);
-                kahan_add(ay[k], cy[k], ty[k]);
-                kahan_add(az[k], cz[k], tz[k]);
-            }
+            if (boxes_near(rlo, rhi, a.ws.tbox[2 * t], a.ws.tbox[2 * t + 1], rn2))
+                force_tile<SOFT, true>(sp, px, py, pz, eps2, rn2, ax, ay, az, cx, cy, cz);
+            else
+                force_tile<SOFT, false>(sp, px, py, pz, eps2, rn2, ax, ay, az, cx, cy, cz);
         }
-        float4* out = a.ws.part + (size_t)sl * q.nr * TILE * RB;
+        float4* out = a.ws.part + (size_t)sl * q.n;
 #pragma unroll
-        for (int k = 0; k < RB; ++k)
-            if (g0 + k * TILE < q.n) out[g0 + k * TILE] = make_float4(ax[k], ay[k], az[k], 0.f);
+        for (int k = 0; k < RB; ++k) out[g0 + k * TILE] = make_float4(ax[k], ay[k], az[k], 0.f);
     }
 }
 
-// Unsplit force kernel (the allocation-free step): one thread per dense slot,
-// one CTA per TILE slots, the same pair arithmetic and near-field rule as
-// k_force_part. The sums go to part[g] (a single slice).
-__global__ void __launch_bounds__(TILE) k_force(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbArgs a) {
+// Unsplit form (the allocation-free step): one thread per sorted position,
+// one CTA per tile of positions; the same pair test, exclusion and term.
+__global__ void __launch_bounds__(TILE) k_force(const __grid_constant__ dsr_dev_heap H,
+                                                const __grid_constant__ NbArgs a) {
+    (void)H;
     __shared__ float4 sp[TILE];
-    const uint32_t n = n_dense(H);
+    const uint32_t n = n_padded(a.ws);
     const uint32_t base = blockIdx.x * TILE;
     if (base >= n) return;
     const uint32_t g = base + threadIdx.x;
-    const float4 pi = ws_load(a.ws.pos, g, n);
+    const float4 pi = a.ws.pos[g];
+    const float4 rlo = a.ws.tbox[2 * blockIdx.x], rhi = a.ws.tbox[2 * blockIdx.x + 1];
     const float eps2 = (float)(a.p.eps * a.p.eps);
     const float rn2 = (float)(a.p.r_near * a.p.r_near);
     float ax = 0.f, ay = 0.f, az = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     for (uint32_t t0 = 0; t0 < n; t0 += TILE) {
         __syncthreads();
-        sp[threadIdx.x] = ws_load(a.ws.pos, t0 + threadIdx.x, n);
+        sp[threadIdx.x] = a.ws.pos[t0 + threadIdx.x];
         __syncthreads();
-        float tx = 0.f, ty = 0.f, tz = 0.f;
-        for (int j = 0; j < TILE; ++j) {
-            const float4 pj = sp[j];
-            const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-            if (r2 < rn2 && near_pair(H, a.ws, g, t0 + j, pj.w, n)) r2 = f_inf();
-            const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-            const float w = pj.w * inv * inv * inv;
-            tx = fmaf(w, dx, tx);
-            ty = fmaf(w, dy, ty);
-            tz = fmaf(w, dz, tz);
+        const bool near = boxes_near(rlo, rhi, a.ws.tbox[2 * (t0 / TILE)], a.ws.tbox[2 * (t0 / TILE) + 1], rn2);
+        for (int j0 = 0; j0 < TILE; j0 += CHUNK) {
+            float tx = 0.f, ty = 0.f, tz = 0.f;
+            for (int j = j0; j < j0 + CHUNK; ++j) {
+                float dx, dy, dz;
+                float r2 = pair_r2(sp[j], pi.x, pi.y, pi.z, eps2, dx, dy, dz);
+                if (near && r2 < rn2) r2 = f_inf();
+                const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                const float w = sp[j].w * inv * inv * inv;
+                tx = fmaf(w, dx, tx);
+                ty = fmaf(w, dy, ty);
+                tz = fmaf(w, dz, tz);
+            }
+            kahan_add(ax, cx, tx);
+            kahan_add(ay, cy, ty);
+            kahan_add(az, cz, tz);
         }
-        kahan_add(ax, cx, tx);
-        kahan_add(ay, cy, ty);
-        kahan_add(az, cz, tz);
     }
-    if (g < n) a.ws.part[g] = make_float4(ax, ay, az, 0.f);
+    a.ws.part[g] = make_float4(ax, ay, az, 0.f);
 }
 
-__device__ __forceinline__ D4 ws_load64(const D4* p, uint32_t g, uint32_t n) {
-    return g < n ? p[g] : d4(0.0, 0.0, 0.0, 0.0);
-}
-
+// ---------------------------------------------------------------------------
+// FP64 pair forces
+// ---------------------------------------------------------------------------
 // One FP64 pair term added to (ax, ay, az): body j at pj acting on a body at
 // (px, py, pz). A zero r^2 (a body on itself with eps = 0) adds nothing.
 __device__ __forceinline__ void pair64(const D4& pj, double px, double py, double pz, double eps2, double& ax,
@@ -319,12 +497,12 @@ __device__ __forceinline__ void pair64(const D4& pj, double px, double py, doubl
     az = fma(w, dz, az);
 }
 
-// FP64 pairs, split form: as k_force_part with RB64 bodies per thread, every
-// pair in FP64 from the full state; sums per slice in part64.
+// Split form, RB64 positions per thread, every pair in FP64.
 __global__ void __launch_bounds__(TILE) k_force_part64(const __grid_constant__ dsr_dev_heap H,
                                                        const __grid_constant__ NbArgs a) {
+    (void)H;
     __shared__ D4 sp[TILE];
-    const SplitShape q = split_shape(H, gridDim.x, RB64);
+    const SplitShape q = split_shape(a.ws, gridDim.x, RB64);
     const double eps2 = a.p.eps * a.p.eps;
     for (uint32_t item = blockIdx.x; item < q.nr * q.ns; item += gridDim.x) {
         const uint32_t row = item % q.nr, sl = item / q.nr;
@@ -332,13 +510,13 @@ __global__ void __launch_bounds__(TILE) k_force_part64(const __grid_constant__ d
         double px[RB64], py[RB64], pz[RB64], ax[RB64], ay[RB64], az[RB64];
 #pragma unroll
         for (int k = 0; k < RB64; ++k) {
-            const D4 u = ws_load64(a.ws.pd, g0 + k * TILE, q.n);
+            const D4 u = a.ws.pd[g0 + k * TILE];
             px[k] = u.x, py[k] = u.y, pz[k] = u.z;
             ax[k] = ay[k] = az[k] = 0.0;
         }
         for (uint32_t t = q.nj * sl / q.ns; t < q.nj * (sl + 1) / q.ns; ++t) {
             __syncthreads();
-            sp[threadIdx.x] = ws_load64(a.ws.pd, t * TILE + threadIdx.x, q.n);
+            sp[threadIdx.x] = a.ws.pd[t * TILE + threadIdx.x];
             __syncthreads();
 #pragma unroll 2
             for (int j = 0; j < TILE; ++j) {
@@ -347,113 +525,95 @@ __global__ void __launch_bounds__(TILE) k_force_part64(const __grid_constant__ d
                 for (int k = 0; k < RB64; ++k) pair64(pj, px[k], py[k], pz[k], eps2, ax[k], ay[k], az[k]);
             }
         }
-        D4* out = a.ws.part64 + (size_t)sl * q.nr * TILE * RB64;
+        D4* out = a.ws.part64 + (size_t)sl * q.n;
 #pragma unroll
-        for (int k = 0; k < RB64; ++k)
-            if (g0 + k * TILE < q.n) out[g0 + k * TILE] = d4(ax[k], ay[k], az[k], 0.0);
+        for (int k = 0; k < RB64; ++k) out[g0 + k * TILE] = d4(ax[k], ay[k], az[k], 0.0);
     }
 }
 
-// FP64 pairs, unsplit (the allocation-free step): one thread per dense slot.
+// Unsplit form (the allocation-free step).
 __global__ void __launch_bounds__(TILE) k_force64(const __grid_constant__ dsr_dev_heap H,
                                                   const __grid_constant__ NbArgs a) {
+    (void)H;
     __shared__ D4 sp[TILE];
-    const uint32_t n = n_dense(H);
+    const uint32_t n = n_padded(a.ws);
     const uint32_t base = blockIdx.x * TILE;
     if (base >= n) return;
     const uint32_t g = base + threadIdx.x;
-    const D4 pi = ws_load64(a.ws.pd, g, n);
+    const D4 pi = a.ws.pd[g];
     const double eps2 = a.p.eps * a.p.eps;
     double ax = 0.0, ay = 0.0, az = 0.0;
     for (uint32_t t0 = 0; t0 < n; t0 += TILE) {
         __syncthreads();
-        sp[threadIdx.x] = ws_load64(a.ws.pd, t0 + threadIdx.x, n);
+        sp[threadIdx.x] = a.ws.pd[t0 + threadIdx.x];
         __syncthreads();
         for (int j = 0; j < TILE; ++j) pair64(sp[j], pi.x, pi.y, pi.z, eps2, ax, ay, az);
     }
-    if (g < n) a.ws.part64[g] = d4(ax, ay, az, 0.0);
+    a.ws.part64[g] = d4(ax, ay, az, 0.0);
 }
 
-// Exclusive prefix sum of the near-pair counts (one CTA of 1024 threads, each
-// summing a contiguous run of bodies), and the fill cursors cleared.
-__global__ void __launch_bounds__(1024) k_near_scan(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbWs ws) {
-    __shared__ uint32_t part[1024];
-    const uint32_t n = n_dense(H);
-    const uint32_t per = (n + 1023) / 1024;
-    const uint32_t lo = threadIdx.x * per, hi = lo + per < n ? lo + per : n;
-    uint32_t s = 0;
-    for (uint32_t g = lo; g < hi; ++g) s += ws.ncnt[g];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (uint32_t d = 1; d < 1024; d <<= 1) {  // inclusive scan of the run sums
-        const uint32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    uint32_t run = part[threadIdx.x] - s;
-    for (uint32_t g = lo; g < hi; ++g) {
-        ws.noff[g] = run;
-        ws.ncur[g] = 0;
-        run += ws.ncnt[g];
-    }
-    if (threadIdx.x == 1023) ws.noff[n] = part[1023];
+// ---------------------------------------------------------------------------
+// update, partner search, merge
+// ---------------------------------------------------------------------------
+// Visit the sorted entries of the 27 cells around (and including) the cell
+// of (x, y, z), cells in a fixed order: fn(q) for each position q of the
+// first order, or (POST) for the position perm2[q] of each entry q of the
+// second order.
+template <bool POST, class F>
+__device__ __forceinline__ void for_neighbours(const NbWs& ws, float x, float y, float z, F fn) {
+    const int K = ws.K;
+    const int cx = cell_coord(x, K), cy = cell_coord(y, K), cz = cell_coord(z, K);
+    const uint32_t* coff = POST ? ws.coff2 : ws.coff;
+    for (int ix = cx > 0 ? cx - 1 : 0; ix <= (cx < K - 1 ? cx + 1 : K - 1); ++ix)
+        for (int iy = cy > 0 ? cy - 1 : 0; iy <= (cy < K - 1 ? cy + 1 : K - 1); ++iy)
+            for (int iz = cz > 0 ? cz - 1 : 0; iz <= (cz < K - 1 ? cz + 1 : K - 1); ++iz) {
+                const uint32_t c = cell_key(ix, iy, iz);
+                for (uint32_t q = coff[c]; q < coff[c + 1]; ++q) fn(POST ? ws.perm2[q] : q);
+            }
 }
 
-// Near pairs grouped by their body i (in arbitrary order within a group; the
-// update sorts each group by the partners' ids).
-__global__ void k_near_fill(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbWs ws) {
-    (void)H;
-    uint32_t m = *ws.npairs;
-    if (m > ws.pair_cap) m = ws.pair_cap;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
-        const int2 p = ws.pairs[k];
-        ws.csr[ws.noff[p.x] + atomicAdd(ws.ncur + p.x, 1u)] = p.y;
-    }
-}
-
-// The update of body g: the FP32 far-field slices summed in slice order (in
-// FP64), the near field in FP64 over the partners sorted by id, then
-// v += a dt and x += v dt on the full state, stored back as FP32 pairs.
-__device__ void update_body(const dsr_dev_heap& H, const NbArgs& a, uint32_t g, uint32_t ns, size_t stride,
-                            bool f64) {
-    const dsr_ref r = slot_ref(H, g);
+// The update of the body at sorted position p: the far-field slices summed
+// in slice order (in FP64); with FP32 pairs, the near field in FP64 over the
+// pairs the force kernels left out (the same FP32 test, on the cells around
+// the body); then v += a dt and x += v dt on the full state, stored back as
+// FP32 pairs. Returns the body's near pairs.
+__device__ uint32_t update_body(const dsr_dev_heap& H, const NbArgs& a, uint32_t p, uint32_t ns, size_t stride,
+                                bool f64) {
+    const dsr_ref r = a.ws.sref[p];
     double ax = 0.0, ay = 0.0, az = 0.0;
     for (uint32_t k = 0; k < ns; ++k) {
         if (f64) {
-            const D4 v = a.ws.part64[k * stride + g];
+            const D4 v = a.ws.part64[k * stride + p];
             ax += v.x;
             ay += v.y;
             az += v.z;
         } else {
-            const float4 v = a.ws.part[k * stride + g];
+            const float4 v = a.ws.part[k * stride + p];
             ax += (double)v.x;
             ay += (double)v.y;
             az += (double)v.z;
         }
     }
-    const D4 pi = a.ws.pd[g];
-    const double eps2 = a.p.eps * a.p.eps;
-    int32_t* seg = a.ws.csr + a.ws.noff[g];
-    const uint32_t cnt = a.ws.noff[g + 1] - a.ws.noff[g];
-    for (uint32_t u = 1; u < cnt; ++u) {  // insertion sort by id (ids are unique)
-        const int32_t x = seg[u];
-        const int32_t key = a.ws.id[x];
-        uint32_t v = u;
-        while (v > 0 && a.ws.id[seg[v - 1]] > key) {
-            seg[v] = seg[v - 1];
-            --v;
-        }
-        seg[v] = x;
-    }
-    for (uint32_t u = 0; u < cnt; ++u) {
-        const D4 pj = a.ws.pd[seg[u]];
-        const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-        const double r2 = dx * dx + dy * dy + dz * dz + eps2;
-        const double w = pj.w / (r2 * sqrt(r2));
-        ax += w * dx;
-        ay += w * dy;
-        az += w * dz;
+    const D4 pi = a.ws.pd[p];
+    const float rn2 = (float)(a.p.r_near * a.p.r_near);
+    uint32_t near = 0;
+    if (!f64 && rn2 > 0.f) {
+        const float4 u = a.ws.pos[p];
+        const float eps2 = (float)(a.p.eps * a.p.eps);
+        const double eps2d = a.p.eps * a.p.eps;
+        for_neighbours<false>(a.ws, u.x, u.y, u.z, [&](uint32_t q) {
+            if (q == p) return;
+            float dx, dy, dz;
+            if (!(pair_r2(a.ws.pos[q], u.x, u.y, u.z, eps2, dx, dy, dz) < rn2)) return;
+            const D4 pj = a.ws.pd[q];
+            const double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
+            const double r2 = ex * ex + ey * ey + ez * ez + eps2d;
+            const double w = pj.w / (r2 * sqrt(r2));
+            ax += w * ex;
+            ay += w * ey;
+            az += w * ez;
+            ++near;
+        });
     }
     const double G = a.p.G, dt = a.p.dt;
     const double vx = get2(H, r, VX) + G * ax * dt;
@@ -466,39 +626,29 @@ __device__ void update_body(const dsr_dev_heap& H, const NbArgs& a, uint32_t g, 
     put2(H, r, PX, x);
     put2(H, r, PY, y);
     put2(H, r, PZ, z);
-    a.ws.npos[g] = make_float4(*fld(H, r, PX), *fld(H, r, PY), *fld(H, r, PZ), *fld(H, r, MASS));
-    a.ws.npd[g] = d4(x, y, z, pi.w);
-    a.ws.nvd[g] = d4(vx, vy, vz, 0.0);
+    a.ws.npos[p] = make_float4(*fld(H, r, PX), *fld(H, r, PY), *fld(H, r, PZ), *fld(H, r, MASS));
+    a.ws.npd[p] = d4(x, y, z, pi.w);
+    a.ws.nvd[p] = d4(vx, vy, vz, 0.0);
+    return near;
 }
 
-// Update of every live body; `grid` is the split force kernel's grid (0: the
+// Update of every body; `grid` is the split force kernel's grid (0: the
 // unsplit kernel's single slice).
 __global__ void k_update(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbArgs a, uint32_t grid) {
     const bool f64 = a.p.pair_precision == DSR_NBODY_PAIRS_FP64;
-    const int rb = f64 ? RB64 : RB;
     uint32_t ns = 1;
     size_t stride = 0;
     if (grid) {
-        const SplitShape q = split_shape(H, grid, rb);
+        const SplitShape q = split_shape(a.ws, grid, f64 ? RB64 : RB);
         ns = q.ns;
-        stride = (size_t)q.nr * TILE * rb;
+        stride = q.n;
     }
-    const uint32_t n = n_dense(H);
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
-        if (slot_live(H, g))
-            update_body(H, a, g, ns, stride, f64);
-        else
-            a.ws.npos[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-}
-
-// Merge-partner test of body gi against gj, both with updated positions:
-// the FP32 test on the high words, widened by `rw2`, selects candidates; the
-// decision is the FP64 distance on the full positions against r_merge.
-__device__ __forceinline__ bool within_merge(const NbArgs& a, uint32_t gi, uint32_t gj) {
-    const D4 u = a.ws.npd[gi], v = a.ws.npd[gj];
-    const double dx = v.x - u.x, dy = v.y - u.y, dz = v.z - u.z;
-    return dx * dx + dy * dy + dz * dz < a.p.r_merge * a.p.r_merge;
+    const uint32_t n = n_bodies(a.ws);
+    uint32_t near = 0;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+        near += update_body(H, a, p, ns, stride, f64);
+    near = __reduce_add_sync(0xFFFFFFFFu, near);
+    if ((threadIdx.x & 31) == 0 && near) atomicAdd(a.ws.npairs, near);
 }
 
 // FP32 radius that selects merge candidates: r_merge plus a margin above the
@@ -508,128 +658,53 @@ __device__ __forceinline__ float wide_merge2(const NbArgs& a) {
     return rw * rw;
 }
 
-// Partner search over one slice of j tiles for RB bodies per thread: per
-// body the lowest partner id in the slice and that partner's dense index.
-// The candidate test fails for almost every pair, so the common path is the
-// squared distances and one test of their minimum; the per-body tests, the
-// FP64 decision and the id sit behind it.
-__global__ void __launch_bounds__(TILE, 5) k_partner_part(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbArgs a) {
-    __shared__ float4 sp[TILE];
-    const SplitShape q = split_shape(H, gridDim.x);
+// Partner of the body at sorted position p, on the updated positions: the
+// lowest id within r_merge (the FP32 test on the high words, widened, picks
+// candidates from the 27 cells around its new cell; the FP64 distance of the
+// full positions decides).
+__global__ void k_partner(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbArgs a) {
+    (void)H;
+    const uint32_t n = n_bodies(a.ws);
     const float rw2 = wide_merge2(a);
-    for (uint32_t item = blockIdx.x; item < q.nr * q.ns; item += gridDim.x) {
-        const uint32_t row = item % q.nr, sl = item / q.nr;
-        const uint32_t g0 = row * TILE * RB + threadIdx.x;
-        float px[RB], py[RB], pz[RB];
-        int32_t best_id[RB], best[RB];
-#pragma unroll
-        for (int k = 0; k < RB; ++k) {
-            const float4 u = ws_load(a.ws.npos, g0 + k * TILE, q.n);
-            px[k] = u.x, py[k] = u.y, pz[k] = u.z;
-            best_id[k] = 0x7FFFFFFF, best[k] = -1;
-        }
-        for (uint32_t t = q.nj * sl / q.ns; t < q.nj * (sl + 1) / q.ns; ++t) {
-            const uint32_t t0 = t * TILE;
-            __syncthreads();
-            sp[threadIdx.x] = ws_load(a.ws.npos, t0 + threadIdx.x, q.n);
-            __syncthreads();
-#pragma unroll 4
-            for (int j = 0; j < TILE; ++j) {
-                const float4 pj = sp[j];
-                float d2[RB];
-#pragma unroll
-                for (int k = 0; k < RB; ++k) {
-                    const float dx = pj.x - px[k], dy = pj.y - py[k], dz = pj.z - pz[k];
-                    d2[k] = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                }
-                float dmin = d2[0];
-#pragma unroll
-                for (int k = 1; k < RB; ++k) dmin = fminf(dmin, d2[k]);
-                if (dmin < rw2 && pj.w > 0.f) {
-                    const uint32_t jg = t0 + j;
-#pragma unroll
-                    for (int k = 0; k < RB; ++k) {
-                        const uint32_t gk = g0 + k * TILE;
-                        if (d2[k] < rw2 && jg != gk && gk < q.n) {
-                            const int32_t jid = a.ws.id[jg];
-                            if (jid < best_id[k] && within_merge(a, gk, jg)) {
-                                best_id[k] = jid;
-                                best[k] = (int32_t)jg;
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        int2* out = a.ws.pbest + (size_t)sl * q.nr * TILE * RB;
-#pragma unroll
-        for (int k = 0; k < RB; ++k)
-            if (g0 + k * TILE < q.n) out[g0 + k * TILE] = make_int2(best_id[k], best[k]);
-    }
-}
-
-// The partner over all slices: the lowest id (ids are unique).
-__global__ void k_partner_combine(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbArgs a, uint32_t grid) {
-    const SplitShape q = split_shape(H, grid);
-    const size_t stride = (size_t)q.nr * TILE * RB;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < q.n; g += gridDim.x * blockDim.x) {
-        int2 b = make_int2(0x7FFFFFFF, -1);
-        for (uint32_t k = 0; k < q.ns; ++k) {
-            const int2 v = a.ws.pbest[k * stride + g];
-            if (v.x < b.x) b = v;
-        }
-        a.ws.partner[g] = a.ws.npos[g].w > 0.f ? b.y : -1;
-    }
-}
-
-// Unsplit partner search (the allocation-free step): lowest id within
-// r_merge, with the candidate test and FP64 decision of k_partner_part.
-__global__ void __launch_bounds__(TILE) k_partner(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbArgs a) {
-    __shared__ float4 sp[TILE];
-    __shared__ int32_t sid[TILE];
-    const uint32_t n = n_dense(H);
-    const uint32_t base = blockIdx.x * TILE;
-    if (base >= n) return;
-    const uint32_t g = base + threadIdx.x;
-    const float4 pi = g < n ? a.ws.npos[g] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float rw2 = wide_merge2(a);
-    int32_t best_id = 0x7FFFFFFF, best = -1;
-    for (uint32_t t0 = 0; t0 < n; t0 += TILE) {
-        __syncthreads();
-        const uint32_t j = t0 + threadIdx.x;
-        sp[threadIdx.x] = j < n ? a.ws.npos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        sid[threadIdx.x] = j < n ? a.ws.id[j] : 0x7FFFFFFF;
-        __syncthreads();
-        for (int k = 0; k < TILE; ++k) {
-            const float4 pj = sp[k];
-            const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const int32_t jid = sid[k];
-            if (d2 < rw2 && jid < best_id && t0 + k != g && pj.w > 0.f && g < n && within_merge(a, g, t0 + k)) {
+    const double rm2 = a.p.r_merge * a.p.r_merge;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const float4 u = a.ws.npos[p];
+        const D4 ud = a.ws.npd[p];
+        int32_t best_id = 0x7FFFFFFF, best = -1;
+        for_neighbours<true>(a.ws, u.x, u.y, u.z, [&](uint32_t q) {
+            if (q == p) return;
+            const float4 v = a.ws.npos[q];
+            const float dx = v.x - u.x, dy = v.y - u.y, dz = v.z - u.z;
+            if (!(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rw2)) return;
+            const int32_t jid = a.ws.id[q];
+            if (jid >= best_id) return;
+            const D4 vd = a.ws.npd[q];
+            const double ex = vd.x - ud.x, ey = vd.y - ud.y, ez = vd.z - ud.z;
+            if (ex * ex + ey * ey + ez * ez < rm2) {
                 best_id = jid;
-                best = (int32_t)(t0 + k);
+                best = (int32_t)q;
             }
-        }
+        });
+        a.ws.partner[p] = best;
     }
-    if (g < n) a.ws.partner[g] = (pi.w > 0.f) ? best : -1;
 }
 
 // Merge mutual partners in FP64; the higher id deletes itself. Last kernel
 // of the step: its last CTA resets R and advances the step counter.
 __global__ void k_merge(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbArgs a) {
-    const uint32_t n = n_dense(H);
+    const uint32_t n = n_bodies(a.ws);
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-        const uint32_t g = base + threadIdx.x;
-        if (g >= n) continue;
-        const int32_t j = a.ws.partner[g];
-        if (j < 0 || a.ws.partner[j] != (int32_t)g) continue;
-        const dsr_ref r = slot_ref(H, g);
-        if (a.ws.id[g] > a.ws.id[j]) {
+        const uint32_t p = base + threadIdx.x;
+        if (p >= n) continue;
+        const int32_t j = a.ws.partner[p];
+        if (j < 0 || a.ws.partner[j] != (int32_t)p) continue;
+        const dsr_ref r = a.ws.sref[p];
+        if (a.ws.id[p] > a.ws.id[j]) {
             dsr_delete(H, r);
             continue;
         }
-        const D4 pg = a.ws.npd[g], pj = a.ws.npd[j];
-        const D4 vg = a.ws.nvd[g], vj = a.ws.nvd[j];
+        const D4 pg = a.ws.npd[p], pj = a.ws.npd[j];
+        const D4 vg = a.ws.nvd[p], vj = a.ws.nvd[j];
         const double M = pg.w + pj.w;
         put2(H, r, VX, (pg.w * vg.x + pj.w * vj.x) / M);
         put2(H, r, VY, (pg.w * vg.y + pj.w * vj.y) / M);
@@ -641,7 +716,7 @@ __global__ void k_merge(const __grid_constant__ dsr_dev_heap H, const __grid_con
         const dsr_u64 k = atomicAdd(a.ws.log_n, 1ull);
         if (k < a.ws.log_cap) {
             a.ws.log[3 * k + 0] = (int32_t)*a.ws.step;
-            a.ws.log[3 * k + 1] = a.ws.id[g];
+            a.ws.log[3 * k + 1] = a.ws.id[p];
             a.ws.log[3 * k + 2] = a.ws.id[j];
         }
     }
@@ -674,9 +749,18 @@ bool heap_matches(const dsr_heap* h) {
 }
 
 bool params_ok(const dsr_nbody_params* p) {
-    return p && p->dt > 0.0 && p->eps >= 0.0 && p->r_merge >= 0.0 && p->r_near >= 0.0 &&
-           p->r_near * p->r_near < (double)FLT_MAX && p->r_merge * p->r_merge < (double)FLT_MAX &&
-           (p->pair_precision == DSR_NBODY_PAIRS_FP32 || p->pair_precision == DSR_NBODY_PAIRS_FP64);
+    return p && p->dt > 0.0 && p->eps >= 0.0 && p->r_merge >= 0.0 && p->r_near >= 0.0 && p->r_near < 1.0 &&
+           p->r_merge < 1.0 && (p->pair_precision == DSR_NBODY_PAIRS_FP32 || p->pair_precision == DSR_NBODY_PAIRS_FP64);
+}
+
+// Cells per axis: as many as fit, up to KMAX, with cells at least as wide as
+// the near radius and the widened merge radius (then the pairs either test
+// selects lie in adjacent cells).
+int cells_per_axis(const dsr_nbody_params& p) {
+    const double rw = p.r_merge * (1.0 + 1e-3) + 1e-5;
+    const double r = (p.r_near > rw ? p.r_near : rw) * 1.001;
+    const int K = (int)(1.0 / r);
+    return K < 1 ? 1 : (K > KMAX ? KMAX : K);
 }
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
@@ -689,98 +773,140 @@ uint32_t split_grid(const dsr_heap* h, const void* kernel) {
 }
 
 struct SplitGrids {
-    uint32_t force, force64, partner;
+    uint32_t force, force64;
 };
 
 SplitGrids split_grids(const dsr_heap* h) {
-    return {split_grid(h, (const void*)k_force_part<true>), split_grid(h, (const void*)k_force_part64),
-            split_grid(h, (const void*)k_partner_part)};
+    return {split_grid(h, (const void*)k_force_part<true>), split_grid(h, (const void*)k_force_part64)};
 }
 
-// Slice entries of a split kernel: ns * nr <= max(grid, nr) items of TILE * rb bodies.
-size_t slots_for(uint64_t S, uint32_t grid, int rb) {
-    const uint64_t nr = (S + TILE * rb - 1) / (TILE * rb);
-    return (size_t)(grid > nr ? grid : nr) * TILE * rb;
+// Padded positions for a heap of S slots.
+uint64_t padded(uint64_t S) { return (S + ROW - 1) / ROW * ROW; }
+
+// Slice entries of a split kernel over at most P padded positions: at most
+// max(grid / rows, 1) slices (and no more than the j tiles) of P entries.
+size_t slots_for(uint64_t P, uint32_t grid, int rb) {
+    const uint64_t nr = P / (TILE * rb);
+    uint64_t ns = nr ? grid / nr : 1;
+    if (ns < 1) ns = 1;
+    if (ns > P / TILE) ns = P / TILE;
+    return (size_t)ns * P;
 }
-size_t split_slots(uint64_t S, SplitGrids g) {
-    const size_t a = slots_for(S, g.force, RB), b = slots_for(S, g.partner, RB);
-    return a > b ? a : b;
-}
-// Bytes of the force slice buffer: FP32 sums (16 bytes a slot) or FP64 sums
-// (32 bytes a slot, RB64 bodies a thread), whichever needs more.
-size_t part_bytes(uint64_t S, SplitGrids g) {
-    const size_t a = slots_for(S, g.force, RB) * 16, b = slots_for(S, g.force64, RB64) * 32;
-    return a > b ? a : b;
+// Bytes of the force slice buffer: FP32 sums (16 bytes an entry) or FP64 sums
+// (32 bytes), whichever needs more. (A step with fewer live bodies has fewer
+// rows, more slices and a smaller padded count; ns * n stays within this.)
+size_t part_bytes(uint64_t P, SplitGrids g) {
+    size_t m = 0;
+    for (uint64_t n = ROW; n <= P; n += ROW) {  // every padded count a step can have
+        const size_t a = slots_for(n, g.force, RB) * 16, b = slots_for(n, g.force64, RB64) * 32;
+        if (a > m) m = a;
+        if (b > m) m = b;
+    }
+    return m;
 }
 
-// Near pairs a workspace holds: 32 per slot, at least 2^20.
-uint64_t pair_cap_for(uint64_t S) { return S * 32 > (1u << 20) ? S * 32 : (1u << 20); }
-
-// Dense per-slot arrays of a step for S slots, carved from p (advanced).
-void carve_dense(uint8_t*& p, uint64_t S, NbWs& w) {
+// The spatial-order and per-position arrays of P padded positions, carved
+// from p (advanced).
+void carve_common(uint8_t*& p, uint64_t P, NbWs& w) {
+    w.ccount = reinterpret_cast<uint32_t*>(p);
+    p += round256(NKEYS * 4);
+    w.coff = reinterpret_cast<uint32_t*>(p);
+    p += round256((NKEYS + 1) * 4);
+    w.coff2 = reinterpret_cast<uint32_t*>(p);
+    p += round256((NKEYS + 1) * 4);
+    w.ckey = reinterpret_cast<uint32_t*>(p);
+    p += round256(P * 4);
+    w.perm = reinterpret_cast<uint32_t*>(p);
+    p += round256(P * 4);
+    w.perm2 = reinterpret_cast<uint32_t*>(p);
+    p += round256(P * 4);
     w.pos = reinterpret_cast<float4*>(p);
-    p += round256(S * 16);
+    p += round256(P * 16);
     w.pd = reinterpret_cast<D4*>(p);
-    p += round256(S * 32);
-    w.npos = reinterpret_cast<float4*>(p);
-    p += round256(S * 16);
-    w.npd = reinterpret_cast<D4*>(p);
-    p += round256(S * 32);
-    w.nvd = reinterpret_cast<D4*>(p);
-    p += round256(S * 32);
+    p += round256(P * 32);
     w.id = reinterpret_cast<int32_t*>(p);
-    p += round256(S * 4);
+    p += round256(P * 4);
+    w.sref = reinterpret_cast<dsr_u64*>(p);
+    p += round256(P * 8);
+    w.tbox = reinterpret_cast<float4*>(p);
+    p += round256(P / TILE * 32);
+    w.npos = reinterpret_cast<float4*>(p);
+    p += round256(P * 16);
+    w.npd = reinterpret_cast<D4*>(p);
+    p += round256(P * 32);
+    w.nvd = reinterpret_cast<D4*>(p);
+    p += round256(P * 32);
     w.partner = reinterpret_cast<int32_t*>(p);
-    p += round256(S * 4);
-    w.ncnt = reinterpret_cast<uint32_t*>(p);
-    p += round256(S * 4);
-    w.noff = reinterpret_cast<uint32_t*>(p);
-    p += round256((S + 1) * 4);
-    w.ncur = reinterpret_cast<uint32_t*>(p);
-    p += round256(S * 4);
+    p += round256(P * 4);
 }
-size_t dense_bytes(uint64_t S) {
-    return 2 * round256(S * 16) + 3 * round256(S * 32) + 4 * round256(S * 4) + round256((S + 1) * 4);
+size_t common_bytes(uint64_t P) {
+    return round256(NKEYS * 4) + 2 * round256((NKEYS + 1) * 4) + 3 * round256(P * 4) + round256(P * 16) +
+           round256(P * 32) + round256(P * 4) + round256(P * 8) + round256(P / TILE * 32) + round256(P * 16) +
+           2 * round256(P * 32) + round256(P * 4);
 }
 
 size_t ws_bytes(uint64_t S, uint64_t log_cap, SplitGrids grid) {
-    const uint64_t pc = pair_cap_for(S);
-    return dense_bytes(S) + round256(pc * 8) + round256(pc * 4) + round256(log_cap * 12) + 256 +
-           round256(part_bytes(S, grid)) + round256(split_slots(S, grid) * 8);
+    const uint64_t P = padded(S);
+    return common_bytes(P) + round256(log_cap * 12) + 256 + round256(part_bytes(P, grid));
 }
 
 NbWs carve(void* base, uint64_t S, uint64_t log_cap, SplitGrids grid) {
+    const uint64_t P = padded(S);
     uint8_t* p = static_cast<uint8_t*>(base);
     NbWs w;
-    carve_dense(p, S, w);
-    const uint64_t pc = pair_cap_for(S);
-    w.pairs = reinterpret_cast<int2*>(p);
-    p += round256(pc * 8);
-    w.csr = reinterpret_cast<int32_t*>(p);
-    p += round256(pc * 4);
-    w.pair_cap = (uint32_t)pc;
+    carve_common(p, P, w);
     w.log = reinterpret_cast<int32_t*>(p);
     p += round256(log_cap * 12);
     w.log_n = reinterpret_cast<dsr_u64*>(p);
     w.step = reinterpret_cast<dsr_u64*>(p + 8);
-    w.npairs = reinterpret_cast<uint32_t*>(p + 16);
+    w.n_live = reinterpret_cast<uint32_t*>(p + 16);
+    w.npairs = reinterpret_cast<uint32_t*>(p + 20);
     p += 256;
     w.part = reinterpret_cast<float4*>(p);
     w.part64 = reinterpret_cast<D4*>(p);
-    p += round256(part_bytes(S, grid));
-    w.pbest = reinterpret_cast<int2*>(p);
     w.log_cap = log_cap;
     return w;
 }
 
-// The kernels between the force sums and the merge that both forms share:
-// the near-pair grouping, the update (grid: the split force grid, or 0 for a
-// single slice), then the partner search and the merge.
-void launch_near_update(dsr_heap* h, const NbArgs& a, uint32_t grid, cudaStream_t s) {
-    const unsigned stream_ctas = (unsigned)(h->sm_count * 4);
-    k_near_scan<<<1, 1024, 0, s>>>(h->dev, a.ws);
-    k_near_fill<<<stream_ctas, 256, 0, s>>>(h->dev, a.ws);
-    k_update<<<stream_ctas, 256, 0, s>>>(h->dev, a, grid);
+// The spatial sort of one order (POST: the updated positions).
+template <bool POST>
+void launch_sort(dsr_heap* h, const NbArgs& a, cudaStream_t s) {
+    const unsigned ctas = (unsigned)(h->sm_count * 4);
+    k_cell_count<POST><<<ctas, 256, 0, s>>>(h->dev, a.ws);
+    k_cell_scan<<<1, 1024, 0, s>>>(a.ws, POST ? 1 : 0);
+    k_cell_place<POST><<<ctas, 256, 0, s>>>(h->dev, a.ws);
+    k_cell_order<POST><<<NKEYS / 256, 256, 0, s>>>(h->dev, a.ws);
+}
+
+// One step. `split`: the split force kernels with their grids (else the
+// unsplit ones, for the allocation-free step); P: padded positions.
+void launch_step(dsr_heap* h, const NbArgs& a, const SplitGrids* split, uint64_t P, cudaStream_t s) {
+    const unsigned ctas = (unsigned)(h->sm_count * 4);
+    const bool f64 = a.p.pair_precision == DSR_NBODY_PAIRS_FP64;
+    const bool soft = a.p.eps * a.p.eps >= (double)FLT_MIN;
+    dsr__launch_scan(h, BODY, s);
+    launch_sort<false>(h, a, s);
+    k_gather<<<ctas, TILE, 0, s>>>(h->dev, a.ws);
+    uint32_t grid = 0;
+    if (split) {
+        grid = f64 ? split->force64 : split->force;
+        if (f64)
+            k_force_part64<<<grid, TILE, 0, s>>>(h->dev, a);
+        else if (soft)
+            k_force_part<true><<<grid, TILE, 0, s>>>(h->dev, a);
+        else
+            k_force_part<false><<<grid, TILE, 0, s>>>(h->dev, a);
+    } else {
+        const unsigned tiles = (unsigned)(P / TILE);
+        if (f64)
+            k_force64<<<tiles, TILE, 0, s>>>(h->dev, a);
+        else
+            k_force<<<tiles, TILE, 0, s>>>(h->dev, a);
+    }
+    k_update<<<ctas, 256, 0, s>>>(h->dev, a, grid);
+    launch_sort<true>(h, a, s);
+    k_partner<<<ctas, 256, 0, s>>>(h->dev, a);
+    k_merge<<<ctas, 256, 0, s>>>(h->dev, a);
 }
 }  // namespace
 
@@ -808,16 +934,17 @@ extern "C" int dsr_nbody_create(dsr_heap* heap, const dsr_nbody_params* p, const
     if (!heap || !params_ok(p) || !rows_dev || !workspace_dev || !out || n_bodies < 1) return DSR_E_INVALID;
     if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255) || !heap_matches(heap)) return DSR_E_INVALID;
     if ((uint64_t)n_bodies > heap->layout.n_blocks * heap->layout.capacity[BODY]) return DSR_E_INVALID;
-    const uint64_t S = heap->layout.n_blocks * 64;
-    if (pair_cap_for(S) > 0xFFFFFFFFull) return DSR_E_INVALID;
+    if (heap->layout.n_blocks * 64 > 0x7FFFFFFFull) return DSR_E_INVALID;
     dsr_nbody* nb = new dsr_nbody;
     nb->heap = heap;
-    nb->S = S;
+    nb->S = heap->layout.n_blocks * 64;
     nb->grid = split_grids(heap);
     nb->args.ws = carve(workspace_dev, nb->S, log_cap, nb->grid);
+    nb->args.ws.K = cells_per_axis(*p);
     nb->args.p = *p;
     cudaStream_t s = dsr__stream(stream);
     cudaError_t e = cudaMemsetAsync(nb->args.ws.log_n, 0, 24, s);
+    if (!e) e = cudaMemsetAsync(nb->args.ws.ccount, 0, NKEYS * 4, s);
     if (e) {
         dsr__set_cuda_error(e, "dsr_nbody_create");
         delete nb;
@@ -838,23 +965,8 @@ extern "C" int dsr_nbody_create(dsr_heap* heap, const dsr_nbody_params* p, const
 extern "C" int dsr_nbody_step(dsr_nbody* nb, int n_steps, void* stream) {
     if (!nb || n_steps < 0) return DSR_E_INVALID;
     cudaStream_t s = dsr__stream(stream);
-    dsr_heap* h = nb->heap;
-    const unsigned stream_ctas = (unsigned)(h->sm_count * 4);
-    const bool soft = nb->args.p.eps * nb->args.p.eps >= (double)FLT_MIN;
-    const bool f64 = nb->args.p.pair_precision == DSR_NBODY_PAIRS_FP64;
     for (int i = 0; i < n_steps; ++i) {
-        dsr__launch_scan(h, BODY, s);
-        k_gather<<<stream_ctas, 256, 0, s>>>(h->dev, nb->args.ws);
-        if (f64)
-            k_force_part64<<<nb->grid.force64, TILE, 0, s>>>(h->dev, nb->args);
-        else if (soft)
-            k_force_part<true><<<nb->grid.force, TILE, 0, s>>>(h->dev, nb->args);
-        else
-            k_force_part<false><<<nb->grid.force, TILE, 0, s>>>(h->dev, nb->args);
-        launch_near_update(h, nb->args, f64 ? nb->grid.force64 : nb->grid.force, s);
-        k_partner_part<<<nb->grid.partner, TILE, 0, s>>>(h->dev, nb->args);
-        k_partner_combine<<<stream_ctas, 256, 0, s>>>(h->dev, nb->args, nb->grid.partner);
-        k_merge<<<stream_ctas, 256, 0, s>>>(h->dev, nb->args);
+        launch_step(nb->heap, nb->args, &nb->grid, padded(nb->S), s);
         int rc = dsr__check_launch("dsr_nbody_step");
         if (rc) return rc;
     }
@@ -882,29 +994,33 @@ extern "C" int dsr_nbody_destroy(dsr_nbody* nb) {
 int dsr__nbody_method(dsr_heap*, int, int, const void*, size_t, cudaStream_t, bool) { return DSR_E_INVALID; }
 
 // ---------------------------------------------------------------------------
-// Allocation-free step. The per-slot scratch of a step (the dense state
-// before and after the update, ids, partners, the far-field sums and the
-// near-pair lists) lives in this file-scope device array instead of a
+// Allocation-free step. The scratch of a step (the cell counts and offsets,
+// the sorted state before and after the update, handles, partners and the
+// far-field sums) lives in this file-scope device array instead of a
 // caller-allocated workspace, for callers that cannot call cudaMalloc.
 // Every GPU that loads the library holds the array until the process exits.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr uint64_t kNoallocPairs = (uint64_t)DSR_NOALLOC_MAX_SLOTS * DSR_NOALLOC_PAIRS_PER_SLOT;
+constexpr uint64_t kNoallocP = (DSR_NOALLOC_MAX_SLOTS + ROW - 1) / ROW * ROW;
 
 struct NoallocScratch {
-    float4 pos[DSR_NOALLOC_MAX_SLOTS];
-    D4 pd[DSR_NOALLOC_MAX_SLOTS];
-    float4 npos[DSR_NOALLOC_MAX_SLOTS];
-    D4 npd[DSR_NOALLOC_MAX_SLOTS];
-    D4 nvd[DSR_NOALLOC_MAX_SLOTS];
-    D4 part[DSR_NOALLOC_MAX_SLOTS];  // far-field sums: FP32 (as float4) or FP64
-    int32_t id[DSR_NOALLOC_MAX_SLOTS];
-    int32_t partner[DSR_NOALLOC_MAX_SLOTS];
-    uint32_t ncnt[DSR_NOALLOC_MAX_SLOTS];
-    uint32_t noff[DSR_NOALLOC_MAX_SLOTS + 1];
-    uint32_t ncur[DSR_NOALLOC_MAX_SLOTS];
-    int2 pairs[kNoallocPairs];
-    int32_t csr[kNoallocPairs];
+    uint32_t ccount[NKEYS];  // zero at load; every sort leaves it zero
+    uint32_t coff[NKEYS + 1];
+    uint32_t coff2[NKEYS + 1];
+    uint32_t ckey[kNoallocP];
+    uint32_t perm[kNoallocP];
+    uint32_t perm2[kNoallocP];
+    float4 pos[kNoallocP];
+    D4 pd[kNoallocP];
+    int32_t id[kNoallocP];
+    dsr_u64 sref[kNoallocP];
+    float4 tbox[kNoallocP / TILE * 2];
+    float4 npos[kNoallocP];
+    D4 npd[kNoallocP];
+    D4 nvd[kNoallocP];
+    int32_t partner[kNoallocP];
+    D4 part[kNoallocP];  // far-field sums: FP32 (as float4) or FP64
+    uint32_t n_live;
     uint32_t npairs;
     dsr_u64 step;
 };
@@ -956,45 +1072,35 @@ extern "C" int dsr_nbody_step_noalloc(dsr_heap* heap, const dsr_nbody_params* p,
     if (rc) return rc;
     NbArgs a;
     a.p = *p;
+    a.ws.ccount = sc->ccount;
+    a.ws.coff = sc->coff;
+    a.ws.coff2 = sc->coff2;
+    a.ws.ckey = sc->ckey;
+    a.ws.perm = sc->perm;
+    a.ws.perm2 = sc->perm2;
+    a.ws.n_live = &sc->n_live;
+    a.ws.npairs = &sc->npairs;
     a.ws.pos = sc->pos;
     a.ws.pd = sc->pd;
+    a.ws.id = sc->id;
+    a.ws.sref = sc->sref;
+    a.ws.tbox = sc->tbox;
     a.ws.npos = sc->npos;
     a.ws.npd = sc->npd;
     a.ws.nvd = sc->nvd;
+    a.ws.partner = sc->partner;
     a.ws.part = reinterpret_cast<float4*>(sc->part);  // one slice: the unsplit force kernels
     a.ws.part64 = sc->part;
-    a.ws.pbest = nullptr;  // the unsplit partner kernel needs no slice buffer
-    a.ws.id = sc->id;
-    a.ws.partner = sc->partner;
-    a.ws.ncnt = sc->ncnt;
-    a.ws.noff = sc->noff;
-    a.ws.ncur = sc->ncur;
-    a.ws.pairs = sc->pairs;
-    a.ws.csr = sc->csr;
-    a.ws.pair_cap = (uint32_t)kNoallocPairs;
-    a.ws.npairs = &sc->npairs;
-    a.ws.step = &sc->step;
     a.ws.log = static_cast<int32_t*>(log_dev);
     a.ws.log_n = static_cast<dsr_u64*>(log_count_dev);
+    a.ws.step = &sc->step;
     a.ws.log_cap = log_cap;
+    a.ws.K = cells_per_axis(*p);
     cudaStream_t s = dsr__stream(stream);
     // The array keeps the previous call's contents. The step counter is the
-    // only value a step reads before this call writes it; the pair count and
-    // the per-body counts are cleared by each step's gather.
+    // only value a step reads before writing it; the cell counts are zero
+    // when the library is loaded and every sort returns them to zero.
     k_set_u64<<<1, 1, 0, s>>>(&sc->step, step0);
-    dsr_heap* h = heap;
-    const unsigned dense_ctas = (unsigned)((S + TILE - 1) / TILE);
-    const unsigned stream_ctas = (unsigned)(h->sm_count * 4);
-    for (int i = 0; i < n_steps; ++i) {
-        dsr__launch_scan(h, BODY, s);
-        k_gather<<<stream_ctas, 256, 0, s>>>(h->dev, a.ws);
-        if (a.p.pair_precision == DSR_NBODY_PAIRS_FP64)
-            k_force64<<<dense_ctas, TILE, 0, s>>>(h->dev, a);
-        else
-            k_force<<<dense_ctas, TILE, 0, s>>>(h->dev, a);
-        launch_near_update(h, a, 0, s);
-        k_partner<<<dense_ctas, TILE, 0, s>>>(h->dev, a);
-        k_merge<<<stream_ctas, 256, 0, s>>>(h->dev, a);
-    }
+    for (int i = 0; i < n_steps; ++i) launch_step(heap, a, nullptr, padded(S), s);
     return dsr__check_launch("dsr_nbody_step_noalloc");
 }
