@@ -245,33 +245,33 @@ KERNELS = {"F1": "dsr_doall_kernel<MFishChoose>", "F2": "dsr_doall_kernel<MFishM
 def phase_bytes(phase, objs, blocks, moves, births, deaths):
     """Algorithmic bytes of one wa-tor method kernel: what its rules read and
     write per visited object and per event, plus the 12-byte R entry (block id
-    and live mask) of every listed block. Fields are int32, grid and claim
-    words uint64, intent uint32.
+    and live mask) of every listed block. Fields, grid words, claim words and
+    intents are 4 bytes each.
 
       F1  per fish: x, y, timer read, timer written (16), four neighbour grid
-          words (32), intent written (4), claim read-modify-written (16; an
-          upper bound, as fish with no empty neighbour claim nothing)   = 68
-      F2  per fish: x, y (8), intent (4), claim (8)                      = 20
-          per move: target and own grid words written (16), x, y written
-          (8), timer read (4)                                            = 28
+          words (16), intent written (4), claim read-modify-written (8; an
+          upper bound, as fish with no empty neighbour claim nothing)   = 44
+      F2  per fish: x, y (8), intent (4), claim (4)                      = 16
+          per move: target and own grid words written (8), x, y written
+          (8), timer read (4), the claim word reset (4)                  = 24
           per birth: timer reset (4), the new fish's three fields (12)   = 16
       S0  per shark: energy read and written                             = 8
-          per death: x, y read (8), grid word cleared (8)                = 16
-      S1  as F1                                                          = 68
-      S2  per shark as F2                                                = 20
-          per move: target grid word read and written (16), own grid word
-          written (8), x, y written (8), timer read (4)                  = 36
+          per death: x, y read (8), grid word cleared (4)                = 12
+      S1  as F1                                                          = 44
+      S2  per shark as F2                                                = 16
+          per move: target grid word read and written (8), own grid word
+          written (4), x, y written (8), timer read (4), claim reset (4) = 28
           per fish eaten: energy read and written                        = 8
           per birth: timer reset (4), the new shark's four fields (16)   = 20
     """
-    per_obj = {"F1": 68, "F2": 20, "S0": 8, "S1": 68, "S2": 20}[phase]
+    per_obj = {"F1": 44, "F2": 16, "S0": 8, "S1": 44, "S2": 16}[phase]
     b = per_obj * objs + 12 * blocks
     if phase == "F2":
-        b += 28 * moves + 16 * births
+        b += 24 * moves + 16 * births
     elif phase == "S0":
-        b += 16 * deaths
+        b += 12 * deaths
     elif phase == "S2":
-        b += 36 * moves + 8 * deaths + 20 * births
+        b += 28 * moves + 8 * deaths + 20 * births
     return b
 
 
@@ -760,10 +760,11 @@ def bench_space(heap_bytes=32 << 20, steps=100):
 def bench_nbody(n=65536, steps=5):
     """C3: n-body with merging, 65,536 bodies (FP32-pair state, FP64 update and
     merges), in both pair-force modes: FP32 pairs (FP64 for pairs within
-    r_near) and FP64 pairs. FLOPs counted as 20 per pair for the force
-    (softened inverse-cube, three FMAs into the acceleration) and 8 per pair
-    for the merge-partner distance test, against the FP32 FMA ceiling
-    measured by dsr_bench_fma."""
+    r_near) and FP64 pairs. FLOPs counted as 20 per pair for the all-pairs
+    force (softened inverse-cube, three FMAs into the acceleration; the
+    near field and the merge-partner search only visit neighbouring cells
+    and are not counted), against the FP32 FMA ceiling measured by
+    dsr_bench_fma."""
     import torch
     from paper_1809_07444_gb300 import _lib as L
     from paper_1809_07444_gb300 import workloads as WL
@@ -771,7 +772,7 @@ def bench_nbody(n=65536, steps=5):
     from paper_1809_07444_gb300.heap import _stream_ptr
 
     rows, _ = WL.nbody_initial(n, 1)
-    out = {"workload": "n-body %d bodies, steps 3-%d" % (n, 2 + steps), "bound": "alu", "flop_per_pair": 28}
+    out = {"workload": "n-body %d bodies, steps 3-%d" % (n, 2 + steps), "bound": "alu", "flop_per_pair": 20}
     for mode in ("fp32", "fp64"):
         nb = NBody(rows, pairs=mode)
         nb.step(2)
@@ -783,7 +784,7 @@ def bench_nbody(n=65536, steps=5):
         e1.record()
         e1.synchronize()
         t = e0.elapsed_time(e1) / 1e3 / steps
-        out[mode + "_pairs"] = {"ms_per_step": t * 1e3, "bodies": live0, "tflops": 28.0 * live0 * live0 / t / 1e12,
+        out[mode + "_pairs"] = {"ms_per_step": t * 1e3, "bodies": live0, "tflops": 20.0 * live0 * live0 / t / 1e12,
                                 "near_pairs_last_step": nb.near_pairs(), "r_near": nb.params.r_near}
         del nb
         torch.cuda.empty_cache()

@@ -88,10 +88,12 @@ int dsr_gol_batch_destroy(dsr_gol_batch* b);
  *   S2 (Shark): winners move; a fish in the target is deleted and energy +=
  *               shark_gain; timer >= shark_breed: leave a new Shark (timer 0,
  *               energy shark_energy0) behind and reset timer.
- * Workspace (dsr_wator_workspace_bytes, which depends on the heap): uint64
- * grid (0 empty, else (handle << 2) | kind) and uint64 claim per cell, the
- * step counter, and a uint32 intent per object slot of the heap (the target
- * an agent chose in F1 / S1, read back in F2 / S2 with the agent's fields).
+ * Workspace (dsr_wator_workspace_bytes, which depends on the heap): a uint32
+ * grid word per cell (0 empty, else (handle << 2) | kind; heaps of at most
+ * 2^24 blocks), a uint32 claim word per cell (the lowest mover cell that
+ * claimed it; the winner resets it when it moves), the step counter, and a
+ * uint32 intent per object slot of the heap (the target an agent chose in
+ * F1 / S1, read back in F2 / S2 with the agent's fields).
  * Each successful move (F2 and S2 winners) adds one to the heap's
  * DSR_CTR_APP0 event counter. */
 enum {

@@ -10,18 +10,35 @@
 namespace {
 enum { FISH = 0, SHARK = 1 };
 enum { X = 0, Y = 1, TIMER = 2, ENERGY = 3 };
-enum : dsr_u64 { K_EMPTY = 0, K_FISH = 1, K_SHARK = 2 };
+enum : uint32_t { K_EMPTY = 0, K_FISH = 1, K_SHARK = 2 };
 constexpr uint32_t NO_MOVE = 0xFFFFFFFFu;
+constexpr uint32_t NO_CLAIM = 0xFFFFFFFFu;  // a claim word no mover holds (cells are below 2^31)
 
 // Device view of one instance: its workspace and its parameters.
 struct WatorInst {
-    dsr_u64* grid;     // 0 = empty, else (handle << 2) | kind
-    dsr_u64* claim;    // lowest claim key of the current phase
+    uint32_t* grid;    // 0 = empty, else (compact handle << 2) | kind (grid_word)
+    uint32_t* claim;   // the lowest mover cell that claimed the cell this phase, or NO_CLAIM
     uint32_t* intent;  // per object slot (intent_index): its chosen target, or NO_MOVE
     dsr_u64 n_slots;   // entries of intent
     dsr_u64* step;     // device step counter (nullptr: unused batch slot)
     dsr_wator_params p;
 };
+
+// Grid words are 32 bits: the kind in the low two bits and a compact handle
+// above them. dsr heap: the handle itself (block * 64 + slot, below 2^30
+// for heaps of at most 2^24 blocks); BitmapAlloc: the slot in the type's
+// array (below 2^30), the type following from the kind.
+__device__ __forceinline__ uint32_t grid_word(const dsr_dev_heap&, dsr_ref r, uint32_t kind) {
+    return ((uint32_t)r << 2) | kind;
+}
+__device__ __forceinline__ dsr_ref grid_ref(const dsr_dev_heap&, uint32_t g) { return g >> 2; }
+__device__ __forceinline__ uint32_t grid_word(const dsr_bm_dev&, dsr_ref r, uint32_t kind) {
+    return ((uint32_t)(r & ((1ull << DSR_BM_SLOT_BITS) - 1)) << 2) | kind;
+}
+__device__ __forceinline__ dsr_ref grid_ref(const dsr_bm_dev&, uint32_t g) {
+    const dsr_u64 type = (g & 3) == K_FISH ? 0 : 1;  // Fish = 0, Shark = 1
+    return (type << DSR_BM_SLOT_BITS) | (g >> 2);
+}
 
 // Intents are indexed by the object's slot, not by its cell: the move phase
 // then reads its own intent together with its fields (one round trip), and
@@ -32,12 +49,12 @@ __device__ __forceinline__ dsr_u64 intent_index(const dsr_bm_dev&, dsr_ref r) {
     return r & ((1ull << DSR_BM_SLOT_BITS) - 1);
 }
 
-// Claim key of phase `ph` (0 fish, 1 shark) of step t for a mover in cell c.
-// Keys of later phases compare lower than every key of earlier phases, so the
-// claim array never needs resetting; within a phase the lowest cell wins.
-__device__ __forceinline__ dsr_u64 claim_key(dsr_u64 t, unsigned ph, uint32_t c) {
-    return ((0xFFFFFFFFull - (2 * t + ph)) << 32) | c;
-}
+// Claims: a mover in cell c claims its target with atomicMin(claim, c), so
+// the lowest mover cell wins a contested cell. The winner's move phase puts
+// the word back to NO_CLAIM once it has read it; a loser that reads the
+// word afterwards sees NO_CLAIM, which is no cell, and loses all the same.
+// Every claimed cell has a winner (no mover dies between its choose and move
+// phases), so every word is NO_CLAIM again when a choose phase starts.
 
 __device__ __forceinline__ void neighbours(uint32_t c, int W, int H, uint32_t nb[4]) {
     const int x = (int)(c % (uint32_t)W), y = (int)(c / (uint32_t)W);
@@ -79,7 +96,7 @@ __device__ __forceinline__ void fish_choose(const HP& H, const WatorInst& I, dsr
     uint32_t tgt = NO_MOVE;
     if (m) {
         tgt = nb[pick(m, (unsigned)(dsr_rand(I.p.seed, 0, t, c) % (dsr_u64)__popc(m)))];
-        atomicMin(I.claim + tgt, claim_key(t, 0, c));
+        atomicMin(I.claim + tgt, c);
     }
     const dsr_u64 ix = intent_index(H, self);
     if (dsr_check(ix < I.n_slots, H.err, H.dbg, 8, ix)) I.intent[ix] = tgt;
@@ -88,7 +105,6 @@ __device__ __forceinline__ void fish_choose(const HP& H, const WatorInst& I, dsr
 // F2: winners move and breed.
 template <class HP>
 __device__ __forceinline__ void fish_move(const HP& H, const WatorInst& I, dsr_ref self) {
-    const dsr_u64 t = *(volatile dsr_u64*)I.step;
     int32_t* px = dsr_field<int32_t>(H, FISH, self, X);
     int32_t* py = dsr_field<int32_t>(H, FISH, self, Y);
     int32_t* timer = dsr_field<int32_t>(H, FISH, self, TIMER);
@@ -100,12 +116,13 @@ __device__ __forceinline__ void fish_move(const HP& H, const WatorInst& I, dsr_r
     const uint32_t c = (uint32_t)(*py * I.p.W + *px);
     if (!cell_ok(H, I, c, 6)) return;
     if (tgt != NO_MOVE && !cell_ok(H, I, tgt, 7)) return;
-    if (tgt == NO_MOVE || I.claim[tgt] != claim_key(t, 0, c)) return;
+    if (tgt == NO_MOVE || I.claim[tgt] != c) return;
+    I.claim[tgt] = NO_CLAIM;
     dsr_count_lanes(H.ctr, DSR_CTR_APP0);
-    I.grid[tgt] = (self << 2) | K_FISH;
+    I.grid[tgt] = grid_word(H, self, K_FISH);
     *px = (int32_t)(tgt % (uint32_t)I.p.W);
     *py = (int32_t)(tgt / (uint32_t)I.p.W);
-    dsr_u64 left = K_EMPTY;
+    uint32_t left = K_EMPTY;
     if (age >= I.p.fish_breed) {
         *timer = 0;
         const dsr_ref n = dsr_new(H, FISH);
@@ -113,7 +130,7 @@ __device__ __forceinline__ void fish_move(const HP& H, const WatorInst& I, dsr_r
             *dsr_field<int32_t>(H, FISH, n, X) = (int32_t)(c % (uint32_t)I.p.W);
             *dsr_field<int32_t>(H, FISH, n, Y) = (int32_t)(c / (uint32_t)I.p.W);
             *dsr_field<int32_t>(H, FISH, n, TIMER) = 0;
-            left = (n << 2) | K_FISH;
+            left = grid_word(H, n, K_FISH);
         }
     }
     I.grid[c] = left;
@@ -142,7 +159,7 @@ __device__ __forceinline__ void shark_choose(const HP& H, const WatorInst& I, ds
     unsigned mf = 0, me = 0;
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
-        const dsr_u64 g = I.grid[nb[d]];
+        const uint32_t g = I.grid[nb[d]];
         mf |= ((g & 3) == K_FISH ? 1u : 0u) << d;
         me |= (g == K_EMPTY ? 1u : 0u) << d;
     }
@@ -150,7 +167,7 @@ __device__ __forceinline__ void shark_choose(const HP& H, const WatorInst& I, ds
     uint32_t tgt = NO_MOVE;
     if (m) {
         tgt = nb[pick(m, (unsigned)(dsr_rand(I.p.seed, 1, t, c) % (dsr_u64)__popc(m)))];
-        atomicMin(I.claim + tgt, claim_key(t, 1, c));
+        atomicMin(I.claim + tgt, c);
     }
     const dsr_u64 ix = intent_index(H, self);
     if (dsr_check(ix < I.n_slots, H.err, H.dbg, 8, ix)) I.intent[ix] = tgt;
@@ -159,7 +176,6 @@ __device__ __forceinline__ void shark_choose(const HP& H, const WatorInst& I, ds
 // S2: winners move, eat and breed.
 template <class HP>
 __device__ __forceinline__ void shark_move(const HP& H, const WatorInst& I, dsr_ref self) {
-    const dsr_u64 t = *(volatile dsr_u64*)I.step;
     int32_t* px = dsr_field<int32_t>(H, SHARK, self, X);
     int32_t* py = dsr_field<int32_t>(H, SHARK, self, Y);
     int32_t* timer = dsr_field<int32_t>(H, SHARK, self, TIMER);
@@ -171,17 +187,18 @@ __device__ __forceinline__ void shark_move(const HP& H, const WatorInst& I, dsr_
     const uint32_t c = (uint32_t)(*py * I.p.W + *px);
     if (!cell_ok(H, I, c, 6)) return;
     if (tgt != NO_MOVE && !cell_ok(H, I, tgt, 7)) return;
-    if (tgt == NO_MOVE || I.claim[tgt] != claim_key(t, 1, c)) return;
+    if (tgt == NO_MOVE || I.claim[tgt] != c) return;
+    I.claim[tgt] = NO_CLAIM;
     dsr_count_lanes(H.ctr, DSR_CTR_APP0);
-    const dsr_u64 g = I.grid[tgt];
+    const uint32_t g = I.grid[tgt];
     if ((g & 3) == K_FISH) {
-        dsr_delete(H, g >> 2);
+        dsr_delete(H, grid_ref(H, g));
         *energy = e0 + I.p.shark_gain;
     }
-    I.grid[tgt] = (self << 2) | K_SHARK;
+    I.grid[tgt] = grid_word(H, self, K_SHARK);
     *px = (int32_t)(tgt % (uint32_t)I.p.W);
     *py = (int32_t)(tgt / (uint32_t)I.p.W);
-    dsr_u64 left = K_EMPTY;
+    uint32_t left = K_EMPTY;
     if (age >= I.p.shark_breed) {
         *timer = 0;
         const dsr_ref n = dsr_new(H, SHARK);
@@ -190,7 +207,7 @@ __device__ __forceinline__ void shark_move(const HP& H, const WatorInst& I, dsr_
             *dsr_field<int32_t>(H, SHARK, n, Y) = (int32_t)(c / (uint32_t)I.p.W);
             *dsr_field<int32_t>(H, SHARK, n, TIMER) = 0;
             *dsr_field<int32_t>(H, SHARK, n, ENERGY) = I.p.shark_energy0;
-            left = (n << 2) | K_SHARK;
+            left = grid_word(H, n, K_SHARK);
         }
     }
     I.grid[c] = left;
@@ -282,14 +299,14 @@ __global__ void k_wator_init(const __grid_constant__ HP H, const uint8_t* kind0,
         __syncwarp();  // whole-warp groups for dsr_new
         if (c >= n) continue;
         const uint8_t k = kind0[c];
-        dsr_u64 g = K_EMPTY;
+        uint32_t g = K_EMPTY;
         if (k == 1) {
             const dsr_ref r = dsr_new(H, FISH);
             if (r != DSR_NULL) {
                 *dsr_field<int32_t>(H, FISH, r, X) = (int32_t)(c % (uint32_t)I.p.W);
                 *dsr_field<int32_t>(H, FISH, r, Y) = (int32_t)(c / (uint32_t)I.p.W);
                 *dsr_field<int32_t>(H, FISH, r, TIMER) = 0;
-                g = (r << 2) | K_FISH;
+                g = grid_word(H, r, K_FISH);
             }
         } else if (k == 2) {
             const dsr_ref r = dsr_new(H, SHARK);
@@ -298,16 +315,16 @@ __global__ void k_wator_init(const __grid_constant__ HP H, const uint8_t* kind0,
                 *dsr_field<int32_t>(H, SHARK, r, Y) = (int32_t)(c / (uint32_t)I.p.W);
                 *dsr_field<int32_t>(H, SHARK, r, TIMER) = 0;
                 *dsr_field<int32_t>(H, SHARK, r, ENERGY) = I.p.shark_energy0;
-                g = (r << 2) | K_SHARK;
+                g = grid_word(H, r, K_SHARK);
             }
         }
         I.grid[c] = g;
-        I.claim[c] = ~0ull;
+        I.claim[c] = NO_CLAIM;
         if (c == 0) *I.step = 0;
     }
 }
 
-__global__ void k_wator_kinds(const dsr_u64* grid, uint8_t* out, uint32_t n) {
+__global__ void k_wator_kinds(const uint32_t* grid, uint8_t* out, uint32_t n) {
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
         out[c] = (uint8_t)(grid[c] & 3);
 }
@@ -315,8 +332,12 @@ __global__ void k_wator_kinds(const dsr_u64* grid, uint8_t* out, uint32_t n) {
 const int kFishFields[3] = {4, 4, 4};
 const int kSharkFields[4] = {4, 4, 4, 4};
 
+// Grid words hold handles below 2^30: heaps of at most 2^24 blocks.
+constexpr dsr_u64 kMaxBlocks = 1ull << 24;
+
 bool heap_matches(const dsr_heap* h) {
     const dsr_layout& L = h->layout;
+    if (L.n_blocks > kMaxBlocks) return false;
     if (L.n_types < 2 || L.n_fields[FISH] != 3 || L.n_fields[SHARK] != 4) return false;
     for (int f = 0; f < 3; ++f)
         if (L.field_bytes[FISH][f] != 4) return false;
@@ -330,20 +351,20 @@ bool params_ok(const dsr_wator_params* p) {
            p->shark_breed >= 1 && p->shark_energy0 >= 1 && p->shark_gain >= 0;
 }
 
-// Workspace: grid u64[n] | claim u64[n] | step counter (256 B) | intent
+// Workspace: grid u32[n] | claim u32[n] | step counter (256 B) | intent
 // u32[slots], each part 256-byte aligned; slots = object slots of the heap.
 size_t ws_bytes(int W, int H, dsr_u64 slots) {
     const size_t n = (size_t)W * H;
-    return ((n * 8 + 255) / 256 * 256) * 2 + 256 + (slots * 4 + 255) / 256 * 256;
+    return ((n * 4 + 255) / 256 * 256) * 2 + 256 + (slots * 4 + 255) / 256 * 256;
 }
 
 WatorInst carve(void* base, const dsr_wator_params& p, dsr_u64 slots) {
     const size_t n = (size_t)p.W * p.H;
     uint8_t* b = static_cast<uint8_t*>(base);
-    const size_t g = (n * 8 + 255) / 256 * 256;
+    const size_t g = (n * 4 + 255) / 256 * 256;
     WatorInst w;
-    w.grid = reinterpret_cast<dsr_u64*>(b);
-    w.claim = reinterpret_cast<dsr_u64*>(b + g);
+    w.grid = reinterpret_cast<uint32_t*>(b);
+    w.claim = reinterpret_cast<uint32_t*>(b + g);
     w.step = reinterpret_cast<dsr_u64*>(b + 2 * g);
     w.intent = reinterpret_cast<uint32_t*>(b + 2 * g + 256);
     w.n_slots = slots;
@@ -545,6 +566,7 @@ struct dsr_wator_bm {
 };
 
 static bool bm_heap_matches(const dsr_bm_heap* h) {
+    if (bm_slots(h) > (1ull << 30)) return false;  // grid words hold slots below 2^30
     if (h->n_types < 2 || h->n_fields[FISH] != 3 || h->n_fields[SHARK] != 4) return false;
     for (int f = 0; f < 3; ++f)
         if (h->field_bytes[FISH][f] != 4) return false;
@@ -674,7 +696,8 @@ extern "C" int dsr_wator_batch_instance_bytes(const dsr_wator_batch* b, int W, i
 
 extern "C" int dsr_wator_batch_add(dsr_wator_batch* b, const dsr_wator_params* p, uint64_t n_blocks,
                                    const void* kind0_dev, void* stream, int* inst_out) {
-    if (!b || !params_ok(p) || !kind0_dev || !inst_out || n_blocks == 0) return DSR_E_INVALID;
+    if (!b || !params_ok(p) || !kind0_dev || !inst_out || n_blocks == 0 || n_blocks > kMaxBlocks)
+        return DSR_E_INVALID;
     int slot = -1;
     dsr_heap* heap = nullptr;
     void* extra = nullptr;

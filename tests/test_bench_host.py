@@ -17,10 +17,10 @@ import bench  # noqa: E402
 
 def test_phase_bytes_follow_the_documented_model():
     # per visited object + 12 per listed block + per event
-    assert bench.phase_bytes("F1", 1000, 20, 0, 0, 0) == 68 * 1000 + 12 * 20
-    assert bench.phase_bytes("F2", 1000, 20, 300, 100, 0) == 20 * 1000 + 12 * 20 + 28 * 300 + 16 * 100
-    assert bench.phase_bytes("S0", 50, 2, 0, 0, 7) == 8 * 50 + 12 * 2 + 16 * 7
-    assert bench.phase_bytes("S2", 50, 2, 30, 5, 9) == 20 * 50 + 12 * 2 + 36 * 30 + 8 * 9 + 20 * 5
+    assert bench.phase_bytes("F1", 1000, 20, 0, 0, 0) == 44 * 1000 + 12 * 20
+    assert bench.phase_bytes("F2", 1000, 20, 300, 100, 0) == 16 * 1000 + 12 * 20 + 24 * 300 + 16 * 100
+    assert bench.phase_bytes("S0", 50, 2, 0, 0, 7) == 8 * 50 + 12 * 2 + 12 * 7
+    assert bench.phase_bytes("S2", 50, 2, 30, 5, 9) == 16 * 50 + 12 * 2 + 28 * 30 + 8 * 9 + 20 * 5
 
 
 def test_roofline_takes_the_slowest_method_kernel():
@@ -53,11 +53,12 @@ def test_summary_carries_batched_and_plain_side_by_side():
                                                 "frees_per_s": 6e10}]},
             "streaming_doall": {"K4": {"100%": {"frac": 0.99}}}, "nbody_65536": {"ms_per_step": 3.0},
             "served": {"jobs_done": 5, "step_ms_p50": 1.0, "step_ms_p99": 2.0, "job_s_p50": 3.0, "job_s_p99": 4.0,
-                       "admit_ms_p50": 0.5, "admit_ms_p99": 0.9}}
+                       "admit_ms_per_job_p50": 0.5, "admit_ms_per_job_p99": 0.9, "step_ms_per_mcell_p50": 0.1,
+                       "step_ms_per_mcell_p99": 0.2}}
     s = bench.summary(line)
     assert s["batched_vs_plain"] == 1.5 and s["plain_object_updates_per_s"] == 2.0e10
     assert s["allocs_per_s"] == 5e9 and s["streaming_frac_of_hbm_100pct_fill"] == {"K4": 0.99}
-    assert s["served"]["admit_ms_p99"] == 0.9
+    assert s["served"]["admit_ms_per_job_p99"] == 0.9 and s["served"]["step_ms_per_mcell_p99"] == 0.2
     assert len(json.dumps(s)) < 1200  # fits the tail a log keeps
 
 
