@@ -68,6 +68,7 @@ struct NbWs {
     uint32_t* coff;    // [NKEYS + 1] first sorted position of each cell (positions before the update)
     uint32_t* coff2;   // [NKEYS + 1] the same for the positions after the update
     uint32_t* ckey;    // [P] cell key of each element being sorted
+    uint32_t* csum;    // [NKEYS / 1024] cells per CTA of the prefix sum
     uint32_t* perm;    // [P] dense slot of each sorted position
     uint32_t* perm2;   // [P] sorted position of each entry of the second order
     uint32_t* n_live;  // bodies in this step
@@ -173,33 +174,61 @@ __global__ void k_cell_count(const __grid_constant__ dsr_dev_heap H, const __gri
     }
 }
 
-// Exclusive prefix sum of the cell counts (one CTA of 1024 threads, each
-// summing 32 consecutive cells). For the first order the total is the live
-// body count, and the step's near-pair count starts at 0.
-__global__ void __launch_bounds__(1024) k_cell_scan(const __grid_constant__ NbWs ws, int post) {
-    __shared__ uint32_t part[1024];
-    constexpr uint32_t PER = NKEYS / 1024;
-    uint32_t* coff = post ? ws.coff2 : ws.coff;
-    const uint32_t lo = threadIdx.x * PER;
-    uint32_t s = 0;
-    for (uint32_t c = lo; c < lo + PER; ++c) s += ws.ccount[c];
-    part[threadIdx.x] = s;
+// Exclusive prefix sum of the cell counts, in two launches of NKEYS / 1024
+// CTAs: each CTA sums its 1024 cells (k_cell_sum), then each CTA scans its
+// cells from the sum of the CTAs before it (k_cell_scan). For the first order
+// the total is the live body count, and the step's near-pair count starts
+// at 0.
+constexpr uint32_t SCAN_CTAS = NKEYS / 1024;
+
+__global__ void __launch_bounds__(1024) k_cell_sum(const __grid_constant__ NbWs ws) {
+    const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, ws.ccount[blockIdx.x * 1024 + threadIdx.x]);
+    __shared__ uint32_t w[32];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = v;
     __syncthreads();
-    for (uint32_t d = 1; d < 1024; d <<= 1) {  // inclusive scan of the run sums
-        const uint32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    if (threadIdx.x < 32) {
+        const uint32_t t = __reduce_add_sync(0xFFFFFFFFu, w[threadIdx.x]);
+        if (threadIdx.x == 0) ws.csum[blockIdx.x] = t;
     }
-    uint32_t run = part[threadIdx.x] - s;
-    for (uint32_t c = lo; c < lo + PER; ++c) {
-        coff[c] = run;
-        run += ws.ccount[c];
+}
+
+__global__ void __launch_bounds__(1024) k_cell_scan(const __grid_constant__ NbWs ws, int post) {
+    __shared__ uint32_t w[32];
+    __shared__ uint32_t base;
+    uint32_t* coff = post ? ws.coff2 : ws.coff;
+    if (threadIdx.x < 32) {
+        uint32_t b = 0;
+        for (uint32_t k = threadIdx.x; k < blockIdx.x; k += 32) b += ws.csum[k];
+        b = __reduce_add_sync(0xFFFFFFFFu, b);
+        if (threadIdx.x == 0) base = b;
     }
-    if (threadIdx.x == 1023) {
-        coff[NKEYS] = part[1023];
+    const uint32_t c = blockIdx.x * 1024 + threadIdx.x;
+    const uint32_t v = ws.ccount[c];
+    const unsigned lane = threadIdx.x & 31;
+    uint32_t x = v;  // inclusive warp scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    if (lane == 31) w[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t t = w[threadIdx.x];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if (threadIdx.x >= (unsigned)o) t += y;
+        }
+        w[threadIdx.x] = t;  // inclusive scan of the warp totals
+    }
+    __syncthreads();
+    const uint32_t before = base + (threadIdx.x >= 32 ? w[(threadIdx.x >> 5) - 1] : 0u) + x - v;
+    coff[c] = before;
+    if (c == NKEYS - 1) {
+        coff[NKEYS] = before + v;
         if (!post) {
-            *ws.n_live = part[1023];
+            *ws.n_live = before + v;
             *ws.npairs = 0;
         }
     }
@@ -555,18 +584,29 @@ __global__ void __launch_bounds__(TILE) k_force64(const __grid_constant__ dsr_de
 // ---------------------------------------------------------------------------
 // update, partner search, merge
 // ---------------------------------------------------------------------------
-// Visit the sorted entries of the 27 cells around (and including) the cell
-// of (x, y, z), cells in a fixed order: fn(q) for each position q of the
-// first order, or (POST) for the position perm2[q] of each entry q of the
-// second order.
+// Visit the sorted entries of the cells around (and including) the cell of
+// (x, y, z) that lie within `rad` of the point on each axis (of the 27
+// neighbours, those the search radius reaches), cells in a fixed order:
+// fn(q) for each position q of the first order, or (POST) for the position
+// perm2[q] of each entry q of the second order. Cells are at least as wide
+// as rad, so no other cell holds a body within rad.
 template <bool POST, class F>
-__device__ __forceinline__ void for_neighbours(const NbWs& ws, float x, float y, float z, F fn) {
+__device__ __forceinline__ void for_neighbours(const NbWs& ws, float x, float y, float z, float rad, F fn) {
     const int K = ws.K;
+    const float inv = 1.f / (float)K;
     const int cx = cell_coord(x, K), cy = cell_coord(y, K), cz = cell_coord(z, K);
+    // a neighbour below (above) on an axis is needed when the point is within
+    // rad of that face of its cell; border cells extend to infinity
+    const int x0 = cx > 0 && x - (float)cx * inv < rad ? cx - 1 : cx;
+    const int x1 = cx < K - 1 && (float)(cx + 1) * inv - x < rad ? cx + 1 : cx;
+    const int y0 = cy > 0 && y - (float)cy * inv < rad ? cy - 1 : cy;
+    const int y1 = cy < K - 1 && (float)(cy + 1) * inv - y < rad ? cy + 1 : cy;
+    const int z0 = cz > 0 && z - (float)cz * inv < rad ? cz - 1 : cz;
+    const int z1 = cz < K - 1 && (float)(cz + 1) * inv - z < rad ? cz + 1 : cz;
     const uint32_t* coff = POST ? ws.coff2 : ws.coff;
-    for (int ix = cx > 0 ? cx - 1 : 0; ix <= (cx < K - 1 ? cx + 1 : K - 1); ++ix)
-        for (int iy = cy > 0 ? cy - 1 : 0; iy <= (cy < K - 1 ? cy + 1 : K - 1); ++iy)
-            for (int iz = cz > 0 ? cz - 1 : 0; iz <= (cz < K - 1 ? cz + 1 : K - 1); ++iz) {
+    for (int ix = x0; ix <= x1; ++ix)
+        for (int iy = y0; iy <= y1; ++iy)
+            for (int iz = z0; iz <= z1; ++iz) {
                 const uint32_t c = cell_key(ix, iy, iz);
                 for (uint32_t q = coff[c]; q < coff[c + 1]; ++q) fn(POST ? ws.perm2[q] : q);
             }
@@ -601,7 +641,9 @@ __device__ uint32_t update_body(const dsr_dev_heap& H, const NbArgs& a, uint32_t
         const float4 u = a.ws.pos[p];
         const float eps2 = (float)(a.p.eps * a.p.eps);
         const double eps2d = a.p.eps * a.p.eps;
-        for_neighbours<false>(a.ws, u.x, u.y, u.z, [&](uint32_t q) {
+        // pairs the FP32 test can pass lie within r_near of the body, up to
+        // the rounding of r^2 (a margin of 1e-3 relative covers it)
+        for_neighbours<false>(a.ws, u.x, u.y, u.z, (float)(a.p.r_near * 1.001), [&](uint32_t q) {
             if (q == p) return;
             float dx, dy, dz;
             if (!(pair_r2(a.ws.pos[q], u.x, u.y, u.z, eps2, dx, dy, dz) < rn2)) return;
@@ -671,7 +713,7 @@ __global__ void k_partner(const __grid_constant__ dsr_dev_heap H, const __grid_c
         const float4 u = a.ws.npos[p];
         const D4 ud = a.ws.npd[p];
         int32_t best_id = 0x7FFFFFFF, best = -1;
-        for_neighbours<true>(a.ws, u.x, u.y, u.z, [&](uint32_t q) {
+        for_neighbours<true>(a.ws, u.x, u.y, u.z, sqrtf(rw2) * 1.001f, [&](uint32_t q) {
             if (q == p) return;
             const float4 v = a.ws.npos[q];
             const float dx = v.x - u.x, dy = v.y - u.y, dz = v.z - u.z;
@@ -814,6 +856,8 @@ void carve_common(uint8_t*& p, uint64_t P, NbWs& w) {
     p += round256((NKEYS + 1) * 4);
     w.coff2 = reinterpret_cast<uint32_t*>(p);
     p += round256((NKEYS + 1) * 4);
+    w.csum = reinterpret_cast<uint32_t*>(p);
+    p += 256;
     w.ckey = reinterpret_cast<uint32_t*>(p);
     p += round256(P * 4);
     w.perm = reinterpret_cast<uint32_t*>(p);
@@ -840,7 +884,7 @@ void carve_common(uint8_t*& p, uint64_t P, NbWs& w) {
     p += round256(P * 4);
 }
 size_t common_bytes(uint64_t P) {
-    return round256(NKEYS * 4) + 2 * round256((NKEYS + 1) * 4) + 3 * round256(P * 4) + round256(P * 16) +
+    return round256(NKEYS * 4) + 2 * round256((NKEYS + 1) * 4) + 256 + 3 * round256(P * 4) + round256(P * 16) +
            round256(P * 32) + round256(P * 4) + round256(P * 8) + round256(P / TILE * 32) + round256(P * 16) +
            2 * round256(P * 32) + round256(P * 4);
 }
@@ -873,7 +917,8 @@ template <bool POST>
 void launch_sort(dsr_heap* h, const NbArgs& a, cudaStream_t s) {
     const unsigned ctas = (unsigned)(h->sm_count * 4);
     k_cell_count<POST><<<ctas, 256, 0, s>>>(h->dev, a.ws);
-    k_cell_scan<<<1, 1024, 0, s>>>(a.ws, POST ? 1 : 0);
+    k_cell_sum<<<SCAN_CTAS, 1024, 0, s>>>(a.ws);
+    k_cell_scan<<<SCAN_CTAS, 1024, 0, s>>>(a.ws, POST ? 1 : 0);
     k_cell_place<POST><<<ctas, 256, 0, s>>>(h->dev, a.ws);
     k_cell_order<POST><<<NKEYS / 256, 256, 0, s>>>(h->dev, a.ws);
 }
@@ -1007,6 +1052,7 @@ struct NoallocScratch {
     uint32_t ccount[NKEYS];  // zero at load; every sort leaves it zero
     uint32_t coff[NKEYS + 1];
     uint32_t coff2[NKEYS + 1];
+    uint32_t csum[SCAN_CTAS];
     uint32_t ckey[kNoallocP];
     uint32_t perm[kNoallocP];
     uint32_t perm2[kNoallocP];
@@ -1075,6 +1121,7 @@ extern "C" int dsr_nbody_step_noalloc(dsr_heap* heap, const dsr_nbody_params* p,
     a.ws.ccount = sc->ccount;
     a.ws.coff = sc->coff;
     a.ws.coff2 = sc->coff2;
+    a.ws.csum = sc->csum;
     a.ws.ckey = sc->ckey;
     a.ws.perm = sc->perm;
     a.ws.perm2 = sc->perm2;
