@@ -89,8 +89,10 @@ class Server:
                 ahead += 1
         resident = {}  # (app, slot) -> [job, steps_left, admitted_at]
         done = []
-        ticks = []  # (start event, end event, resident count)
+        ticks = []  # (start event, end event, resident count, resident cells)
         admit_ms, retire_ms = [], []  # host time of ticks that changed the resident set
+        admit_n = []  # jobs admitted in those ticks
+        cells = 0  # cells of the resident jobs
         t0 = time.perf_counter()
         visits = 0
 
@@ -121,6 +123,7 @@ class Server:
                     continue
                 del starts[job["id"]]
                 resident[(job["app"], slot)] = [job, int(job["steps"]), now()]
+                cells += int(job["side"]) ** 2
                 admitted += 1
             kept.extend(waiting)
             waiting = kept
@@ -139,6 +142,7 @@ class Server:
             if admitted:
                 self.stream.synchronize()  # the admitted jobs' initial states are created
                 admit_ms.append((time.perf_counter() - t_adm) * 1e3)
+                admit_n.append(admitted)
             # one tick: a batched step of each application that has jobs
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(self.stream)
@@ -147,7 +151,7 @@ class Server:
             if self.gb.inst:
                 self.gb.step(1)
             b.record(self.stream)
-            ticks.append((a, b, len(resident)))
+            ticks.append((a, b, len(resident), cells))
             finished = []
             for key, rec in resident.items():
                 rec[1] -= 1
@@ -160,6 +164,7 @@ class Server:
                 for key in finished:
                     app, slot = key
                     job, _, t_adm = resident.pop(key)
+                    cells -= int(job["side"]) ** 2
                     batch = self._batch(app)
                     heap = batch.heap(slot)
                     visits += heap.counters()["visits"]
@@ -172,10 +177,11 @@ class Server:
         pool.shutdown(wait=False, cancel_futures=True)
         torch.cuda.synchronize()
         wall = now()
-        step_ms = [x.elapsed_time(y) for x, y, _ in ticks]
+        step_ms = [x.elapsed_time(y) for x, y, _, _ in ticks]
         for key, rec in resident.items():  # count the work of jobs still resident
             visits += self._batch(key[0]).heap(key[1]).counters()["visits"]
-        return {"done": done, "step_ms": step_ms, "resident": [k for _, _, k in ticks], "admit_ms": admit_ms,
+        return {"done": done, "step_ms": step_ms, "resident": [k for _, _, k, _ in ticks],
+                "resident_cells": [c for _, _, _, c in ticks], "admit_ms": admit_ms, "admit_n": admit_n,
                 "retire_ms": retire_ms, "wall_s": wall, "visits": visits,
                 "unfinished": len(resident) + len(waiting) + len(pending)}
 
@@ -187,6 +193,11 @@ def summarize(report):
         return float(np.percentile(np.array(xs), q)) if len(xs) else 0.0
 
     lat = [d["completed"] - d["arrival"] for d in report["done"]]
+    # device time per million resident cells: a tick's time grows with the
+    # cells resident, so raw tick percentiles mix load with stalls; per cell,
+    # a p99 far above the p50 points at stalls
+    per_cell = [ms / (c / 1e6) for ms, c in zip(report["step_ms"], report.get("resident_cells", [])) if c]
+    per_job = [ms / n for ms, n in zip(report.get("admit_ms", []), report.get("admit_n", [])) if n]
     return {
         "jobs_done": len(report["done"]), "jobs_unfinished": report["unfinished"], "ticks": len(report["step_ms"]),
         "step_ms_p50": pct(report["step_ms"], 50), "step_ms_p99": pct(report["step_ms"], 99),
@@ -195,6 +206,8 @@ def summarize(report):
         "retire_ms_p50": pct(report.get("retire_ms", []), 50),
         "retire_ms_p99": pct(report.get("retire_ms", []), 99),
         "resident_p50": pct(report.get("resident", []), 50), "resident_max": max(report.get("resident", [0]) or [0]),
+        "step_ms_per_mcell_p50": pct(per_cell, 50), "step_ms_per_mcell_p99": pct(per_cell, 99),
+        "admit_ms_per_job_p50": pct(per_job, 50), "admit_ms_per_job_p99": pct(per_job, 99),
         "object_updates_per_s": report["visits"] / report["wall_s"] if report["wall_s"] else 0.0,
         "wall_s": report["wall_s"],
     }

@@ -164,4 +164,5 @@ def test_report_times_admissions_and_retirements():
     out = serve.summarize(rep)
     assert len(rep["admit_ms"]) >= 1 and len(rep["retire_ms"]) >= 1
     assert out["admit_ms_p99"] >= out["admit_ms_p50"] >= 0 and 1 <= out["resident_max"] <= 5
-    assert len(rep["resident"]) == out["ticks"]
+    assert len(rep["resident"]) == out["ticks"] == len(rep["resident_cells"])
+    assert out["step_ms_per_mcell_p50"] > 0 and out["admit_ms_per_job_p50"] >= 0
