@@ -660,10 +660,11 @@ __device__ __forceinline__ void dsr_doall_body(const dsr_dev_heap& H, int T, con
         __syncwarp();
         const dsr_u64 i = g >> sh;
         const unsigned s = (unsigned)(g & ((1u << sh) - 1));
-        if (((H.R_mask[i] >> s) & 1ull) && dsr_check(H.R_bid[i] < H.M, H.err, H.dbg, 10, i)) {
-            const uint32_t bid = H.R_bid[i];
+        // i < R_count: both entries are valid, so they load together
+        const dsr_u64 mask = H.R_mask[i];
+        const uint32_t bid = H.R_bid[i];
+        if (((mask >> s) & 1ull) && dsr_check(bid < H.M, H.err, H.dbg, 10, i))
             Method::run(H, dsr_listed_type(H, T, bid), args, ((dsr_u64)bid << 6) | s);
-        }
     }
     if (dsr_doall_finish(H, keep_list != 0)) dsr_call_finish<Method>(H, T, args, 0);
 }
@@ -712,7 +713,8 @@ __global__ void dsr_doall_kernel_vec4(const __grid_constant__ dsr_dev_heap H, in
         const dsr_u64 i = g >> sh;
         const unsigned q = (unsigned)(g & ((1u << sh) - 1));
         const unsigned live = (unsigned)(H.R_mask[i] >> (4 * q)) & 0xFu;
-        if (live && dsr_check(H.R_bid[i] < H.M, H.err, H.dbg, 10, i)) Method::run4(H, T, args, H.R_bid[i], 4 * q, live);
+        const uint32_t bid = H.R_bid[i];
+        if (live && dsr_check(bid < H.M, H.err, H.dbg, 10, i)) Method::run4(H, T, args, bid, 4 * q, live);
     }
     if (dsr_doall_finish(H, keep_list != 0)) dsr_call_finish<Method>(H, T, args, 0);
 }

@@ -142,8 +142,9 @@ __global__ void dsr_bm_doall_kernel(const __grid_constant__ dsr_bm_dev H, int T,
         __syncwarp();  // warp-uniform loop, as in dsr_doall_kernel
         const dsr_u64 i = g >> 6;
         const unsigned s = (unsigned)(g & 63);
-        if ((H.R_mask[i] >> s) & 1ull)
-            Method::run(H, T, args, ((dsr_u64)T << DSR_BM_SLOT_BITS) | (((dsr_u64)H.R_word[i] << 6) | s));
+        const dsr_u64 mask = H.R_mask[i];  // loaded together with the word index
+        const dsr_u64 word = H.R_word[i];
+        if ((mask >> s) & 1ull) Method::run(H, T, args, ((dsr_u64)T << DSR_BM_SLOT_BITS) | ((word << 6) | s));
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -119,6 +119,16 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     s = t;
 }
 
+// Error-free sum (Knuth's TwoSum): s + x = t + err exactly, t = fl(s + x).
+// Accumulating err in e keeps s + e within about 2^-43 relative of the exact
+// sum of a few dozen FP32 terms, in FP32 arithmetic only.
+__device__ __forceinline__ void two_sum_add(float& s, float& e, float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    e += (s - (t - bp)) + (x - bp);
+    s = t;
+}
+
 // Dense slot count of the current block list.
 __device__ __forceinline__ uint32_t n_dense(const dsr_dev_heap& H) { return (*(volatile uint32_t*)H.R_count) << 6; }
 
@@ -621,18 +631,27 @@ __device__ uint32_t update_body(const dsr_dev_heap& H, const NbArgs& a, uint32_t
                                 bool f64) {
     const dsr_ref r = a.ws.sref[p];
     double ax = 0.0, ay = 0.0, az = 0.0;
-    for (uint32_t k = 0; k < ns; ++k) {
-        if (f64) {
+    if (f64) {
+        for (uint32_t k = 0; k < ns; ++k) {
             const D4 v = a.ws.part64[k * stride + p];
             ax += v.x;
             ay += v.y;
             az += v.z;
-        } else {
-            const float4 v = a.ws.part[k * stride + p];
-            ax += (double)v.x;
-            ay += (double)v.y;
-            az += (double)v.z;
         }
+    } else {
+        // FP32 slices: summed as FP32 pairs (error-free additions), which is
+        // as exact here as FP64 additions and keeps the FP64 units, a small
+        // fraction of GB300's FP32 rate, for the near field and the update
+        float sx = 0.f, sy = 0.f, sz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+        for (uint32_t k = 0; k < ns; ++k) {
+            const float4 v = a.ws.part[k * stride + p];
+            two_sum_add(sx, ex, v.x);
+            two_sum_add(sy, ey, v.y);
+            two_sum_add(sz, ez, v.z);
+        }
+        ax = (double)sx + (double)ex;
+        ay = (double)sy + (double)ey;
+        az = (double)sz + (double)ez;
     }
     const D4 pi = a.ws.pd[p];
     const float rn2 = (float)(a.p.r_near * a.p.r_near);
