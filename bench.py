@@ -895,7 +895,8 @@ def bench_served(seconds=20.0, n_jobs=10000, arena_gb=64, lo=128, hi=4096, steps
 # the (steps, warmup) window it was taken on. The bench reports it only when
 # it runs that window (the population, hence the bytes of a launch, changes
 # from step to step); a kernel changed since its capture has no entry.
-TRAFFIC = {}
+TRAFFIC = {"F2": {"bytes": 68634957, "steps": 20, "warmup": 5, "cache_control": "none",
+                  "source": "profiles/wator2048_fish_move_traffic.md"}}
 
 
 def roofline(phases, peak, peak_kind, steps, warmup):
@@ -906,13 +907,33 @@ def roofline(phases, peak, peak_kind, steps, warmup):
     cap = TRAFFIC.get(p)
     same_window = cap is not None and (cap["steps"], cap["warmup"]) == (steps, warmup)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
             "traffic": cap["bytes"] if same_window else None,
-            "traffic_window": ({"steps": cap["steps"], "warmup": cap["warmup"], "source": cap["source"]}
+            "traffic_window": ({"steps": cap["steps"], "warmup": cap["warmup"], "source": cap["source"],
+                                "cache_control": cap.get("cache_control")}
                                if cap is not None else None),
             "kernel": ph["kernel"], "phase": p,
             "algorithmic_bytes_per_launch": ph["bytes_per_launch"], "launch_ms": ph["method_ms_per_step"],
             "timing": "CUDA events on the launching stream around every launch of the timed steps",
             "peak_source": ("measured hbm_gbs" if peak_kind == "measured" else "fallback 6.8 TB/s")}
+
+
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal
+
+
+def batched_hbm_estimate(line, peak):
+    """Algorithmic HBM bandwidth of the batched step, estimated: the batched
+    form runs the same five phases over instances of the same rules, so its
+    bytes per object-update are taken from the plain run's per-phase byte
+    counts (summed over the phases of a step) divided by the plain run's
+    object-updates per step."""
+    bytes_step = sum(ph["bytes_per_launch"] for ph in line["phases"].values())
+    visits_step = line["value"] * line["ms_per_step"] / 1e3
+    per_update = bytes_step / visits_step
+    gbs = line["batched"]["object_updates_per_s"] * per_update / 1e9
+    return {"algorithmic_gbs": gbs, "bytes_per_object_update": per_update, "frac": gbs / peak,
+            "frac_of_nominal": gbs / NOMINAL_HBM_GBS,
+            "method": "plain run's algorithmic bytes per object-update x batched object-updates/s"}
 
 
 def summary(line):
@@ -937,6 +958,7 @@ def summary(line):
         out["batched_object_updates_per_s"] = r3(b["object_updates_per_s"])
         out["batched_vs_plain"] = r3(b["object_updates_per_s"] / line["value"])
         out["batched_vs_one_by_one"] = r3(b.get("speedup_vs_one_by_one"))
+        out["batched_frac_of_hbm_est"] = r3(g(b, "hbm_est", "frac"))
     a = g(line, "alloc_free_microbench", "rows")
     if a:
         two = [x for x in a if x["types"] == 2 and x["objects"] == 1 << 24]
@@ -1053,6 +1075,7 @@ def main():
         # the other halves of the metric: batched vs plain, alloc+free/s, the
         # streaming do-all against the HBM roofline, and the served form
         line["batched"] = bench_batched()
+        line["batched"]["hbm_est"] = batched_hbm_estimate(line, peak)
         line["alloc_free_microbench"] = bench_alloc_sweep()
         line["streaming_doall"] = bench_streaming_sweep()
         line["gol_64"] = bench_gol()

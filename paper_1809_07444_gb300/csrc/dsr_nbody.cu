@@ -600,6 +600,29 @@ __global__ void __launch_bounds__(TILE) k_force64(const __grid_constant__ dsr_de
 // fn(q) for each position q of the first order, or (POST) for the position
 // perm2[q] of each entry q of the second order. Cells are at least as wide
 // as rad, so no other cell holds a body within rad.
+// The same walk restricted to the cells of column ix - 1 + slab (slab 0, 1
+// or 2: the lower, own and upper x neighbour), nothing when the search does
+// not reach that column.
+template <class F>
+__device__ __forceinline__ void for_neighbours_slab(const NbWs& ws, float x, float y, float z, float rad, int slab,
+                                                    F fn) {
+    const int K = ws.K;
+    const float inv = 1.f / (float)K;
+    const int cx = cell_coord(x, K), cy = cell_coord(y, K), cz = cell_coord(z, K);
+    const int ix = cx - 1 + slab;
+    if (slab == 0 && !(cx > 0 && x - (float)cx * inv < rad)) return;
+    if (slab == 2 && !(cx < K - 1 && (float)(cx + 1) * inv - x < rad)) return;
+    const int y0 = cy > 0 && y - (float)cy * inv < rad ? cy - 1 : cy;
+    const int y1 = cy < K - 1 && (float)(cy + 1) * inv - y < rad ? cy + 1 : cy;
+    const int z0 = cz > 0 && z - (float)cz * inv < rad ? cz - 1 : cz;
+    const int z1 = cz < K - 1 && (float)(cz + 1) * inv - z < rad ? cz + 1 : cz;
+    for (int iy = y0; iy <= y1; ++iy)
+        for (int iz = z0; iz <= z1; ++iz) {
+            const uint32_t c = cell_key(ix, iy, iz);
+            for (uint32_t q = ws.coff[c]; q < ws.coff[c + 1]; ++q) fn(q);
+        }
+}
+
 template <bool POST, class F>
 __device__ __forceinline__ void for_neighbours(const NbWs& ws, float x, float y, float z, float rad, F fn) {
     const int K = ws.K;
@@ -622,15 +645,26 @@ __device__ __forceinline__ void for_neighbours(const NbWs& ws, float x, float y,
             }
 }
 
-// The update of the body at sorted position p: the far-field slices summed
-// in slice order (in FP64); with FP32 pairs, the near field in FP64 over the
-// pairs the force kernels left out (the same FP32 test, on the cells around
-// the body); then v += a dt and x += v dt on the full state, stored back as
-// FP32 pairs. Returns the body's near pairs.
-__device__ uint32_t update_body(const dsr_dev_heap& H, const NbArgs& a, uint32_t p, uint32_t ns, size_t stride,
-                                bool f64) {
-    const dsr_ref r = a.ws.sref[p];
-    double ax = 0.0, ay = 0.0, az = 0.0;
+// r^-3 for r2 = r^2 in FP64. Newton's iteration for 1/sqrt(r2), y <- y (3 -
+// r2 y^2) / 2, from the FP32 estimate: a relative error e becomes about
+// 1.5 e^2, so two steps take the estimate's 2^-22 below FP64 rounding, with
+// six FP64 multiply-adds where a square root and a division cost several
+// times that on GB300's FP64 units. Outside the FP32 range of the estimate
+// the plain expression is used.
+__device__ __forceinline__ double rsqrt_cubed(double r2) {
+    if (!(r2 >= (double)FLT_MIN && r2 <= (double)FLT_MAX)) return 1.0 / (r2 * sqrt(r2));
+    double y = (double)rsqrtf((float)r2);
+    y = y * (1.5 - 0.5 * r2 * y * y);
+    y = y * (1.5 - 0.5 * r2 * y * y);
+    return y * y * y;
+}
+
+// Far field of the body at sorted position p: its slices summed in slice
+// order. FP32 slices are summed as FP32 pairs (error-free additions), which
+// is as exact here as FP64 additions and keeps the FP64 units, a small
+// fraction of GB300's FP32 rate, free for the near field and the update.
+__device__ __forceinline__ void far_field(const NbArgs& a, uint32_t p, uint32_t ns, size_t stride, bool f64,
+                                          double& ax, double& ay, double& az) {
     if (f64) {
         for (uint32_t k = 0; k < ns; ++k) {
             const D4 v = a.ws.part64[k * stride + p];
@@ -638,64 +672,80 @@ __device__ uint32_t update_body(const dsr_dev_heap& H, const NbArgs& a, uint32_t
             ay += v.y;
             az += v.z;
         }
-    } else {
-        // FP32 slices: summed as FP32 pairs (error-free additions), which is
-        // as exact here as FP64 additions and keeps the FP64 units, a small
-        // fraction of GB300's FP32 rate, for the near field and the update
-        float sx = 0.f, sy = 0.f, sz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
-        for (uint32_t k = 0; k < ns; ++k) {
-            const float4 v = a.ws.part[k * stride + p];
-            two_sum_add(sx, ex, v.x);
-            two_sum_add(sy, ey, v.y);
-            two_sum_add(sz, ez, v.z);
+        return;
+    }
+    float sx = 0.f, sy = 0.f, sz = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+    // slices loaded four at a time, then added in order
+    uint32_t k = 0;
+    for (; k + 4 <= ns; k += 4) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = a.ws.part[(k + u) * stride + p];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            two_sum_add(sx, ex, v[u].x);
+            two_sum_add(sy, ey, v[u].y);
+            two_sum_add(sz, ez, v[u].z);
         }
-        ax = (double)sx + (double)ex;
-        ay = (double)sy + (double)ey;
-        az = (double)sz + (double)ez;
     }
-    const D4 pi = a.ws.pd[p];
-    const float rn2 = (float)(a.p.r_near * a.p.r_near);
-    uint32_t near = 0;
-    if (!f64 && rn2 > 0.f) {
-        const float4 u = a.ws.pos[p];
-        const float eps2 = (float)(a.p.eps * a.p.eps);
-        const double eps2d = a.p.eps * a.p.eps;
-        // pairs the FP32 test can pass lie within r_near of the body, up to
-        // the rounding of r^2 (a margin of 1e-3 relative covers it)
-        for_neighbours<false>(a.ws, u.x, u.y, u.z, (float)(a.p.r_near * 1.001), [&](uint32_t q) {
-            if (q == p) return;
-            float dx, dy, dz;
-            if (!(pair_r2(a.ws.pos[q], u.x, u.y, u.z, eps2, dx, dy, dz) < rn2)) return;
-            const D4 pj = a.ws.pd[q];
-            const double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
-            const double r2 = ex * ex + ey * ey + ez * ez + eps2d;
-            const double w = pj.w / (r2 * sqrt(r2));
-            ax += w * ex;
-            ay += w * ey;
-            az += w * ez;
-            ++near;
-        });
+    for (; k < ns; ++k) {
+        const float4 v = a.ws.part[k * stride + p];
+        two_sum_add(sx, ex, v.x);
+        two_sum_add(sy, ey, v.y);
+        two_sum_add(sz, ez, v.z);
     }
-    const double G = a.p.G, dt = a.p.dt;
-    const double vx = get2(H, r, VX) + G * ax * dt;
-    const double vy = get2(H, r, VY) + G * ay * dt;
-    const double vz = get2(H, r, VZ) + G * az * dt;
-    const double x = pi.x + vx * dt, y = pi.y + vy * dt, z = pi.z + vz * dt;
-    put2(H, r, VX, vx);
-    put2(H, r, VY, vy);
-    put2(H, r, VZ, vz);
-    put2(H, r, PX, x);
-    put2(H, r, PY, y);
-    put2(H, r, PZ, z);
-    a.ws.npos[p] = make_float4(*fld(H, r, PX), *fld(H, r, PY), *fld(H, r, PZ), *fld(H, r, MASS));
-    a.ws.npd[p] = d4(x, y, z, pi.w);
-    a.ws.nvd[p] = d4(vx, vy, vz, 0.0);
-    return near;
+    ax = (double)sx + (double)ex;
+    ay = (double)sy + (double)ey;
+    az = (double)sz + (double)ez;
 }
 
-// Update of every body; `grid` is the split force kernel's grid (0: the
-// unsplit kernel's single slice).
-__global__ void k_update(const __grid_constant__ dsr_dev_heap H, const __grid_constant__ NbArgs a, uint32_t grid) {
+// One near pair in FP64 from the full state: the acceleration of the body
+// at full position pi from body j (position and mass pj).
+__device__ __forceinline__ void near_term(const D4& pi, const D4& pj, double eps2d, double& cx, double& cy,
+                                          double& cz) {
+    const double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
+    const double w = pj.w * rsqrt_cubed(ex * ex + ey * ey + ez * ez + eps2d);
+    cx = w * ex;
+    cy = w * ey;
+    cz = w * ez;
+}
+
+// A queued near pair of a warp and its FP64 term.
+struct NearSlot {
+    uint32_t p, q;
+    double x, y, z;
+};
+constexpr int NEAR_Q = 4;                       // pairs a lane queues; more are computed in place
+constexpr int NEAR_SLOTS = 32 * NEAR_Q;         // per warp
+constexpr int UPDATE_THREADS = 256;
+
+// The update: four lanes per body. Lanes 0-2 of a body's quad take the near
+// field (FP32 pairs only) from the lower, own and upper x column of cells
+// around it: the pairs the force kernels left out (the same FP32 test),
+// added in FP64 from the full state in cell and body order. Lane 3 sums the
+// far-field slices. Lane k of the quad (k < 3) then adds the four parts of
+// axis k in a fixed order (far, then the columns from low to high), so a
+// step stays deterministic, and does that axis of v += a dt, x += v dt
+// (semi-implicit Euler) in FP64 on the full state, stored back as FP32
+// pairs; lane 3 writes the mass parts of the new state. `grid` is the split
+// force kernel's grid (0: the unsplit kernel's single slice).
+//
+// FP64 work in a warp. GB300 issues FP64 instructions at a small fraction of
+// its FP32 rate, and a warp instruction costs the same however few lanes it
+// runs for. A near pair found by one lane in a divergent branch would cost
+// its ~20 FP64 instructions for the whole warp. So the walk only queues the
+// pairs (up to NEAR_Q a lane, in walk order) in a per-warp list, compacted
+// by a prefix sum; the warp then computes the list's terms with all lanes
+// busy, and each lane adds its own terms back in walk order. A lane with more
+// than NEAR_Q pairs computes the rest in place, in order, into a second sum.
+// For the same reason the update is split by axis over the quad.
+// At least three CTAs per SM (at most 85 registers): the walk is a chain of
+// dependent loads, and with two (90 registers unbounded) it waited on them;
+// four spilled and made the step slower.
+constexpr int UPDATE_MIN_CTAS = 3;
+__global__ void __launch_bounds__(UPDATE_THREADS, UPDATE_MIN_CTAS) k_update(const __grid_constant__ dsr_dev_heap H,
+                                                           const __grid_constant__ NbArgs a, uint32_t grid) {
+    __shared__ NearSlot slots[UPDATE_THREADS / 32][NEAR_SLOTS];
     const bool f64 = a.p.pair_precision == DSR_NBODY_PAIRS_FP64;
     uint32_t ns = 1;
     size_t stride = 0;
@@ -705,9 +755,105 @@ __global__ void k_update(const __grid_constant__ dsr_dev_heap H, const __grid_co
         stride = q.n;
     }
     const uint32_t n = n_bodies(a.ws);
+    const unsigned lane = threadIdx.x & 31u, sub = lane & 3u, quad = lane & ~3u;
+    NearSlot* sl = slots[threadIdx.x >> 5];
+    const float rn2 = (float)(a.p.r_near * a.p.r_near);
+    const float rad = (float)(a.p.r_near * 1.001);
+    const float eps2 = (float)(a.p.eps * a.p.eps);
+    const double eps2d = a.p.eps * a.p.eps;
+    const bool near_on = !f64 && rn2 > 0.f;
     uint32_t near = 0;
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
-        near += update_body(H, a, p, ns, stride, f64);
+    // 4 n lanes, rounded up to whole warps: every lane of a warp runs the
+    // same iterations, so the warp-wide steps below see the whole warp
+    const uint64_t lanes = ((uint64_t)n * 4 + 31) & ~31ull;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < lanes; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = (uint32_t)(t >> 2);
+        const bool live = p < n;
+        double ax = 0.0, ay = 0.0, az = 0.0;  // far field (lane 3) or queued near terms (lanes 0-2)
+        double ox = 0.0, oy = 0.0, oz = 0.0;  // near terms beyond the queue
+        uint32_t cnt = 0, qd[NEAR_Q] = {0, 0, 0, 0};
+        if (live && sub == 3) {
+            far_field(a, p, ns, stride, f64, ax, ay, az);
+        } else if (live && near_on) {
+            const D4 pi = a.ws.pd[p];
+            const float4 u = a.ws.pos[p];
+            // pairs the FP32 test can pass lie within r_near of the body, up
+            // to the rounding of r^2 (a margin of 1e-3 relative covers it)
+            for_neighbours_slab(a.ws, u.x, u.y, u.z, rad, (int)sub, [&](uint32_t q) {
+                if (q == p) return;
+                float dx, dy, dz;
+                if (!(pair_r2(a.ws.pos[q], u.x, u.y, u.z, eps2, dx, dy, dz) < rn2)) return;
+                if (cnt < NEAR_Q) {
+#pragma unroll
+                    for (int e = 0; e < NEAR_Q; ++e)
+                        if ((int)cnt == e) qd[e] = q;
+                } else {
+                    double cx, cy, cz;
+                    near_term(pi, a.ws.pd[q], eps2d, cx, cy, cz);
+                    ox += cx;
+                    oy += cy;
+                    oz += cz;
+                }
+                ++cnt;
+            });
+        }
+        near += cnt;
+        // compact the queued pairs of the warp: exclusive prefix sum of m
+        const uint32_t m = cnt < NEAR_Q ? cnt : NEAR_Q;
+        uint32_t incl = m;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if ((int)lane >= o) incl += v;
+        }
+        const uint32_t excl = incl - m, total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (total) {
+#pragma unroll
+            for (int e = 0; e < NEAR_Q; ++e)
+                if ((uint32_t)e < m) sl[excl + e].p = p, sl[excl + e].q = qd[e];
+            __syncwarp();
+            for (uint32_t k = lane; k < total; k += 32) {
+                double cx, cy, cz;
+                near_term(a.ws.pd[sl[k].p], a.ws.pd[sl[k].q], eps2d, cx, cy, cz);
+                sl[k].x = cx, sl[k].y = cy, sl[k].z = cz;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < NEAR_Q; ++e)
+                if ((uint32_t)e < m) ax += sl[excl + e].x, ay += sl[excl + e].y, az += sl[excl + e].z;
+            __syncwarp();  // the list is read before the next iteration writes it
+        }
+        if (cnt > NEAR_Q) ax += ox, ay += oy, az += oz;
+        // lane k of the quad gathers axis k: far (lane 3), then columns 0, 1, 2
+        double part[4];
+#pragma unroll
+        for (int src = 0; src < 4; ++src) {
+            const double vx = __shfl_sync(0xFFFFFFFFu, ax, quad + src);
+            const double vy = __shfl_sync(0xFFFFFFFFu, ay, quad + src);
+            const double vz = __shfl_sync(0xFFFFFFFFu, az, quad + src);
+            part[src] = sub == 0 ? vx : (sub == 1 ? vy : vz);
+        }
+        if (!live) continue;
+        const dsr_ref r = a.ws.sref[p];
+        double* npd = reinterpret_cast<double*>(a.ws.npd + p);
+        double* nvd = reinterpret_cast<double*>(a.ws.nvd + p);
+        float* npos = reinterpret_cast<float*>(a.ws.npos + p);
+        if (sub < 3) {
+            const double g = ((part[3] + part[0]) + part[1]) + part[2];
+            const double x0 = reinterpret_cast<const double*>(a.ws.pd + p)[sub];
+            const double v = get2(H, r, VX + (int)sub) + a.p.G * g * a.p.dt;
+            const double x = x0 + v * a.p.dt;
+            put2(H, r, VX + (int)sub, v);
+            put2(H, r, PX + (int)sub, x);
+            npos[sub] = *fld(H, r, PX + (int)sub);
+            npd[sub] = x;
+            nvd[sub] = v;
+        } else {
+            npos[3] = *fld(H, r, MASS);
+            npd[3] = a.ws.pd[p].w;
+            nvd[3] = 0.0;
+        }
+    }
     near = __reduce_add_sync(0xFFFFFFFFu, near);
     if ((threadIdx.x & 31) == 0 && near) atomicAdd(a.ws.npairs, near);
 }
@@ -967,7 +1113,7 @@ void launch_step(dsr_heap* h, const NbArgs& a, const SplitGrids* split, uint64_t
         else
             k_force<<<tiles, TILE, 0, s>>>(h->dev, a);
     }
-    k_update<<<ctas, 256, 0, s>>>(h->dev, a, grid);
+    k_update<<<ctas, UPDATE_THREADS, 0, s>>>(h->dev, a, grid);
     launch_sort<true>(h, a, s);
     k_partner<<<ctas, 256, 0, s>>>(h->dev, a);
     k_merge<<<ctas, 256, 0, s>>>(h->dev, a);

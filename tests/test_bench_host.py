@@ -62,6 +62,17 @@ def test_summary_carries_batched_and_plain_side_by_side():
     assert len(json.dumps(s)) < 1200  # fits the tail a log keeps
 
 
+def test_batched_hbm_estimate_uses_the_plain_bytes_per_update():
+    # plain: 2e10 updates/s at 0.5 ms a step = 1e7 updates a step; 4e8 bytes
+    # a step over the phases = 40 bytes an update; batched 3e10 updates/s
+    phases = {p: {"bytes_per_launch": 8.0e7} for p in bench.PHASES}
+    line = {"value": 2.0e10, "ms_per_step": 0.5, "phases": phases, "batched": {"object_updates_per_s": 3.0e10}}
+    h = bench.batched_hbm_estimate(line, 6000.0)
+    assert h["bytes_per_object_update"] == pytest.approx(40.0)
+    assert h["algorithmic_gbs"] == pytest.approx(1200.0) and h["frac"] == pytest.approx(0.2)
+    assert h["frac_of_nominal"] == pytest.approx(1200.0 / bench.NOMINAL_HBM_GBS)
+
+
 def test_reference_arm_prints_the_oracle_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
                           "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
