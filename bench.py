@@ -275,11 +275,14 @@ def phase_bytes(phase, objs, blocks, moves, births, deaths):
     return b
 
 
-def replay_phase_counts(lib, k0, seed, warmup, steps, L):
+def replay_phase_counts(lib, k0, seed, warmup, steps, L, flush=None):
     """Event counts of each phase over steps [warmup, warmup + steps) of a
     fresh run of the same simulation (wa-tor is deterministic, so this is the
     timed window's work): objects visited, blocks listed, moves, births and
-    deaths, summed per phase. Host synchronisation between phases; not timed."""
+    deaths, summed per phase. Host synchronisation between phases. Each
+    phase's scan and method kernel are also timed with CUDA events
+    ("scan_ms", "method_ms", summed), with L2 flushed (`flush`, a buffer
+    larger than L2) before every step as in the timed steps."""
     import torch
     from paper_1809_07444_gb300.apps import Wator
     from paper_1809_07444_gb300.heap import _stream_ptr
@@ -290,17 +293,28 @@ def replay_phase_counts(lib, k0, seed, warmup, steps, L):
     methods = {"F1": (0, L.METHOD_WATOR_F1), "F2": (0, L.METHOD_WATOR_F2), "S0": (1, L.METHOD_WATOR_S0),
                "S1": (1, L.METHOD_WATOR_S1), "S2": (1, L.METHOD_WATOR_S2)}
     w.step(warmup)
-    tot = {p: dict(objs=0, blocks=0, moves=0, births=0, deaths=0) for p in PHASES}
-    for _ in range(steps):
+    tot = {p: dict(objs=0, blocks=0, moves=0, births=0, deaths=0, scan_ms=0.0, method_ms=0.0) for p in PHASES}
+    stream = torch.cuda.current_stream()
+    for k in range(steps):
+        if flush is not None:
+            flush.fill_(k & 0xFF)
         for p in PHASES:
             t, m = methods[p]
             c0 = w.heap.counters()
+            a, b, e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+            a.record(stream)
             L.check(lib.dsr_doall_scan(w.heap.handle, t, sp), "dsr_doall_scan")
+            b.record(stream)
             torch.cuda.synchronize()
             nblocks = int(w.heap.arena[8:12].cpu().view(torch.int32).item())  # R length in the heap header
+            e0.record(stream)
             L.check(lib.dsr_doall_run(w.heap.handle, t, m, C.byref(wh), C.sizeof(wh), sp), "dsr_doall_run")
+            e1.record(stream)
+            e1.synchronize()
             c1 = w.heap.counters()
             d = tot[p]
+            d["scan_ms"] += a.elapsed_time(b)
+            d["method_ms"] += e0.elapsed_time(e1)
             d["objs"] += c1["visits"] - c0["visits"]
             d["blocks"] += nblocks
             d["moves"] += c1["app0"] - c0["app0"]
@@ -336,13 +350,19 @@ def run_gpu(args, rank, world):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # warm-up
+    # warm-up, every phase timed: the slowest method kernel is the one the
+    # timed steps bracket with events (the roofline kernel); events around
+    # every kernel would lengthen the timed steps themselves
+    sim.phase_timing(args.warmup)
     for _ in range(args.warmup):
         L.check(lib.dsr_wator_step(sim.handle, 1, sp), "dsr_wator_step")
+    warm_ms, _, n_warm = sim.phase_times()
+    dominant = max(PHASES, key=lambda p: warm_ms[p]) if n_warm else None
     torch.cuda.synchronize()
     c0 = sim.heap.counters()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     sim.phase_timing(args.steps)
+    sim.phase_select(PHASES.index(dominant) if dominant else None)
     barrier()
     with Clocks(dev) as clk:
         for k in range(args.steps):
@@ -360,20 +380,26 @@ def run_gpu(args, rank, world):
         raise RuntimeError("device error flags %d" % st["error_flags"])
 
     phase_ms, scan_ms, n_rec = sim.phase_times()
+    sim.phase_select(None)
     sim.phase_timing(0)
     if n_rec != args.steps:
         raise RuntimeError("phase timing recorded %d of %d steps" % (n_rec, args.steps))
-    counts = replay_phase_counts(lib, k0, seed, args.warmup, args.steps, L)
+    counts = replay_phase_counts(lib, k0, seed, args.warmup, args.steps, L, flush)
     replay_visits = sum(c["objs"] for c in counts.values())
     if replay_visits != visits:
         raise RuntimeError("replay visited %d objects, the timed window %d" % (replay_visits, visits))
     phases = {}
     for p in PHASES:
-        c = counts[p]
+        c = dict(counts[p])
+        r_scan, r_method = c.pop("scan_ms"), c.pop("method_ms")
+        timed = dominant is None or p == dominant
+        ms = phase_ms[p] if timed else r_method
         by = phase_bytes(p, **c)
-        phases[p] = dict(c, kernel=KERNELS[p], method_ms_per_step=phase_ms[p] / args.steps,
-                         scan_ms_per_step=scan_ms[p] / args.steps, bytes_per_launch=by / args.steps,
-                         gbs=by / (phase_ms[p] * 1e-3) / 1e9 if phase_ms[p] > 0 else None)
+        phases[p] = dict(c, kernel=KERNELS[p], method_ms_per_step=ms / args.steps,
+                         scan_ms_per_step=(scan_ms[p] if dominant is None else r_scan) / args.steps,
+                         bytes_per_launch=by / args.steps, gbs=by / (ms * 1e-3) / 1e9 if ms > 0 else None,
+                         timing="timed steps" if timed else "replay of the timed steps",
+                         replay_method_ms_per_step=r_method / args.steps)
 
     # e2e through the C ABI with host buffers
     k0_host = torch.from_numpy(np.ascontiguousarray(k0.reshape(-1))).pin_memory()
@@ -901,7 +927,8 @@ TRAFFIC = {"F2": {"bytes": 68634957, "steps": 20, "warmup": 5, "cache_control": 
 
 def roofline(phases, peak, peak_kind, steps, warmup):
     """HBM roofline of the method kernel with the largest share of the step."""
-    p = max(PHASES, key=lambda q: phases[q]["method_ms_per_step"])
+    timed = [q for q in PHASES if phases[q].get("timing", "timed steps") == "timed steps"]
+    p = max(timed or PHASES, key=lambda q: phases[q]["method_ms_per_step"])
     ph = phases[p]
     achieved = ph["gbs"]
     cap = TRAFFIC.get(p)
@@ -914,7 +941,7 @@ def roofline(phases, peak, peak_kind, steps, warmup):
                                if cap is not None else None),
             "kernel": ph["kernel"], "phase": p,
             "algorithmic_bytes_per_launch": ph["bytes_per_launch"], "launch_ms": ph["method_ms_per_step"],
-            "timing": "CUDA events on the launching stream around every launch of the timed steps",
+            "timing": "CUDA events on the launching stream around every launch of this kernel in the timed steps",
             "peak_source": ("measured hbm_gbs" if peak_kind == "measured" else "fallback 6.8 TB/s")}
 
 

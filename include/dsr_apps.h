@@ -137,13 +137,23 @@ int dsr_wator_destroy(dsr_wator* w);
  * max_steps > 0, creates 11 CUDA events per step for the next max_steps
  * steps (device current = the heap's); each of those steps then records them
  * on its stream at its start and after every scan and method kernel. 0 frees
- * them. Events cost a few microseconds of host time per step and nothing on
- * the device. DSR_E_CUDA if an event cannot be created (none are kept). */
+ * them. Each recorded event also lengthens the step on the device: on a
+ * GB300, the 11 events of a 2048 x 2048 step added 5-20 us to its 0.29 ms
+ * (dsr_wator_phase_select records two). DSR_E_CUDA if an event cannot be
+ * created (none are kept). */
 int dsr_wator_phase_timing(dsr_wator* w, int max_steps);
+/* Restricts the events of dsr_wator_phase_timing to the method kernel of one
+ * phase: phase 0..4 (F1, F2, S0, S1, S2) records only the two events around
+ * that kernel, -1 (the default) records all 11. Starts a new window (steps
+ * recorded before are dropped); dsr_wator_phase_times then reports that
+ * phase's method time and 0 for the other entries. DSR_E_INVALID for another
+ * phase value. */
+int dsr_wator_phase_select(dsr_wator* w, int phase);
 /* Waits for the last recorded step, then writes the summed device
  * milliseconds of the steps recorded since the last call: out_ms[0..4] the
- * method kernels of F1, F2, S0, S1, S2, out_ms[5..9] their scans; *steps =
- * the number of steps. Starts a new window (the events are reused). */
+ * method kernels of F1, F2, S0, S1, S2, out_ms[5..9] their scans (the times
+ * between a phase's start and its method kernel); *steps = the number of
+ * steps. Starts a new window (the events are reused). */
 int dsr_wator_phase_times(dsr_wator* w, double* out_ms /* 10 */, int* steps);
 
 /* Wa-tor on the BitmapAlloc comparator (dsr_bm_heap_* in dsr.h): the same

@@ -134,6 +134,7 @@ SIGNATURES = {
     "dsr_wator_kinds": (_i, [_vp, _vp, _vp]),
     "dsr_wator_destroy": (_i, [_vp]),
     "dsr_wator_phase_timing": (_i, [_vp, _i]),
+    "dsr_wator_phase_select": (_i, [_vp, _i]),
     "dsr_wator_attach": (_i, [_vp, _vp, _vp, C.POINTER(_vp)]),
     "dsr_bm_heap_bytes": (_i, [C.POINTER(TypeDesc), _i, C.POINTER(_u64), C.POINTER(_sz)]),
     "dsr_bm_heap_create": (_i, [C.POINTER(TypeDesc), _i, C.POINTER(_u64), _vp, _sz, _vp, C.POINTER(_vp)]),

@@ -136,6 +136,12 @@ class Wator:
         max_steps steps (0 turns it off)."""
         L.check(self.lib.dsr_wator_phase_timing(self.handle, int(max_steps)), "dsr_wator_phase_timing")
 
+    def phase_select(self, phase):
+        """Time only the method kernel of one phase (its index in PHASES), or
+        every scan and method kernel with None; starts a new window."""
+        L.check(self.lib.dsr_wator_phase_select(self.handle, -1 if phase is None else int(phase)),
+                "dsr_wator_phase_select")
+
     def phase_times(self):
         """({phase: method-kernel ms}, {phase: scan ms}, steps) summed over the
         steps recorded since the last call."""

@@ -403,6 +403,7 @@ struct dsr_wator {
     // phase timing: kPhaseEvents events per step, created when enabled
     std::vector<cudaEvent_t> ev;
     int ev_steps = 0;  // steps recorded in the current window
+    int ev_phase = -1; // the one phase whose method kernel is timed, or -1: all
 };
 constexpr int kPhaseEvents = 11;  // step start, then after each scan and each method kernel
 
@@ -463,11 +464,16 @@ extern "C" int dsr_wator_step(dsr_wator* w, int n_steps, void* stream) {
     dsr_heap* h = w->heap;
     for (int i = 0; i < n_steps; ++i) {
         cudaEvent_t* e = nullptr;
+        const int sel = w->ev_phase;
         if ((size_t)(w->ev_steps + 1) * kPhaseEvents <= w->ev.size()) {
             e = w->ev.data() + (size_t)w->ev_steps++ * kPhaseEvents;
-            cudaEventRecord(e[0], s);
+            if (sel < 0) cudaEventRecord(e[0], s);
         }
-        auto E = [&](int k) { return e ? e[k] : nullptr; };
+        // event k: k = 2p + 1 after phase p's scan, k = 2p + 2 after its method
+        auto E = [&](int k) -> cudaEvent_t {
+            if (!e || (sel >= 0 && k != 2 * sel + 1 && k != 2 * sel + 2)) return nullptr;
+            return e[k];
+        };
         // F1 neither creates nor deletes fish, so F2 runs over F1's block
         // list (the fish live at the start of the step); likewise S2 over
         // S1's (the sharks that survived S0).
@@ -497,11 +503,33 @@ extern "C" int dsr_wator_phase_timing(dsr_wator* w, int max_steps) {
     return DSR_OK;
 }
 
+extern "C" int dsr_wator_phase_select(dsr_wator* w, int phase) {
+    if (!w || phase < -1 || phase > 4) return DSR_E_INVALID;
+    w->ev_phase = phase;
+    w->ev_steps = 0;  // a window records one selection
+    return DSR_OK;
+}
+
 extern "C" int dsr_wator_phase_times(dsr_wator* w, double* out_ms, int* steps) {
     if (!w || !out_ms || !steps) return DSR_E_INVALID;
     for (int k = 0; k < 10; ++k) out_ms[k] = 0;
     *steps = w->ev_steps;
-    if (w->ev_steps) {
+    const int sel = w->ev_phase;
+    if (w->ev_steps && sel >= 0) {
+        // only the selected phase's method kernel was bracketed
+        const size_t last = (size_t)(w->ev_steps - 1) * kPhaseEvents + 2 * sel + 2;
+        cudaError_t err = cudaEventSynchronize(w->ev[last]);
+        for (int i = 0; i < w->ev_steps && err == cudaSuccess; ++i) {
+            const cudaEvent_t* e = w->ev.data() + (size_t)i * kPhaseEvents;
+            float run = 0;
+            err = cudaEventElapsedTime(&run, e[2 * sel + 1], e[2 * sel + 2]);
+            out_ms[sel] += run;
+        }
+        if (err != cudaSuccess) {
+            dsr__set_cuda_error(err, "dsr_wator_phase_times");
+            return DSR_E_CUDA;
+        }
+    } else if (w->ev_steps) {
         cudaError_t err = cudaEventSynchronize(w->ev[(size_t)w->ev_steps * kPhaseEvents - 1]);
         for (int i = 0; i < w->ev_steps && err == cudaSuccess; ++i) {
             const cudaEvent_t* e = w->ev.data() + (size_t)i * kPhaseEvents;

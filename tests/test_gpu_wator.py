@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from paper_1809_07444_gb300 import _lib as L
 from paper_1809_07444_gb300 import workloads as WL
 from paper_1809_07444_gb300.apps import Wator
 
@@ -71,6 +72,23 @@ def test_wator_phase_timing_records_every_step():
     w.phase_timing(0)
     w.step(1)
     assert w.phase_times()[2] == 0
+
+
+def test_wator_phase_select_times_one_method_kernel():
+    w = Wator(64, 64, WL.wator_initial(64, 64, 1), 1)
+    w.phase_timing(6)
+    w.step(2)
+    w.phase_select(1)  # F2 only; drops the two steps above
+    w.step(3)
+    run, scan, n = w.phase_times()
+    assert n == 3 and run["F2"] > 0
+    assert all(v == 0 for p, v in run.items() if p != "F2") and all(v == 0 for v in scan.values())
+    w.phase_select(None)
+    w.step(1)
+    run, scan, n = w.phase_times()
+    assert n == 1 and all(v > 0 for v in run.values())
+    with pytest.raises(L.DsrError):
+        w.phase_select(5)
 
 
 def test_wator_2048_full_size_all_500_steps():
