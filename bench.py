@@ -835,6 +835,32 @@ def bench_nbody(n=65536, steps=5):
     return out
 
 
+def bench_batched_fixed(n_inst=256, steps=20, warmup=3):
+    """The batched workload with the default tuning (256 threads, 64-slot
+    blocks, fan-out 64) and nothing else: no autotuning, no one-by-one
+    comparison. The short case for profiling the batched step."""
+    import torch
+    from paper_1809_07444_gb300 import workloads as WL
+    from paper_1809_07444_gb300.apps import WatorBatch
+
+    sides = [int(s) for s in WL.batched_sides(n_inst, 1)]
+    need = sum(WatorBatch.blocks_for(s, s) * 1100 + s * s * 24 for s in sides)
+    b = WatorBatch(need + (256 << 20), max_instances=n_inst)
+    slots = [b.add(s, s, WL.wator_initial(s, s, 1000 + i), 1000 + i) for i, s in enumerate(sides)]
+    b.step(warmup)
+    torch.cuda.synchronize()
+    v0 = sum(b.heap(x).counters()["visits"] for x in slots)
+    e0, e1 = _ev()
+    e0.record()
+    b.step(steps)
+    e1.record()
+    e1.synchronize()
+    v1 = sum(b.heap(x).counters()["visits"] for x in slots)
+    t = e0.elapsed_time(e1) / 1e3
+    return {"workload": "wator-batched-%d (sides log-uniform [64, 1024], seeds 1000+i), default tuning" % n_inst,
+            "steps": steps, "warmup": warmup, "ms_per_step": t * 1e3 / steps, "object_updates_per_s": (v1 - v0) / t}
+
+
 def bench_batched(n_inst=256, steps=20, one_by_one_steps=3):
     """The batched workload (256 wa-tor instances, sides log-uniform in
     [64, 1024]) advanced by graph-captured group steps, against the same
@@ -1029,6 +1055,8 @@ def replica_seed(rank):
 
 LEGS = {
     "batched": lambda a: bench_batched(),
+    # the batched step alone at the default tuning: the case profiled under ncu
+    "batched_fixed": lambda a: bench_batched_fixed(),
     "alloc": lambda a: bench_alloc_sweep(),
     # one small allocation round (2^20 objects, 2 types) after one untimed
     # round: the case profiled under ncu
