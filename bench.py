@@ -182,6 +182,57 @@ def oracle_config_rates():
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
+# NVML clocks-event reason bits (nvml.h): the ones a run is judged by
+NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+
+def nvml_reason_names(bits):
+    """Names of the judged clocks-event reasons set in an NVML reason word."""
+    return sorted(name for bit, name in NVML_REASONS.items() if bits & bit)
+
+
+class NvmlSampler:
+    """SM clock and clocks-event reasons of one GPU, read through NVML (the
+    driver's management library, read-only queries) about every millisecond
+    in a thread, so that a timed region of a few milliseconds still gets
+    several samples. Raises on __init__ when NVML is not available."""
+
+    def __init__(self, index):
+        nv = C.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.nv = nv
+        self.h = C.c_void_p()
+        if nv.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(self.h)) != 0:
+            raise RuntimeError("no NVML device %d" % index)
+        self.reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = C.c_uint(0)
+        nv.nvmlDeviceGetMaxClockInfo(self.h, C.c_int(1), C.byref(mx))  # NVML_CLOCK_SM = 1
+        self.max_mhz = float(mx.value)
+        self.samples = []  # (sm MHz, reason bits)
+        self.stop = threading.Event()
+
+    def _run(self):
+        clk, rs = C.c_uint(0), C.c_ulonglong(0)
+        while not self.stop.is_set():
+            if self.nv.nvmlDeviceGetClockInfo(self.h, C.c_int(1), C.byref(clk)) == 0 and \
+                    self.reasons_fn(self.h, C.byref(rs)) == 0:
+                self.samples.append((float(clk.value), int(rs.value)))
+            time.sleep(0.0005)
+
+    def start(self):
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
+        t0 = time.perf_counter()
+        while not self.samples and time.perf_counter() - t0 < 1.0:  # sampling before the region starts
+            time.sleep(0.0005)
+
+    def finish(self):
+        self.stop.set()
+        self.t.join(timeout=2)
+
+
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -191,8 +242,15 @@ class Clocks:
         self.index = index
         self.rows = []
         self.proc = None
+        self.nvml = None
 
     def __enter__(self):
+        try:
+            self.nvml = NvmlSampler(self.index)
+            self.nvml.start()
+            return self
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -208,6 +266,8 @@ class Clocks:
             self.rows.append([c.strip() for c in line.split(",")])
 
     def __exit__(self, *a):
+        if self.nvml:
+            self.nvml.finish()
         if self.proc:
             self.proc.terminate()
             try:
@@ -216,6 +276,13 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
+        if self.nvml and self.nvml.samples:
+            sm = [c for c, _ in self.nvml.samples]
+            bits = 0
+            for _, r in self.nvml.samples:
+                bits |= r
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.nvml.max_mhz,
+                    "reasons": nvml_reason_names(bits), "samples": len(sm), "source": "nvml, ~1 ms"}
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
@@ -227,7 +294,7 @@ class Clocks:
                 if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": sorted(reasons), "samples": len(self.rows), "source": "nvidia-smi, 200 ms"}
 
 
 # ---------------------------------------------------------------------------
