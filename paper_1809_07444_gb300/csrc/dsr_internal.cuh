@@ -59,12 +59,21 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
     if (type < 0 || type >= h->dev.n_types) return DSR_E_INVALID;
     if (with_scan) dsr__launch_scan(h, type, s, 1u + (unsigned)reuse, exact);
     if (ev_scan) cudaEventRecord(ev_scan, s);
+    // The occupancy-limited grid of this kernel and CTA size is looked up
+    // once and cached; a heap whose tuning fixes the CTAs per SM computes its
+    // own and leaves the cache alone (other heaps keep the occupancy limit).
     static int grid_cache[17] = {0};
     const int threads = h->tune.threads;
     const bool small = threads <= 256;  // the occupancy-bounded kernel
     const void* kfn = small ? (const void*)dsr_doall_kernel_256<M> : (const void*)dsr_doall_kernel<M>;
-    int& grid = grid_cache[threads / 64];
-    if (grid == 0 || h->tune.ctas_per_sm > 0) grid = dsr__persistent_grid(h, kfn, threads);
+    int grid;
+    if (h->tune.ctas_per_sm > 0) {
+        grid = dsr__persistent_grid(h, kfn, threads);
+    } else {
+        int& cached = grid_cache[threads / 64];
+        if (cached == 0) cached = dsr__persistent_grid(h, kfn, threads);
+        grid = cached;
+    }
     // Persistent grid: the CTAs that fit on the GPU at once, capped by the
     // work a do-all over this heap can list. (Every CTA ends with one atomic
     // on the completion counter, so a much larger grid costs more in those
@@ -78,9 +87,15 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
     int rc;
     if constexpr (dsr_has_run4<M>::value) {
         if (dsr__vec4_ok(h, type)) {
-            static int vgrid = 0;
-            if (vgrid == 0 || h->tune.ctas_per_sm > 0)
+            static int vgrid_cache[17] = {0};
+            int vgrid;
+            if (h->tune.ctas_per_sm > 0) {
                 vgrid = dsr__persistent_grid(h, (const void*)dsr_doall_kernel_vec4<M>, threads);
+            } else {
+                int& cached = vgrid_cache[threads / 64];
+                if (cached == 0) cached = dsr__persistent_grid(h, (const void*)dsr_doall_kernel_vec4<M>, threads);
+                vgrid = cached;
+            }
             int gv = vgrid < g ? vgrid : g;
             dsr_doall_kernel_vec4<M><<<gv, threads, 0, s>>>(h->dev, type, args, reuse > 0 ? 1 : 0);
             rc = dsr__check_launch("dsr_doall_kernel_vec4");
