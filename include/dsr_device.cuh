@@ -48,6 +48,9 @@ typedef dsr_u64 dsr_ref;
 #define DSR_CTR_SLOTS 256u       /* event-counter rows (indexed by SM id) */
 #define DSR_SLOW_WAITS 64u       /* rounds a leader may wait for another initialisation */
 #define DSR_CHASE_ROUNDS 4       /* atomics on one block per search before searching again */
+#ifndef DSR_FRESH_REST
+#define DSR_FRESH_REST 12        /* slots still wanted after a first round that send a leader to a fresh block */
+#endif
 
 /* One hierarchical bitmap: level l has nwords[l] 64-bit containers, of
  * which the low 2^shift bits are used (the fan-out: 64, 32 or 16). */
@@ -418,10 +421,10 @@ __device__ inline dsr_grab dsr_init_block(const dsr_dev_heap& H, int T, int k, u
  * active[T] (the block is full). Slow path: take a block from free (find and
  * clear), initialise it for T with the first slots already taken, publish
  * its bitmap, then set allocated[T] and, if slots remain, active[T]. */
-__device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsigned hint) {
+__device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsigned hint, bool fresh = false) {
     unsigned empty_rounds = 0;  // slow paths that found no free block
     for (unsigned a = 0; a < DSR_ALLOC_CAP; ++a) {
-        long long b = dsr_hb_find(H.active_bm[T], hint + a * 0x61C88647u);
+        long long b = fresh && a == 0 ? -1 : dsr_hb_find(H.active_bm[T], hint + a * 0x61C88647u);
         if (b < 0) {
             // Many warps miss the fast path at the same moment (a kernel that
             // starts by allocating). Rather than each opening its own block,
@@ -526,7 +529,10 @@ __device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
         dsr_u64 bid = 0, bits = 0;
         uint32_t st = 0;
         if ((int)lane == leader) {
-            const dsr_grab g = dsr_reserve(H, T, need - served, hint + (unsigned)served);
+            // a group still wanting many slots after a first round takes a
+            // fresh block rather than walking partly filled ones one by one
+            const bool fresh = DSR_FRESH_REST > 0 && served > 0 && need - served >= DSR_FRESH_REST;
+            const dsr_grab g = dsr_reserve(H, T, need - served, hint + (unsigned)served, fresh);
             bid = g.bid;
             bits = g.bits;
             st = g.status;
