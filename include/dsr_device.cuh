@@ -420,7 +420,11 @@ __device__ inline dsr_grab dsr_init_block(const dsr_dev_heap& H, int T, int k, u
  * keep those actually obtained; if that emptied the free bits, clear
  * active[T] (the block is full). Slow path: take a block from free (find and
  * clear), initialise it for T with the first slots already taken, publish
- * its bitmap, then set allocated[T] and, if slots remain, active[T]. */
+ * its bitmap, then set allocated[T] and, if slots remain, active[T]. With
+ * `fresh` the first attempt goes to the slow path directly; when the
+ * throttle holds it back or no free block is left, the fast path follows as
+ * usual, so a heap whose only free slots are in active blocks still serves
+ * the request. */
 __device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsigned hint, bool fresh = false) {
     unsigned empty_rounds = 0;  // slow paths that found no free block
     for (unsigned a = 0; a < DSR_ALLOC_CAP; ++a) {
