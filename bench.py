@@ -182,12 +182,13 @@ def oracle_config_rates():
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
-# NVML clocks-event reason bits (nvml.h): the ones a run is judged by
+# NVML clocks-event reason bits (nvml.h): power capping, and the slowdowns
+# that make a timing run suspect
 NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
 
 def nvml_reason_names(bits):
-    """Names of the judged clocks-event reasons set in an NVML reason word."""
+    """Names of the reasons above that are set in an NVML reason word."""
     return sorted(name for bit, name in NVML_REASONS.items() if bits & bit)
 
 
