@@ -75,7 +75,7 @@ def test_batched_hbm_estimate_uses_the_plain_bytes_per_update():
 
 def test_clock_reasons_decode_the_nvml_bits():
     # sw_power_cap 0x4, hw_slowdown 0x8, sw_thermal 0x20, hw_thermal 0x40;
-    # idle (0x1) and the others are not judged
+    # idle (0x1) and the other reasons are not reported
     assert bench.nvml_reason_names(0) == []
     assert bench.nvml_reason_names(0x1 | 0x4) == ["sw_power_cap"]
     assert bench.nvml_reason_names(0x8 | 0x20 | 0x40) == ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"]
