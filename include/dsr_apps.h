@@ -119,6 +119,13 @@ int dsr_wator_workspace_bytes(const dsr_heap* heap, int W, int H, size_t* out);
  * timer 0; sharks timer 0 and energy shark_energy0. */
 int dsr_wator_create(dsr_heap* heap, const dsr_wator_params* p, const void* kind0_dev, void* workspace_dev,
                      void* stream, dsr_wator** out);
+/* Advances n_steps steps on `stream` (each step: F1, F2, S0, S1, S2 as
+ * do-alls). A step is replayed from a CUDA graph of its 8 launches that the
+ * handle captures on first use on a private stream (one for untimed steps,
+ * one for the current dsr_wator_phase_timing / _phase_select setting, which
+ * is captured when that setting is made); while `stream` is itself being
+ * captured, the kernels are launched into that capture instead. If a
+ * capture fails the handle launches kernel by kernel from then on. */
 int dsr_wator_step(dsr_wator* w, int n_steps, void* stream);
 /* A handle over a heap and workspace that already hold a wa-tor state, with
  * no initialisation: resuming from a checkpoint. A checkpoint of a wa-tor

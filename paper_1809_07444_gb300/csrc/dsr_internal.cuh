@@ -49,7 +49,8 @@ void dsr__launch_scan(const dsr_heap* h, int type, cudaStream_t s, unsigned visi
 // Run a do-all: scan + compaction of allocated[type] into R, then the method
 // kernel over the listed blocks.
 // ev_scan / ev_run (optional): recorded on s after the scan and after the
-// method kernel, for per-phase timing. reuse > 0: the block list is kept for
+// method kernel, for per-phase timing (as external records, so that under
+// stream capture they become event-record nodes of the graph). reuse > 0: the block list is kept for
 // `reuse` more do-alls over the same live set, and the scan counts each
 // listed object 1 + reuse times as visited (the visits those do-alls make).
 // exact: visit the objects of `type` only, not those of its subtypes.
@@ -58,7 +59,7 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
                cudaEvent_t ev_scan = nullptr, cudaEvent_t ev_run = nullptr, int reuse = 0, bool exact = false) {
     if (type < 0 || type >= h->dev.n_types) return DSR_E_INVALID;
     if (with_scan) dsr__launch_scan(h, type, s, 1u + (unsigned)reuse, exact);
-    if (ev_scan) cudaEventRecord(ev_scan, s);
+    if (ev_scan) cudaEventRecordWithFlags(ev_scan, s, cudaEventRecordExternal);
     // The occupancy-limited grid of this kernel and CTA size is looked up
     // once and cached; a heap whose tuning fixes the CTAs per SM computes its
     // own and leaves the cache alone (other heaps keep the occupancy limit).
@@ -99,7 +100,7 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
             int gv = vgrid < g ? vgrid : g;
             dsr_doall_kernel_vec4<M><<<gv, threads, 0, s>>>(h->dev, type, args, reuse > 0 ? 1 : 0);
             rc = dsr__check_launch("dsr_doall_kernel_vec4");
-            if (ev_run) cudaEventRecord(ev_run, s);
+            if (ev_run) cudaEventRecordWithFlags(ev_run, s, cudaEventRecordExternal);
             return rc;
         }
     }
@@ -108,7 +109,7 @@ int dsr__doall(dsr_heap* h, int type, const typename M::Args& args, cudaStream_t
     else
         dsr_doall_kernel<M><<<g, threads, 0, s>>>(h->dev, type, args, reuse > 0 ? 1 : 0);
     rc = dsr__check_launch("dsr_doall_kernel");
-    if (ev_run) cudaEventRecord(ev_run, s);
+    if (ev_run) cudaEventRecordWithFlags(ev_run, s, cudaEventRecordExternal);
     return rc;
 }
 

@@ -397,6 +397,19 @@ int launch_kinds(const dsr_heap* heap, const WatorInst& I, void* out, cudaStream
 // ===========================================================================
 // plain form
 // ===========================================================================
+constexpr int kPhaseEvents = 11;  // step start, then after each scan and each method kernel
+
+// One step replayed as a CUDA graph: its 8 launches (and, when the step is
+// timed, its event records as event-record nodes, pointed at each step's
+// own events before the launch). Captured on first use, once for untimed
+// steps and once for the current timing selection.
+struct StepGraph {
+    cudaGraph_t graph = nullptr;  // kept while exec lives: ev_node are its nodes
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t ev_node[kPhaseEvents] = {};  // timed graph: the node of event k, or null
+    int sel = -2;                                // timing selection captured (-2: untimed)
+};
+
 struct dsr_wator {
     dsr_heap* heap;
     WatorInst inst;
@@ -404,10 +417,19 @@ struct dsr_wator {
     std::vector<cudaEvent_t> ev;
     int ev_steps = 0;  // steps recorded in the current window
     int ev_phase = -1; // the one phase whose method kernel is timed, or -1: all
+    StepGraph plain, timed;
+    cudaStream_t capture = nullptr;  // private stream for the captures
+    bool graphs_off = false;         // a capture failed: launch kernel by kernel
 };
-constexpr int kPhaseEvents = 11;  // step start, then after each scan and each method kernel
+
+static void drop_graph(StepGraph& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g = StepGraph{};
+}
 
 static void free_events(dsr_wator* w) {
+    drop_graph(w->timed);  // its nodes name these events
     for (cudaEvent_t e : w->ev) cudaEventDestroy(e);
     w->ev.clear();
     w->ev_steps = 0;
@@ -458,30 +480,124 @@ extern "C" int dsr_wator_attach(dsr_heap* heap, const dsr_wator_params* p, void*
     return DSR_OK;
 }
 
+// The launches of one step on s; e: the step's kPhaseEvents events (null:
+// untimed), of which only the selected phase's two are recorded when sel >= 0.
+static int issue_step(dsr_wator* w, cudaStream_t s, const cudaEvent_t* e, int sel) {
+    dsr_heap* h = w->heap;
+    if (e && sel < 0) cudaEventRecordWithFlags(e[0], s, cudaEventRecordExternal);
+    // event k: k = 2p + 1 after phase p's scan, k = 2p + 2 after its method
+    auto E = [&](int k) -> cudaEvent_t {
+        if (!e || (sel >= 0 && k != 2 * sel + 1 && k != 2 * sel + 2)) return nullptr;
+        return e[k];
+    };
+    // F1 neither creates nor deletes fish, so F2 runs over F1's block list
+    // (the fish live at the start of the step); likewise S2 over S1's (the
+    // sharks that survived S0).
+    int rc = dsr__doall<MFishChoose>(h, FISH, w->inst, s, true, E(1), E(2), 1);
+    if (!rc) rc = dsr__doall<MFishMove>(h, FISH, w->inst, s, false, E(3), E(4));
+    if (!rc) rc = dsr__doall<MSharkStarve>(h, SHARK, w->inst, s, true, E(5), E(6));
+    if (!rc) rc = dsr__doall<MSharkChoose>(h, SHARK, w->inst, s, true, E(7), E(8), 1);
+    if (!rc) rc = dsr__doall<MSharkMove>(h, SHARK, w->inst, s, false, E(9), E(10));
+    return rc;
+}
+
+// Capture one step into g (timed with the events e as placeholders when e is
+// given). Returns false, leaving g empty, if any step of it fails.
+static bool capture_step(dsr_wator* w, StepGraph& g, const cudaEvent_t* e, int sel) {
+    if (!w->capture && cudaStreamCreateWithFlags(&w->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        w->capture = nullptr;
+        return false;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(w->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    const int rc = issue_step(w, w->capture, e, sel);
+    const cudaError_t end = cudaStreamEndCapture(w->capture, &graph);
+    bool ok = rc == DSR_OK && end == cudaSuccess && graph;
+    StepGraph out;
+    out.sel = e ? sel : -2;
+    if (ok && e) {
+        // the event-record nodes, by the placeholder event they record
+        size_t n = 0;
+        ok = cudaGraphGetNodes(graph, nullptr, &n) == cudaSuccess;
+        std::vector<cudaGraphNode_t> nodes(n);
+        if (ok && n) ok = cudaGraphGetNodes(graph, nodes.data(), &n) == cudaSuccess;
+        for (size_t i = 0; ok && i < n; ++i) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess) ok = false;
+            if (!ok || t != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev = nullptr;
+            if (cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) != cudaSuccess) ok = false;
+            for (int k = 0; ok && k < kPhaseEvents; ++k)
+                if (ev == e[k]) out.ev_node[k] = nodes[i];
+        }
+    }
+    if (ok) ok = cudaGraphInstantiate(&out.exec, graph, 0) == cudaSuccess;
+    out.graph = graph;
+    cudaGetLastError();  // a failed capture leaves no error behind for later calls
+    if (!ok) {
+        drop_graph(out);
+        return false;
+    }
+    drop_graph(g);
+    g = out;
+    return true;
+}
+
+// Capture the timed step graph for the current selection now, with the
+// window's first events as placeholders, so that a timed step does not
+// spend its time in a capture.
+static void prepare_timed(dsr_wator* w) {
+    if (w->graphs_off || w->ev.empty()) return;
+    if (!capture_step(w, w->timed, w->ev.data(), w->ev_phase)) w->graphs_off = true;
+}
+
+// One step by graph replay; false if the graph cannot be had (the caller
+// then launches the step kernel by kernel).
+static bool replay_step(dsr_wator* w, cudaStream_t s, const cudaEvent_t* e, int sel, int* rc) {
+    StepGraph& g = e ? w->timed : w->plain;
+    if (!g.exec || (e && g.sel != sel)) {
+        if (!capture_step(w, g, e, sel)) return false;
+    }
+    cudaError_t err = cudaSuccess;
+    if (e)
+        for (int k = 0; k < kPhaseEvents && err == cudaSuccess; ++k)
+            if (g.ev_node[k]) err = cudaGraphExecEventRecordNodeSetEvent(g.exec, g.ev_node[k], e[k]);
+    if (err != cudaSuccess) {  // nothing launched yet: the caller launches the step itself
+        cudaGetLastError();
+        return false;
+    }
+    err = cudaGraphLaunch(g.exec, s);
+    if (err != cudaSuccess) {
+        dsr__set_cuda_error(err, "dsr_wator_step graph");
+        *rc = DSR_E_CUDA;
+    } else {
+        *rc = DSR_OK;
+    }
+    return true;
+}
+
 extern "C" int dsr_wator_step(dsr_wator* w, int n_steps, void* stream) {
     if (!w || n_steps < 0) return DSR_E_INVALID;
     cudaStream_t s = dsr__stream(stream);
-    dsr_heap* h = w->heap;
+    // Steps are replayed as a captured graph, except while the caller's
+    // stream is itself being captured (the kernels then go into the caller's
+    // graph) or after a capture failed.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool use_graph = !w->graphs_off && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+                           cs == cudaStreamCaptureStatusNone;
     for (int i = 0; i < n_steps; ++i) {
         cudaEvent_t* e = nullptr;
-        const int sel = w->ev_phase;
-        if ((size_t)(w->ev_steps + 1) * kPhaseEvents <= w->ev.size()) {
+        if ((size_t)(w->ev_steps + 1) * kPhaseEvents <= w->ev.size())
             e = w->ev.data() + (size_t)w->ev_steps++ * kPhaseEvents;
-            if (sel < 0) cudaEventRecord(e[0], s);
+        int rc = DSR_OK;
+        if (use_graph && !w->graphs_off) {
+            if (replay_step(w, s, e, w->ev_phase, &rc)) {
+                if (rc) return rc;
+                continue;
+            }
+            w->graphs_off = true;
         }
-        // event k: k = 2p + 1 after phase p's scan, k = 2p + 2 after its method
-        auto E = [&](int k) -> cudaEvent_t {
-            if (!e || (sel >= 0 && k != 2 * sel + 1 && k != 2 * sel + 2)) return nullptr;
-            return e[k];
-        };
-        // F1 neither creates nor deletes fish, so F2 runs over F1's block
-        // list (the fish live at the start of the step); likewise S2 over
-        // S1's (the sharks that survived S0).
-        int rc = dsr__doall<MFishChoose>(h, FISH, w->inst, s, true, E(1), E(2), 1);
-        if (!rc) rc = dsr__doall<MFishMove>(h, FISH, w->inst, s, false, E(3), E(4));
-        if (!rc) rc = dsr__doall<MSharkStarve>(h, SHARK, w->inst, s, true, E(5), E(6));
-        if (!rc) rc = dsr__doall<MSharkChoose>(h, SHARK, w->inst, s, true, E(7), E(8), 1);
-        if (!rc) rc = dsr__doall<MSharkMove>(h, SHARK, w->inst, s, false, E(9), E(10));
+        rc = issue_step(w, s, e, w->ev_phase);
         if (rc) return rc;
     }
     return DSR_OK;
@@ -500,6 +616,7 @@ extern "C" int dsr_wator_phase_timing(dsr_wator* w, int max_steps) {
         }
         w->ev.push_back(e);
     }
+    prepare_timed(w);
     return DSR_OK;
 }
 
@@ -507,6 +624,8 @@ extern "C" int dsr_wator_phase_select(dsr_wator* w, int phase) {
     if (!w || phase < -1 || phase > 4) return DSR_E_INVALID;
     w->ev_phase = phase;
     w->ev_steps = 0;  // a window records one selection
+    drop_graph(w->timed);
+    prepare_timed(w);
     return DSR_OK;
 }
 
@@ -556,7 +675,11 @@ extern "C" int dsr_wator_kinds(dsr_wator* w, void* kind_out_dev, void* stream) {
 }
 
 extern "C" int dsr_wator_destroy(dsr_wator* w) {
-    if (w) free_events(w);
+    if (w) {
+        free_events(w);
+        drop_graph(w->plain);
+        if (w->capture) cudaStreamDestroy(w->capture);
+    }
     delete w;
     return DSR_OK;
 }

@@ -91,6 +91,41 @@ def test_wator_phase_select_times_one_method_kernel():
         w.phase_select(5)
 
 
+def test_wator_steps_inside_a_caller_graph_capture_match():
+    # dsr_wator_step replays its own captured graph, except while the
+    # caller's stream is being captured: then its kernels go into the
+    # caller's graph, whose replays must advance the simulation exactly as
+    # stepping does
+    import ctypes as C
+
+    import torch
+    from paper_1809_07444_gb300.heap import _stream_ptr
+    lib = L.load()
+    k0 = WL.wator_initial(128, 128, 3)
+    a = Wator(128, 128, k0, 3)
+    b = Wator(128, 128, k0, 3)
+    torch.cuda.synchronize()  # both initialised on the default stream
+    s = torch.cuda.Stream()
+    a.step(2)
+    with torch.cuda.stream(s):
+        L.check(lib.dsr_wator_step(b.handle, 2, _stream_ptr(s)), "dsr_wator_step")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        L.check(lib.dsr_wator_step(b.handle, 1, _stream_ptr(s)), "dsr_wator_step")
+    for _ in range(6):
+        a.step(1)
+        with torch.cuda.stream(s):
+            g.replay()
+        torch.cuda.synchronize()
+        assert a.hash() == b.hash()
+    fa, sa = a.dump()
+    fb, sb = b.dump()
+    assert np.array_equal(fa, fb) and np.array_equal(sa, sb)
+    assert a.heap.stats()["error_flags"] == 0 and b.heap.stats()["error_flags"] == 0
+    del g
+
+
 def test_wator_2048_full_size_all_500_steps():
     # the 2048 x 2048 workload (30% fish, 3% sharks) for its full 500 steps:
     # state hash and event counts every step, full multisets and the grid
