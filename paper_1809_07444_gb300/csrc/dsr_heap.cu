@@ -477,6 +477,7 @@ extern "C" int dsr_heap_set_bases(dsr_heap* h, const int* base) {
             if (((sub[t] >> u) & 1u) && L.capacity[u] > 32) sh = 6;
         h->dev.span_sh[t] = sh;
     }
+    h->version += 1;
     return DSR_OK;
 }
 

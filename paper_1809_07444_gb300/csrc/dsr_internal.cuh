@@ -18,6 +18,7 @@ struct dsr_heap {
     int device;
     int sm_count;
     dsr_u64* stats_dev;  // scratch in the arena header
+    uint64_t version = 0;  // bumped when `dev` changes after creation (launches captured in a graph hold a copy)
 };
 
 // Arena header (first DSR_HEADER_BYTES bytes of the arena).

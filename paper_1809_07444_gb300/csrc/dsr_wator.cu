@@ -408,6 +408,7 @@ struct StepGraph {
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t ev_node[kPhaseEvents] = {};  // timed graph: the node of event k, or null
     int sel = -2;                                // timing selection captured (-2: untimed)
+    uint64_t version = 0;                        // the heap view's version captured
 };
 
 struct dsr_wator {
@@ -515,6 +516,7 @@ static bool capture_step(dsr_wator* w, StepGraph& g, const cudaEvent_t* e, int s
     bool ok = rc == DSR_OK && end == cudaSuccess && graph;
     StepGraph out;
     out.sel = e ? sel : -2;
+    out.version = w->heap->version;
     if (ok && e) {
         // the event-record nodes, by the placeholder event they record
         size_t n = 0;
@@ -555,7 +557,7 @@ static void prepare_timed(dsr_wator* w) {
 // then launches the step kernel by kernel).
 static bool replay_step(dsr_wator* w, cudaStream_t s, const cudaEvent_t* e, int sel, int* rc) {
     StepGraph& g = e ? w->timed : w->plain;
-    if (!g.exec || (e && g.sel != sel)) {
+    if (!g.exec || (e && g.sel != sel) || g.version != w->heap->version) {
         if (!capture_step(w, g, e, sel)) return false;
     }
     cudaError_t err = cudaSuccess;
