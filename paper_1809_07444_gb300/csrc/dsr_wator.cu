@@ -300,22 +300,18 @@ __global__ void k_wator_init(const __grid_constant__ HP H, const uint8_t* kind0,
         if (c >= n) continue;
         const uint8_t k = kind0[c];
         uint32_t g = K_EMPTY;
-        if (k == 1) {
-            const dsr_ref r = dsr_new(H, FISH);
+        if (k == 1 || k == 2) {
+            // one dsr_new for fish and sharks: the two groups' leaders then
+            // run their reservations side by side rather than one after the
+            // other in two branches
+            const int T = k == 1 ? FISH : SHARK;
+            const dsr_ref r = dsr_new(H, T);
             if (r != DSR_NULL) {
-                *dsr_field<int32_t>(H, FISH, r, X) = (int32_t)(c % (uint32_t)I.p.W);
-                *dsr_field<int32_t>(H, FISH, r, Y) = (int32_t)(c / (uint32_t)I.p.W);
-                *dsr_field<int32_t>(H, FISH, r, TIMER) = 0;
-                g = grid_word(H, r, K_FISH);
-            }
-        } else if (k == 2) {
-            const dsr_ref r = dsr_new(H, SHARK);
-            if (r != DSR_NULL) {
-                *dsr_field<int32_t>(H, SHARK, r, X) = (int32_t)(c % (uint32_t)I.p.W);
-                *dsr_field<int32_t>(H, SHARK, r, Y) = (int32_t)(c / (uint32_t)I.p.W);
-                *dsr_field<int32_t>(H, SHARK, r, TIMER) = 0;
-                *dsr_field<int32_t>(H, SHARK, r, ENERGY) = I.p.shark_energy0;
-                g = grid_word(H, r, K_SHARK);
+                *dsr_field<int32_t>(H, T, r, X) = (int32_t)(c % (uint32_t)I.p.W);
+                *dsr_field<int32_t>(H, T, r, Y) = (int32_t)(c / (uint32_t)I.p.W);
+                *dsr_field<int32_t>(H, T, r, TIMER) = 0;
+                if (T == SHARK) *dsr_field<int32_t>(H, SHARK, r, ENERGY) = I.p.shark_energy0;
+                g = grid_word(H, r, k == 1 ? K_FISH : K_SHARK);
             }
         }
         I.grid[c] = g;
