@@ -1015,7 +1015,7 @@ def bench_served(seconds=20.0, n_jobs=10000, arena_gb=64, lo=128, hi=4096, steps
 # the (steps, warmup) window it was taken on. The bench reports it only when
 # it runs that window (the population, hence the bytes of a launch, changes
 # from step to step); a kernel changed since its capture has no entry.
-TRAFFIC = {"F2": {"bytes": 68277683, "steps": 20, "warmup": 5, "cache_control": "none",
+TRAFFIC = {"F2": {"bytes": 68276505, "steps": 20, "warmup": 5, "cache_control": "none",
                   "source": "profiles/wator2048_fish_move_traffic.md"}}
 
 

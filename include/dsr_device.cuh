@@ -424,11 +424,18 @@ __device__ inline dsr_grab dsr_init_block(const dsr_dev_heap& H, int T, int k, u
  * `fresh` the first attempt goes to the slow path directly; when the
  * throttle holds it back or no free block is left, the fast path follows as
  * usual, so a heap whose only free slots are in active blocks still serves
- * the request. */
-__device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsigned hint, bool fresh = false) {
+ * the request. With near_block >= 0 (a block of this heap) the first
+ * attempt takes that block instead of a search: its free-slot word is read
+ * and the slots are taken as from a found block; a full block, one of
+ * another type or one being reclaimed gives nothing and the search
+ * follows. */
+__device__ inline dsr_grab dsr_reserve(const dsr_dev_heap& H, int T, int k, unsigned hint, bool fresh = false,
+                                       long long near_block = -1) {
     unsigned empty_rounds = 0;  // slow paths that found no free block
     for (unsigned a = 0; a < DSR_ALLOC_CAP; ++a) {
-        long long b = fresh && a == 0 ? -1 : dsr_hb_find(H.active_bm[T], hint + a * 0x61C88647u);
+        long long b = a == 0 && near_block >= 0 ? near_block
+                      : fresh && a == 0       ? -1
+                                              : dsr_hb_find(H.active_bm[T], hint + a * 0x61C88647u);
         if (b < 0) {
             // Many warps miss the fast path at the same moment (a kernel that
             // starts by allocating). Rather than each opening its own block,
@@ -516,8 +523,12 @@ __device__ __forceinline__ dsr_u64 dsr_heap_key(const dsr_dev_heap& H) {
  * leader (allocation request coalescing, Section 2.4): it reserves slots for
  * all of them, in as few atomics as the free slots allow, and hands them out
  * by shuffle. Returns DSR_NULL (and sets DSR_ERR_OOM or DSR_ERR_RETRY) on
- * failure. The new object's fields are not initialised. */
-__device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
+ * failure. The new object's fields are not initialised. `near` (optional):
+ * an object of the same heap whose block the leader tries first, before
+ * searching the bitmaps (the leader's own hint counts for its group), for
+ * example the parent of a newborn or an object just deleted; a hint only,
+ * any handle of the heap or DSR_NULL is allowed. */
+__device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T, dsr_ref near = DSR_NULL) {
     const unsigned act = __activemask();
     const unsigned peers = __match_any_sync(act, dsr_heap_key(H) | (dsr_u64)T);
     const unsigned lane = dsr_lane();
@@ -529,14 +540,19 @@ __device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
     int served = 0;
     // Each round the leader takes as many slots as the block it finds (or a
     // new block) offers, until the group is served.
+    int round = 0;  // reservation rounds of the leader
     while (served < need) {
         dsr_u64 bid = 0, bits = 0;
         uint32_t st = 0;
         if ((int)lane == leader) {
-            // a group still wanting many slots after a first round takes a
-            // fresh block rather than walking partly filled ones one by one
-            const bool fresh = DSR_FRESH_REST > 0 && served > 0 && need - served >= DSR_FRESH_REST;
-            const dsr_grab g = dsr_reserve(H, T, need - served, hint + (unsigned)served, fresh);
+            // The first round tries the leader's placement hint, if it gave
+            // one. A group still wanting many slots after a round that
+            // searched takes a fresh block rather than walking partly
+            // filled ones one by one.
+            const long long nb = round == 0 && near != DSR_NULL && (near >> 6) < H.M ? (long long)(near >> 6) : -1;
+            const bool fresh = DSR_FRESH_REST > 0 && served > 0 && round > (near != DSR_NULL ? 1 : 0) &&
+                               need - served >= DSR_FRESH_REST;
+            const dsr_grab g = dsr_reserve(H, T, need - served, hint + (unsigned)served, fresh, nb);
             bid = g.bid;
             bits = g.bits;
             st = g.status;
@@ -550,6 +566,7 @@ __device__ inline dsr_ref dsr_new(const dsr_dev_heap& H, int T) {
         const int n = __popcll(bits);
         if (rank >= served && rank < served + n) mine = (bid << 6) | (dsr_u64)dsr_nth_bit(bits, rank - served);
         served += n;
+        ++round;
     }
     return mine;
 }

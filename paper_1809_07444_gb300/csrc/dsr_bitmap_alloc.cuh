@@ -95,6 +95,8 @@ __device__ inline dsr_ref dsr_new(const dsr_bm_dev& H, int T) {
     }
     return mine;
 }
+// The placement hint of dsr_new has no counterpart in the comparator.
+__device__ inline dsr_ref dsr_new(const dsr_bm_dev& H, int T, dsr_ref) { return dsr_new(H, T); }
 
 /* delete: lanes freeing slots of one bitmap word of one heap are combined
  * into one atomicAnd. */

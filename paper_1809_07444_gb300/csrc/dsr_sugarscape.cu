@@ -190,7 +190,7 @@ struct MReplace {
         }
         count_event(a, EV_AWAY, away);
         dsr_delete(H, self);  // first, so that the new agent may take the slot
-        const dsr_ref r = dsr_new(H, AGENT);
+        const dsr_ref r = dsr_new(H, AGENT, self);  // tried first: the block just given a free slot
         if (r == DSR_NULL) return;  // out of memory: DSR_ERR_OOM is set
         *fld(H, r, F_X) = (int32_t)(at % a.p.W);
         *fld(H, r, F_Y) = (int32_t)(at / a.p.W);
